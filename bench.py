@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Benchmark of exact betweenness centrality (Brandes) on one GB300.
+
+Metric: BC GTEPS = (sources x canonical edges) / seconds.  One step is one
+complete BC job over the workload's source list (forward BFS with path
+counts, backward dependency sweep, BC accumulation, output scaling) through
+the library's C ABI with inputs resident in HBM; the `e2e` figure repeats the
+step through the same C ABI starting from host buffers (graph upload, compute,
+result download).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference]
+
+Under torchrun (N > 1) the workload's sources are split into N contiguous
+shards, each rank computes its shard's partial BC and the partial vectors are
+summed onto rank 0 (the one exchange step of the method).  `--impl reference`
+times the CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import bcgen  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    # R-MAT scale 16, edge factor 16, all 65,536 sources in batches of 64
+    "rmat16-exact": dict(kind="rmat", scale=16, ef=16, seed=1, sources="all", batch_k=64,
+                         schedule="batch"),
+    # R-MAT scale 20, edge factor 16, 4096 / 1024 seeded uniform sources
+    "rmat20-sampled4096": dict(kind="rmat", scale=20, ef=16, seed=1, sources=4096,
+                               src_seed=1, batch_k=64, schedule="batch"),
+    "rmat20-sampled1024": dict(kind="rmat", scale=20, ef=16, seed=1, sources=1024,
+                               src_seed=1, batch_k=64, schedule="batch"),
+    # directed preferential attachment n = 2^20, 8 out-edges, 4096 sources
+    "ba20-sampled4096": dict(kind="ba", n=1 << 20, out=8, seed=1, sources=4096, src_seed=1,
+                             batch_k=64, schedule="batch"),
+    # R-MAT scale 10, edge factor 8, all 1024 sources, one source per launch
+    "rmat10-exact-plain": dict(kind="rmat", scale=10, ef=8, seed=1, sources="all", batch_k=1,
+                               schedule="plain", fp64=True),
+}
+
+
+def make_graph(w):
+    if w["kind"] == "rmat":
+        return bcgen.rmat(w["scale"], w["ef"], seed=w["seed"])
+    return bcgen.ba_directed(w["n"], w["out"], 9, seed=w["seed"])
+
+
+def source_list(w, n):
+    if w["sources"] == "all":
+        return np.arange(n, dtype=np.int32)
+    return bcgen.sample_sources(n, w["sources"], seed=w["src_seed"])
+
+
+def describe(name, w, g, nsrc):
+    d = {"workload": name, "graph": g.name, "n": g.n, "m": g.m, "sources": nsrc,
+         "batch_k": w["batch_k"], "schedule": w["schedule"]}
+    return d
+
+
+# ---- bytes model --------------------------------------------------------------
+
+def bytes_model(stats, schedule, delta_bytes):
+    """Algorithmic bytes of the BC kernels for the counters of one job
+    (element granularity, each element the design must touch counted once).
+
+    batch: 124 B per frontier entry (queue id/mask, CSR offsets, dense mask
+           read/write/clear, visited, BC read-modify-write), 12 B per scanned
+           edge (column id + the 8-byte mask of the other endpoint),
+           (8 + b) B per (source, DAG edge) (path count of the predecessor,
+           coefficient of the successor), (24 + b) B per (source, reached
+           vertex) (path count write, read, reset; coefficient write).
+    plain: (84 + b) B per entry, 8 B per scanned edge (column + int32 depth),
+           (8 + b) B per DAG edge.
+    """
+    E = stats["frontier_entries"]
+    I, O = stats["scanned_in_edges"], stats["scanned_out_edges"]
+    D, R = stats["dag_pairs"], stats["reached_pairs"]
+    b = delta_bytes
+    if schedule == "batch":
+        return 124 * E + 12 * (I + O) + (8 + b) * D + (24 + b) * R
+    return (84 + b) * E + 8 * (I + O) + (8 + b) * D
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ["bc_kernels.cu", "bc_internal.cuh"]:
+        with open(os.path.join(ROOT, "paper_1409_7764_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the batch kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(workload)
+    if not entry or entry.get("kernel_sha") != kernel_source_sha():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{device}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- CPU oracle baseline ----------------------------------------------------------
+
+def _oracle_chunk(args):
+    n, rp, ci, srcs = args
+    import oracle
+    oracle.bc(n, rp, ci, srcs)
+    return len(srcs)
+
+
+def cpu_oracle_run(pool, cores, g, srcs, target_s):
+    """Times the oracle (as it stands) on a bounded sample of the workload's
+    sources, split over `cores` spawned worker processes."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.bc(g.n, g.row_ptr, g.col_idx, srcs[:1])
+    t1 = max(time.perf_counter() - t0, 1e-4)
+    count = int(max(cores, min(len(srcs), target_s * cores / t1)))
+    sample = srcs[:count]
+    parts = [(g.n, g.row_ptr, g.col_idx, s) for s in np.array_split(sample, cores) if len(s)]
+    t0 = time.perf_counter()
+    done = sum(pool.map(_oracle_chunk, parts))
+    wall = time.perf_counter() - t0
+    return {"value": done * g.m / wall / 1e9, "unit": "GTEPS", "cores": len(parts),
+            "kind": "oracle",
+            "sample": f"first {done} of the workload's {len(srcs)} sources "
+                      f"(sequential Brandes in C, one process per core)",
+            "seconds": wall}
+
+
+# ---- reference arm ------------------------------------------------------------------
+
+def run_reference(args, w, name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g = make_graph(w)
+    srcs = source_list(w, g.n)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(g.n, g.row_ptr, g.col_idx, srcs[:1])] * cores)
+        per_step_target = 6.0
+        res = []
+        for i in range(args.warmup + args.steps):
+            r = cpu_oracle_run(pool, cores, g, srcs, per_step_target)
+            if i >= args.warmup:
+                res.append(r)
+    vals = [r["value"] for r in res]
+    value = statistics.mean(vals)
+    secs = [r["seconds"] for r in res]
+    line = {
+        "impl": "reference", "metric": "BC GTEPS (sources*m/s)", "value": value,
+        "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+        "config": describe(name, w, g, len(srcs)),
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": res[0]["cores"],
+                         "kind": "oracle", "sample": res[0]["sample"]},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm ----------------------------------------------------------------------
+
+def run_ours(args, w, name):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    g = make_graph(w)
+    srcs = source_list(w, g.n)
+    shards = np.array_split(srcs, world)
+    mine = shards[rank]
+
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cores)  # before any GPU call
+        pool.map(_oracle_chunk, [(g.n, g.row_ptr, g.col_idx, srcs[:1])] * cores)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1409_7764_gb300 as bc
+    stream = torch.cuda.current_stream()
+    ctx = bc.Context(local, stream=stream)
+    fp64 = bool(w.get("fp64", False)) or args.fp64
+    opts = dict(schedule=w["schedule"], batch_k=w["batch_k"], delta_fp64=fp64)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    out = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.sources(G, mine, out=out, **opts)
+        if dist is not None:
+            dist.reduce(out, dst=0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    stats = []
+    for _ in range(args.steps):
+        flush.fill_(1)  # L2 flush between timed steps (outside the events)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step()
+        e.record(stream)
+        evs.append((s, e))
+        stats.append(ctx.last_stats())
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in evs]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = len(srcs) * g.m / (ms_per_step / 1e3) / 1e9
+
+    # kernel-level roofline of the batch (or plain) kernel on this rank
+    st = stats[-1]
+    delta_bytes = 8 if fp64 else 4
+    algo_bytes = bytes_model(st, w["schedule"], delta_bytes)
+    launches = max(st["batches"], 1)
+    my_ms = sum(step_ms) / args.steps
+    achieved = algo_bytes / (my_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = ncu_traffic(name)
+
+    # end-to-end: host CSR in, host BC out, through the C ABI
+    e2e_ms = []
+    host_out = np.empty(g.n, dtype=np.float64)
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = ctx.create_graph(g.row_ptr, g.col_idx)
+        ctx.sources(G2, mine, out=host_out, **opts)
+        ctx.destroy_graph(G2)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_step = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    e2e_value = len(srcs) * g.m / (e2e_step / 1e3) / 1e9
+    h2d = 4 * (g.n + 1) + 4 * g.m + (0 if w["sources"] == "all" else 4 * len(mine))
+    d2h = 8 * g.n
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # the plain one-source-per-launch path on a sample of the same sources
+        if w["schedule"] == "batch":
+            sample = mine[:min(len(mine), args.plain_sample)]
+            ctx.sources(G, sample[:4], out=out, schedule="plain", delta_fp64=fp64)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            ctx.sources(G, sample, out=out, schedule="plain", delta_fp64=fp64)
+            e.record(stream)
+            torch.cuda.synchronize()
+            pms = s.elapsed_time(e)
+            extra["plain"] = {"value": len(sample) * g.m / (pms / 1e3) / 1e9, "unit": "GTEPS",
+                              "sources": int(len(sample)),
+                              "note": "one source per launch, same graph and sources"}
+            # the other dependency precision on the same job
+            s.record(stream)
+            ctx.sources(G, mine, out=out, **dict(opts, delta_fp64=not fp64))
+            e.record(stream)
+            torch.cuda.synchronize()
+            oms = s.elapsed_time(e)
+            extra["fp64_delta" if not fp64 else "fp32_delta"] = {
+                "value": len(srcs) * g.m / (oms / 1e3) / 1e9, "unit": "GTEPS"}
+
+    cpu = None
+    if pool is not None:
+        cpu = cpu_oracle_run(pool, cores, g, srcs, args.cpu_seconds)
+        pool.close()
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "u64+f64" if fp64 else "u64+f32",
+            "data": "synthetic",
+            "config": dict(describe(name, w, g, len(srcs)),
+                           l2="flushed between timed steps (512 MiB write)",
+                           parallelism=f"source shards x{world}"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "kernel": f"{w['schedule']}_kernel",
+                         "algo_bytes_per_launch": algo_bytes / launches,
+                         "launch_ms": my_ms / launches},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(st["kernel_launches"]) * args.steps,
+            "clocks": clk,
+            "counters": {k: st[k] for k in ("frontier_entries", "scanned_in_edges",
+                                            "scanned_out_edges", "dag_pairs", "reached_pairs",
+                                            "heavy_chunks", "max_levels", "batches")},
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat16-exact", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64", action="store_true", help="FP64 dependencies")
+    ap.add_argument("--plain-sample", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the plain / precision extras")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w, args.workload)
+    else:
+        run_ours(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * bc_gb300.h -- C ABI of the GB300 (sm_103a) exact betweenness-centrality
+ * library.
+ *
+ * Method.  Betweenness centrality of a vertex v is the sum, over ordered
+ * pairs of distinct vertices s != v != t, of the fraction of shortest s->t
+ * paths that pass through v (paper, Section I).  Exact values come from
+ * Brandes' algorithm, which the paper names (Section I) and studies on the GPU
+ * (Section II.A): per source s, a level-synchronous BFS gives the depth d[]
+ * and the shortest-path counts sigma[]; a reverse-level sweep then gives the
+ * dependencies
+ *     delta[v] = sum over successors w (edge v->w, d[w] = d[v] + 1) of
+ *                sigma[v] / sigma[w] * (1 + delta[w]),
+ * and BC[v] accumulates delta[v] over all sources s != v.  Graphs are
+ * unweighted and directed (paper, Section II.C); BC values are raw sums with
+ * no normalisation unless an option asks for it.
+ *
+ * Conventions shared by every entry point.
+ *   - Return values are bc_status codes: 0 on success, BC_PENDING (1) for an
+ *     unfinished job, negative on error.  Nothing aborts the process and no
+ *     device code traps; a device-side failure is reported as a status.
+ *   - Input arrays are copied before the call returns; the caller keeps
+ *     ownership and may free them immediately.  Output buffers are always
+ *     owned by the caller.
+ *   - Output BC vectors are float64[n].  bc_opts.out_device selects whether
+ *     bc_out is host memory (0) or device memory on the context's GPU (1).
+ *   - Vertex ids are int32 in [0, n); edge counts are int64 but must stay
+ *     below 2^31.
+ *   - Depths and path counts are exact integers (int32 / uint64).  A source
+ *     whose path count reaches 2^64 makes the call return
+ *     BC_ERR_SIGMA_OVERFLOW; bc_out is still written but is not valid for the
+ *     flagged sources (bc_stats.overflow_sources counts them).
+ *   - A context is not thread-safe: calls on one context must not overlap,
+ *     except that bc_submit / bc_poll may be called while jobs run on the
+ *     context's internal scheduler thread.
+ */
+#ifndef BC_GB300_H
+#define BC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bc_ctx bc_ctx; /* opaque; one per GPU */
+typedef int64_t bc_graph;     /* graph handle, > 0 */
+typedef int64_t bc_job;       /* job handle, > 0 */
+
+typedef enum {
+  BC_OK = 0,
+  BC_PENDING = 1,             /* bc_poll: job not finished yet */
+  BC_ERR_ARG = -1,            /* bad argument (null pointer, source id out of range, bad option) */
+  BC_ERR_GRAPH = -2,          /* malformed CSR, or unknown graph handle */
+  BC_ERR_OOM = -3,            /* device or host allocation failed */
+  BC_ERR_CUDA = -4,           /* a CUDA runtime call failed */
+  BC_ERR_TIMEOUT = -5,        /* a bounded device-side wait ran out */
+  BC_ERR_SIGMA_OVERFLOW = -6, /* some shortest-path count reached 2^64 */
+  BC_ERR_NOT_FOUND = -7,      /* unknown or already consumed job handle */
+  BC_ERR_ADMISSION = -8,      /* job footprint exceeds the context's HBM budget */
+  BC_ERR_INTERNAL = -9        /* device-side capacity check failed (a bug) */
+} bc_status;
+
+/* Work schedules.  AUTO picks per graph. */
+enum {
+  BC_SCHED_AUTO = 0,
+  BC_SCHED_PLAIN = 1, /* one source per kernel launch, whole GPU, level-synchronous */
+  BC_SCHED_BATCH = 2  /* up to 64 sources per launch, bitset frontiers, [n][64] state */
+};
+
+typedef struct {
+  int32_t delta_fp64;    /* 0: dependencies in FP32 (fast path); 1: FP64 */
+  int32_t batch_k;       /* sources per batch for BC_SCHED_BATCH: 0 = 64, else 1..64 */
+  int32_t schedule;      /* BC_SCHED_* */
+  int32_t normalize;     /* 0: raw sums; 1: divide by (n-1)(n-2) when n > 2 */
+  int32_t scale_sampled; /* 0: raw sum over the given sources; 1: multiply by n/k */
+  int32_t out_device;    /* 0: bc_out is host memory; 1: device memory */
+} bc_opts;
+
+/* Per-call statistics.  Counters feed the bytes model of the roofline. */
+typedef struct {
+  int64_t n;                 /* vertices */
+  int64_t m;                 /* canonical edges */
+  int64_t sources;           /* sources processed */
+  int64_t batches;           /* kernel passes (one per batch, or per source for PLAIN) */
+  int64_t kernel_launches;   /* kernels launched by the call */
+  int32_t max_levels;        /* deepest BFS level count over all sources */
+  int32_t overflow_sources;  /* sources whose path count reached 2^64 */
+  double device_ms;          /* device time of the BC kernels (CUDA events) */
+  int64_t frontier_entries;  /* (vertex, level) pairs with a non-empty frontier mask */
+  int64_t scanned_out_edges; /* out-edges scanned, forward discovery plus backward */
+  int64_t scanned_in_edges;  /* in-edges scanned by the path-count pull */
+  int64_t dag_pairs;         /* sum over sources of shortest-path DAG edges */
+  int64_t reached_pairs;     /* sum over sources of reached vertices (incl. source) */
+  int64_t heavy_chunks;      /* edge chunks of high-degree vertices split across warps */
+} bc_stats;
+
+/* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * to order work on, or NULL for a stream the context creates and owns.
+ * hbm_budget_bytes caps the device memory the context may hold for job
+ * state (0 = 90% of the memory free at creation); graphs count against it.
+ * Errors: BC_ERR_ARG (null out), BC_ERR_CUDA (no such device). */
+bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx **out);
+
+/* Waits for outstanding jobs, frees every graph and buffer, destroys the
+ * context.  The handle is invalid afterwards. */
+bc_status bc_shutdown(bc_ctx *ctx);
+
+/* Uploads a directed graph given as host CSR: out-neighbours of v are
+ * col_idx[row_ptr[v] .. row_ptr[v+1]).  Rejected with BC_ERR_GRAPH when
+ * n < 0, row_ptr[0] != 0, row_ptr decreases, row_ptr[n] != m, m >= 2^31 or
+ * a column is outside [0, n).  The graph is canonicalised (rows sorted,
+ * duplicate edges and self-loops dropped; paper Section II.D stores graphs
+ * as adjacency lists, and a duplicate edge would double path counts); the
+ * resulting edge count is written to *m_effective (nullable).  Both arrays
+ * are copied; the graph stays resident in HBM until bc_destroy_graph. */
+bc_status bc_create_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx,
+                          int32_t n, int64_t m, bc_graph *out, int64_t *m_effective);
+
+/* Frees a graph.  Fails with BC_ERR_ARG while a submitted job still uses it. */
+bc_status bc_destroy_graph(bc_ctx *ctx, bc_graph g);
+
+/* Exact BC over all n sources (paper, Section I).  bc_out: float64[n].
+ * opts may be NULL (FP32 dependencies, automatic schedule, raw output to
+ * host memory).  Blocks until the result is written. */
+bc_status bc_exact(bc_ctx *ctx, bc_graph g, const bc_opts *opts, double *bc_out);
+
+/* BC summed over the k given sources (host int32[k], each in [0, n);
+ * a repeated source counts once per occurrence).  With scale_sampled the
+ * sum is multiplied by n/k, the usual estimator of exact BC from sampled
+ * sources (paper, Section I cites approximate BC by sampling).  Errors:
+ * BC_ERR_ARG for k < 0 or a source out of range. */
+bc_status bc_sources(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t k,
+                     const bc_opts *opts, double *bc_out);
+
+/* Queues a BC job (src == NULL: all sources; else k host sources, copied)
+ * for the context's scheduler thread and returns at once.  Jobs are admitted
+ * when their device footprint fits the HBM budget next to the jobs already
+ * running; jobs run concurrently on separate streams.  A job that could never
+ * fit is refused with BC_ERR_ADMISSION.  opts is copied (out_device must be
+ * 0: results are handed over by bc_poll). */
+bc_status bc_submit(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t k, const bc_opts *opts,
+                    bc_job *out);
+
+/* Non-blocking.  Returns BC_PENDING while the job runs; otherwise writes the
+ * job's float64[n] result to host bc_out, its statistics to stats
+ * (nullable), forgets the job and returns the job's final status.  A
+ * consumed or unknown handle gives BC_ERR_NOT_FOUND. */
+bc_status bc_poll(bc_ctx *ctx, bc_job job, double *bc_out, bc_stats *stats);
+
+/* Like bc_poll but waits up to timeout_ms (<0: no limit) for completion;
+ * BC_ERR_TIMEOUT when the limit passes first (the job keeps running). */
+bc_status bc_wait(bc_ctx *ctx, bc_job job, int64_t timeout_ms, double *bc_out, bc_stats *stats);
+
+/* Statistics of the last completed synchronous call (bc_exact / bc_sources /
+ * bc_exact_many / bc_debug_*) on this context. */
+bc_status bc_last_stats(bc_ctx *ctx, bc_stats *stats);
+
+/* Per-source vectors of one source through the PLAIN schedule: depth d
+ * (int32, -1 unreached), path count sigma (uint64, 0 unreached) and
+ * dependency delta (float64; delta[s] is the source's own dependency, which
+ * BC excludes).  Host arrays of n entries each; any may be NULL. */
+bc_status bc_debug_source(bc_ctx *ctx, bc_graph g, int32_t s, int32_t *d_out,
+                          uint64_t *sigma_out, double *delta_out);
+
+/* Same vectors for k sources through the schedule opts selects, laid out
+ * source-major: entry [j*n + v].  Host arrays; any may be NULL. */
+bc_status bc_debug_sources(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t k,
+                           const bc_opts *opts, int32_t *d_out, uint64_t *sigma_out,
+                           double *delta_out);
+
+/* Exact BC of `count` resident graphs in one persistent launch: each graph's
+ * sources run in batches of up to 64 inside thread blocks that loop over a
+ * queue of (graph, batch) items.  bc_out receives the graphs' vectors back to
+ * back (graph i at offset sum_{j<i} n_j).  Intended for many small graphs
+ * (n <= 65536 each); larger graphs return BC_ERR_ARG. */
+bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, const bc_opts *opts,
+                        double *bc_out);
+
+/* Test hook for failure detection: with block >= 0 the next BATCH launch on
+ * this context has that thread block skip its first grid-barrier arrival
+ * and the others give up after timeout_ms, so the call returns
+ * BC_ERR_TIMEOUT and the context stays usable.  block < 0 disables it. */
+bc_status bc_debug_inject_barrier_skip(bc_ctx *ctx, int32_t block, int32_t timeout_ms);
+
+/* Static description of a status code. */
+const char *bc_status_str(bc_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BC_GB300_H */

@@ -1,0 +1,1020 @@
+// Host side of the GB300 betweenness-centrality library: the C ABI declared
+// in include/bc_gb300.h.
+//
+//  - graph registry: validation, canonicalisation (sorted rows, no duplicate
+//    edges or self-loops), in-CSR construction and chunk counts, one device
+//    allocation per graph, resident until destroyed;
+//  - workspaces: device state of one in-flight batch, cached and reused; the
+//    kernels leave a workspace zeroed, so reuse needs no clearing;
+//  - jobs: a source list split into batches of up to 64 (BATCH schedule) or
+//    single sources (PLAIN), one cooperative launch each, stream-ordered,
+//    followed by one scaling pass and one copy of the float64 result;
+//  - scheduler: a host thread that admits submitted jobs when their device
+//    footprint fits the HBM budget next to running jobs, launches each on a
+//    stream of its own so their kernels overlap, and retires them by event.
+#include "bc_internal.cuh"
+#include "bc_gb300.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+using namespace bcgpu;
+
+namespace {
+
+constexpr int kMaxSlots = 8; // concurrently running submitted jobs
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves typed arrays out of one device allocation.
+struct Carver {
+  size_t off = 0;
+  char *base = nullptr;
+  template <typename T> T *take(size_t count) {
+    off = align_up(off, 256);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+  }
+  ~DeviceGuard() {
+    if (prev_ != dev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = 0, dev_ = 0;
+};
+
+struct GraphRec {
+  int64_t handle = 0;
+  GraphDev dev;
+  void *mem = nullptr;
+  size_t bytes = 0;
+  int active_jobs = 0;
+};
+
+struct WsRec {
+  bool batch = true;
+  int32_t n = 0;
+  int64_t cap = 0, hcap = 0, chunk_cap = 0;
+  Work w;
+  void *mem = nullptr;
+  size_t bytes = 0;
+  bool dirty = false;
+};
+
+struct WsNeed {
+  bool batch;
+  int32_t n;
+  int64_t cap, hcap, chunk_cap;
+  bool fits(const WsRec &r) const {
+    return r.batch == batch && r.n >= n && r.cap >= cap && r.hcap >= hcap &&
+           r.chunk_cap >= chunk_cap;
+  }
+};
+
+WsNeed ws_need(const GraphDev &g, bool batch, int kb) {
+  WsNeed nd;
+  nd.batch = batch;
+  nd.n = g.n;
+  const int64_t kk = batch ? kb : 1;
+  nd.cap = std::max<int64_t>(1, (int64_t)g.n * kk);
+  nd.hcap = std::max<int64_t>(1, g.heavy_vertices * kk);
+  nd.chunk_cap = std::max<int64_t>(1, g.heavy_chunks);
+  return nd;
+}
+
+// Lays out (mem == nullptr: only sizes) the arrays of a workspace.
+size_t ws_layout(WsRec &r, char *mem) {
+  Carver c;
+  c.base = mem;
+  const size_t n = (size_t)r.n;
+  const size_t kk = r.batch ? kK : 1;
+  Work &w = r.w;
+  w.n = r.n;
+  w.k_max = (int32_t)kk;
+  w.ctl = c.take<Ctl>(1);
+  if (r.batch) {
+    w.vis = c.take<uint64_t>(n);
+    w.fr = c.take<uint64_t>(4 * n);
+    w.qm = c.take<uint64_t>((size_t)r.cap);
+    w.d = nullptr;
+  } else {
+    w.d = c.take<int32_t>(n);
+    w.vis = nullptr;
+    w.fr = nullptr;
+    w.qm = nullptr;
+  }
+  w.qv = c.take<int32_t>((size_t)r.cap);
+  w.cap = r.cap;
+  w.qoff = c.take<int64_t>(n + 3);
+  w.hpack = c.take<unsigned long long>(n + 3);
+  w.hoff = c.take<int64_t>(n + 3);
+  w.hq_e = c.take<int64_t>((size_t)r.hcap);
+  w.hq_c = c.take<int64_t>((size_t)r.hcap);
+  w.harrive = c.take<unsigned>((size_t)r.hcap);
+  w.hcap = r.hcap;
+  w.partial = c.take<uint64_t>((size_t)r.chunk_cap * kk);
+  w.partial_ovf = c.take<uint64_t>((size_t)r.chunk_cap);
+  w.chunk_cap = r.chunk_cap;
+  w.sigma = c.take<uint64_t>(n * kk);
+  w.cdep = c.take<double>(n * kk);
+  return align_up(c.off, 256);
+}
+
+// Brings a workspace to its resting state: all masks, counts and arrival
+// counters zero, depths -1.
+cudaError_t ws_clear(WsRec &r, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(r.mem, 0, r.bytes, st);
+  if (e == cudaSuccess && !r.batch) e = cudaMemsetAsync(r.w.d, 0xff, sizeof(int32_t) * r.n, st);
+  return e;
+}
+
+struct JobRec;
+
+} // namespace
+
+struct bc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};
+  int sm_count = 0;
+  int grid_batch[2] = {0, 0}; // [fp64]
+  int grid_plain[2] = {0, 0};
+
+  std::mutex mu;
+  std::unordered_map<int64_t, std::unique_ptr<GraphRec>> graphs;
+  int64_t next_graph = 1;
+  std::vector<std::unique_ptr<WsRec>> free_ws;
+
+  bc_stats last{};
+  int32_t inject_block = -1;
+  int32_t inject_timeout_ms = 0;
+
+  // scheduler
+  std::thread sched;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<JobRec *> pending;
+  std::vector<JobRec *> running;
+  std::map<int64_t, std::unique_ptr<JobRec>> jobs;
+  int64_t next_job = 1;
+  cudaStream_t slot_stream[kMaxSlots] = {};
+  bool slot_busy[kMaxSlots] = {};
+};
+
+namespace {
+
+// One BC job: a graph, a source list and options; runs on one stream.
+struct JobRec {
+  int64_t handle = 0;
+  GraphRec *g = nullptr;
+  std::vector<int32_t> src; // empty + all_sources: 0..n-1
+  bool all_sources = false;
+  bc_opts opts{};
+  int64_t k = 0;            // number of sources
+  // run state
+  int slot = -1;
+  cudaStream_t st = nullptr;
+  std::unique_ptr<WsRec> ws;
+  int32_t *d_src = nullptr;
+  double *d_bc = nullptr;
+  int8_t *d_ovf = nullptr;
+  unsigned long long *d_cnt = nullptr;
+  int32_t *h_src = nullptr;   // pinned staging
+  double *h_out = nullptr;    // pinned result (async jobs)
+  unsigned long long *h_cnt = nullptr; // pinned: counters + err + ovf count
+  int *h_err = nullptr;
+  int8_t *h_ovf = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evdone = nullptr;
+  int64_t launches = 0;
+  int64_t batches = 0;
+  size_t footprint = 0;
+  bc_status status = BC_PENDING;
+  bc_stats stats{};
+  bool done = false;
+};
+
+bc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BC_OK;
+  if (e == cudaErrorMemoryAllocation) return BC_ERR_OOM;
+  return BC_ERR_CUDA;
+}
+
+#define BC_TRY(expr)                                \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return cuda_status(_e);  \
+  } while (0)
+
+bc_opts default_opts() {
+  bc_opts o;
+  std::memset(&o, 0, sizeof(o));
+  return o;
+}
+
+bool opts_valid(const bc_opts &o) {
+  return (o.delta_fp64 == 0 || o.delta_fp64 == 1) && o.batch_k >= 0 && o.batch_k <= kK &&
+         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH &&
+         (o.normalize == 0 || o.normalize == 1) &&
+         (o.scale_sampled == 0 || o.scale_sampled == 1) &&
+         (o.out_device == 0 || o.out_device == 1);
+}
+
+int resolve_schedule(const bc_opts &o, const GraphDev &) {
+  if (o.schedule != BC_SCHED_AUTO) return o.schedule;
+  return BC_SCHED_BATCH;
+}
+
+int resolve_batch_k(const bc_opts &o) { return o.batch_k == 0 ? kK : o.batch_k; }
+
+// Grid of a persistent launch: the co-resident maximum for large graphs, a
+// smaller share of the GPU for small ones so that concurrent jobs overlap.
+int pick_grid(const bc_ctx *ctx, const GraphDev &g, bool batch, bool fp64) {
+  const int gmax = batch ? ctx->grid_batch[fp64] : ctx->grid_plain[fp64];
+  if (const char *env = std::getenv("BC_GRID")) {
+    int v = std::atoi(env);
+    if (v > 0) return std::min(v, gmax);
+  }
+  const int64_t want = std::max<int64_t>(2, ((int64_t)g.n + 127) / 128);
+  return (int)std::min<int64_t>(gmax, want);
+}
+
+// ---- graphs -----------------------------------------------------------------
+
+bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                      int64_t m, std::unique_ptr<GraphRec> &out, int64_t *m_eff) {
+  if (n < 0 || m < 0 || m >= ((int64_t)1 << 31)) return BC_ERR_GRAPH;
+  if (!row_ptr || (m > 0 && !col_idx)) return BC_ERR_ARG;
+  if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != m) return BC_ERR_GRAPH;
+  for (int32_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return BC_ERR_GRAPH;
+  for (int64_t e = 0; e < m; ++e)
+    if (col_idx[e] < 0 || col_idx[e] >= n) return BC_ERR_GRAPH;
+
+  // canonical out-CSR: rows sorted, unique, no self-loop
+  std::vector<int32_t> rp((size_t)n + 1), ci;
+  bool canonical = true;
+  for (int32_t v = 0; v < n && canonical; ++v)
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+      if (col_idx[e] == v || (e > row_ptr[v] && col_idx[e] <= col_idx[e - 1])) {
+        canonical = false;
+        break;
+      }
+  if (canonical) {
+    std::memcpy(rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+    ci.assign(col_idx, col_idx + m);
+  } else {
+    ci.reserve((size_t)m);
+    rp[0] = 0;
+    std::vector<int32_t> row;
+    for (int32_t v = 0; v < n; ++v) {
+      row.assign(col_idx + row_ptr[v], col_idx + row_ptr[v + 1]);
+      std::sort(row.begin(), row.end());
+      int32_t prev = -1;
+      for (int32_t x : row)
+        if (x != v && x != prev) {
+          ci.push_back(x);
+          prev = x;
+        }
+      rp[(size_t)v + 1] = (int32_t)ci.size();
+    }
+  }
+  const int64_t me = (int64_t)ci.size();
+  // in-CSR by counting sort over destinations (sources stay ascending)
+  std::vector<int32_t> ip((size_t)n + 1, 0), ii((size_t)std::max<int64_t>(me, 1));
+  for (int64_t e = 0; e < me; ++e) ip[(size_t)ci[e] + 1]++;
+  for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
+  {
+    std::vector<int32_t> fill(ip.begin(), ip.end() - 1);
+    for (int32_t v = 0; v < n; ++v)
+      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) ii[(size_t)fill[ci[e]]++] = v;
+  }
+  std::vector<int32_t> nch((size_t)std::max<int32_t>(n, 1), 0);
+  int64_t hv = 0, hc = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (ip[(size_t)v + 1] - ip[v]);
+    if (cost > kChunk) {
+      nch[v] = (int32_t)((cost + kChunk - 1) / kChunk);
+      ++hv;
+      hc += nch[v];
+    }
+  }
+
+  auto g = std::make_unique<GraphRec>();
+  Carver c;
+  int32_t *d_rp = c.take<int32_t>((size_t)n + 1);
+  int32_t *d_ci = c.take<int32_t>((size_t)me);
+  int32_t *d_ip = c.take<int32_t>((size_t)n + 1);
+  int32_t *d_ii = c.take<int32_t>((size_t)me);
+  int32_t *d_nc = c.take<int32_t>((size_t)n);
+  (void)d_rp; (void)d_ci; (void)d_ip; (void)d_ii; (void)d_nc;
+  const size_t bytes = align_up(c.off, 256);
+  if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
+  void *mem = nullptr;
+  BC_TRY(cudaMalloc(&mem, bytes));
+  Carver c2;
+  c2.base = static_cast<char *>(mem);
+  d_rp = c2.take<int32_t>((size_t)n + 1);
+  d_ci = c2.take<int32_t>((size_t)me);
+  d_ip = c2.take<int32_t>((size_t)n + 1);
+  d_ii = c2.take<int32_t>((size_t)me);
+  d_nc = c2.take<int32_t>((size_t)n);
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && me) e = cudaMemcpyAsync(d_ci, ci.data(), sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && me) e = cudaMemcpyAsync(d_ii, ii.data(), sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_nc, nch.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return cuda_status(e);
+  }
+  g->mem = mem;
+  g->bytes = bytes;
+  g->dev.n = n;
+  g->dev.m = me;
+  g->dev.row_ptr = d_rp;
+  g->dev.col_idx = d_ci;
+  g->dev.in_ptr = d_ip;
+  g->dev.in_idx = d_ii;
+  g->dev.nchunks = d_nc;
+  g->dev.heavy_vertices = hv;
+  g->dev.heavy_chunks = hc;
+  ctx->used += bytes;
+  if (m_eff) *m_eff = me;
+  out = std::move(g);
+  return BC_OK;
+}
+
+GraphRec *find_graph(bc_ctx *ctx, bc_graph h) {
+  auto it = ctx->graphs.find(h);
+  return it == ctx->graphs.end() ? nullptr : it->second.get();
+}
+
+// ---- workspaces -------------------------------------------------------------
+
+bc_status ws_acquire(bc_ctx *ctx, const WsNeed &nd, cudaStream_t st, std::unique_ptr<WsRec> &out) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (size_t i = 0; i < ctx->free_ws.size(); ++i)
+      if (nd.fits(*ctx->free_ws[i])) {
+        out = std::move(ctx->free_ws[i]);
+        ctx->free_ws.erase(ctx->free_ws.begin() + (ptrdiff_t)i);
+        break;
+      }
+  }
+  if (out) {
+    if (out->dirty) {
+      BC_TRY(ws_clear(*out, st));
+      out->dirty = false;
+    }
+    return BC_OK;
+  }
+  auto r = std::make_unique<WsRec>();
+  r->batch = nd.batch;
+  r->n = nd.n;
+  r->cap = nd.cap;
+  r->hcap = nd.hcap;
+  r->chunk_cap = nd.chunk_cap;
+  r->bytes = ws_layout(*r, nullptr);
+  // make room: drop cached workspaces until the new one fits the budget
+  while (ctx->used + r->bytes > ctx->budget) {
+    std::unique_ptr<WsRec> victim;
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      if (ctx->free_ws.empty()) break;
+      victim = std::move(ctx->free_ws.back());
+      ctx->free_ws.pop_back();
+    }
+    cudaFree(victim->mem);
+    ctx->used -= victim->bytes;
+  }
+  if (ctx->used + r->bytes > ctx->budget) return BC_ERR_ADMISSION;
+  void *mem = nullptr;
+  BC_TRY(cudaMalloc(&mem, r->bytes));
+  r->mem = mem;
+  ws_layout(*r, static_cast<char *>(mem));
+  ctx->used += r->bytes;
+  cudaError_t e = ws_clear(*r, st);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    ctx->used -= r->bytes;
+    return cuda_status(e);
+  }
+  out = std::move(r);
+  return BC_OK;
+}
+
+void ws_release(bc_ctx *ctx, std::unique_ptr<WsRec> ws) {
+  if (!ws) return;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->free_ws.push_back(std::move(ws));
+}
+
+// ---- jobs -------------------------------------------------------------------
+
+size_t job_footprint(const GraphDev &g, int sched, int kb, int64_t k) {
+  WsRec r;
+  WsNeed nd = ws_need(g, sched == BC_SCHED_BATCH, kb);
+  r.batch = nd.batch;
+  r.n = nd.n;
+  r.cap = nd.cap;
+  r.hcap = nd.hcap;
+  r.chunk_cap = nd.chunk_cap;
+  return ws_layout(r, nullptr) + sizeof(double) * (size_t)g.n + (size_t)k * 5 + 4096;
+}
+
+void job_free_buffers(JobRec *j) {
+  if (j->d_src) cudaFreeAsync(j->d_src, j->st);
+  if (j->d_bc) cudaFreeAsync(j->d_bc, j->st);
+  if (j->d_ovf) cudaFreeAsync(j->d_ovf, j->st);
+  if (j->d_cnt) cudaFreeAsync(j->d_cnt, j->st);
+  j->d_src = nullptr;
+  j->d_bc = nullptr;
+  j->d_ovf = nullptr;
+  j->d_cnt = nullptr;
+  if (j->h_src) cudaFreeHost(j->h_src);
+  if (j->h_cnt) cudaFreeHost(j->h_cnt);
+  if (j->h_ovf) cudaFreeHost(j->h_ovf);
+  j->h_src = nullptr;
+  j->h_cnt = nullptr;
+  j->h_ovf = nullptr;
+  j->h_err = nullptr;
+  if (j->ev0) cudaEventDestroy(j->ev0);
+  if (j->ev1) cudaEventDestroy(j->ev1);
+  if (j->evdone) cudaEventDestroy(j->evdone);
+  j->ev0 = j->ev1 = j->evdone = nullptr;
+}
+
+struct DebugOut {
+  int32_t *d = nullptr; // device [k][n]
+  uint64_t *sigma = nullptr;
+  double *delta = nullptr;
+};
+
+// Enqueues a whole job on j->st: inputs, one launch per batch, scaling, copy
+// of the result to `out` (device or host pointer per opts.out_device; an
+// async job passes its pinned buffer) and of the job counters.
+bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
+  const GraphDev &g = j->g->dev;
+  const int sched = resolve_schedule(j->opts, g);
+  const bool batch = sched == BC_SCHED_BATCH;
+  const bool fp64 = j->opts.delta_fp64 != 0;
+  const int kb = batch ? resolve_batch_k(j->opts) : 1;
+  const int64_t n = g.n, k = j->k;
+  cudaStream_t st = j->st;
+
+  bc_status s = ws_acquire(ctx, ws_need(g, batch, kb), st, j->ws);
+  if (s != BC_OK) return s;
+  BC_TRY(cudaMallocHost(&j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
+  BC_TRY(cudaMallocHost(&j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
+  BC_TRY(cudaMallocHost(&j->h_ovf, (size_t)std::max<int64_t>(k, 1)));
+  j->h_err = reinterpret_cast<int *>(j->h_cnt + CNT_N);
+  if (j->all_sources)
+    for (int64_t i = 0; i < k; ++i) j->h_src[i] = (int32_t)i;
+  else if (k)
+    std::memcpy(j->h_src, j->src.data(), sizeof(int32_t) * (size_t)k);
+  BC_TRY(cudaMallocAsync(&j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));
+  BC_TRY(cudaMallocAsync(&j->d_bc, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
+  BC_TRY(cudaMallocAsync(&j->d_ovf, (size_t)std::max<int64_t>(k, 1), st));
+  BC_TRY(cudaMallocAsync(&j->d_cnt, sizeof(unsigned long long) * CNT_N, st));
+  if (k) BC_TRY(cudaMemcpyAsync(j->d_src, j->h_src, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
+  BC_TRY(cudaMemsetAsync(j->d_bc, 0, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
+  BC_TRY(cudaMemsetAsync(j->d_ovf, 0, (size_t)std::max<int64_t>(k, 1), st));
+  BC_TRY(cudaMemsetAsync(j->d_cnt, 0, sizeof(unsigned long long) * CNT_N, st));
+  BC_TRY(cudaMemsetAsync(j->ws->w.ctl, 0, sizeof(Ctl), st));
+  BC_TRY(cudaEventCreate(&j->ev0));
+  BC_TRY(cudaEventCreate(&j->ev1));
+  BC_TRY(cudaEventCreateWithFlags(&j->evdone, cudaEventDisableTiming));
+
+  KParams p;
+  p.g = g;
+  p.w = j->ws->w;
+  p.bc = j->d_bc;
+  p.ovf_flags = j->d_ovf;
+  p.job_cnt = j->d_cnt;
+  if (ctx->inject_block >= 0 && batch) {
+    p.skip_block = ctx->inject_block;
+    p.timeout_ns = (long long)ctx->inject_timeout_ms * 1000000LL;
+    ctx->inject_block = -1;
+  }
+  const int grid = pick_grid(ctx, g, batch, fp64);
+  if (grid <= 0) return BC_ERR_CUDA;
+  BC_TRY(cudaEventRecord(j->ev0, st));
+  j->batches = 0;
+  j->launches = 0;
+  for (int64_t b0 = 0; b0 < k; b0 += kb) {
+    p.src = j->d_src + b0;
+    p.k = (int32_t)std::min<int64_t>(kb, k - b0);
+    p.src_base = b0;
+    if (dbg) {
+      p.dbg_d = dbg->d + b0 * n;
+      p.dbg_sigma = dbg->sigma + b0 * n;
+      p.dbg_delta = dbg->delta + b0 * n;
+    }
+    BC_TRY(batch ? launch_batch(p, fp64, grid, st) : launch_plain(p, fp64, grid, st));
+    ++j->batches;
+    ++j->launches;
+  }
+  BC_TRY(cudaEventRecord(j->ev1, st));
+  double factor = 1.0;
+  if (j->opts.normalize && n > 2) factor /= (double)(n - 1) * (double)(n - 2);
+  if (j->opts.scale_sampled && k > 0) factor *= (double)n / (double)k;
+  if (out && n > 0) {
+    if (j->opts.out_device) {
+      BC_TRY(launch_scale(j->d_bc, out, n, factor, st));
+    } else {
+      BC_TRY(launch_scale(j->d_bc, j->d_bc, n, factor, st));
+      BC_TRY(cudaMemcpyAsync(out, j->d_bc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    }
+    ++j->launches;
+  }
+  BC_TRY(cudaMemcpyAsync(j->h_cnt, j->d_cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+  BC_TRY(cudaMemcpyAsync(j->h_err, &j->ws->w.ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (k) BC_TRY(cudaMemcpyAsync(j->h_ovf, j->d_ovf, (size_t)k, cudaMemcpyDeviceToHost, st));
+  BC_TRY(cudaEventRecord(j->evdone, st));
+  return BC_OK;
+}
+
+// After evdone completed: statistics, status, workspace hand-back.
+bc_status job_finish(bc_ctx *ctx, JobRec *j) {
+  bc_stats &s = j->stats;
+  std::memset(&s, 0, sizeof(s));
+  s.n = j->g->dev.n;
+  s.m = j->g->dev.m;
+  s.sources = j->k;
+  s.batches = j->batches;
+  s.kernel_launches = j->launches;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, j->ev0, j->ev1) == cudaSuccess) s.device_ms = ms;
+  s.frontier_entries = (int64_t)j->h_cnt[CNT_ENTRIES];
+  s.scanned_out_edges = (int64_t)j->h_cnt[CNT_OUT_EDGES];
+  s.scanned_in_edges = (int64_t)j->h_cnt[CNT_IN_EDGES];
+  s.dag_pairs = (int64_t)j->h_cnt[CNT_DAG];
+  s.reached_pairs = (int64_t)j->h_cnt[CNT_REACHED];
+  s.heavy_chunks = (int64_t)j->h_cnt[CNT_HEAVY];
+  s.max_levels = (int32_t)j->h_cnt[CNT_MAXLEV];
+  int32_t novf = 0;
+  for (int64_t i = 0; i < j->k; ++i) novf += j->h_ovf[i] ? 1 : 0;
+  s.overflow_sources = novf;
+  bc_status st = BC_OK;
+  const int kerr = *j->h_err;
+  if (kerr != KERR_NONE) {
+    st = kerr == KERR_TIMEOUT ? BC_ERR_TIMEOUT : BC_ERR_INTERNAL;
+    j->ws->dirty = true;
+  } else if (novf) {
+    st = BC_ERR_SIGMA_OVERFLOW;
+  }
+  ws_release(ctx, std::move(j->ws));
+  job_free_buffers(j);
+  return st;
+}
+
+bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool all,
+                   const bc_opts *opts_in, double *out, const DebugOut *dbg) {
+  bc_opts opts = opts_in ? *opts_in : default_opts();
+  if (!opts_valid(opts)) return BC_ERR_ARG;
+  JobRec j;
+  j.g = g;
+  j.opts = opts;
+  j.k = k;
+  j.all_sources = all;
+  if (!all && k) j.src.assign(src, src + k);
+  j.st = ctx->stream;
+  bc_status s = job_launch(ctx, &j, out, dbg);
+  if (s != BC_OK) {
+    cudaStreamSynchronize(j.st);
+    if (j.ws) {
+      j.ws->dirty = true;
+      ws_release(ctx, std::move(j.ws));
+    }
+    job_free_buffers(&j);
+    return s;
+  }
+  cudaError_t e = cudaEventSynchronize(j.evdone);
+  if (e != cudaSuccess) {
+    job_free_buffers(&j);
+    return cuda_status(e);
+  }
+  s = job_finish(ctx, &j);
+  ctx->last = j.stats;
+  return s;
+}
+
+bc_status check_sources(const GraphRec *g, const int32_t *src, int64_t k) {
+  if (k < 0) return BC_ERR_ARG;
+  if (k > 0 && !src) return BC_ERR_ARG;
+  for (int64_t i = 0; i < k; ++i)
+    if (src[i] < 0 || src[i] >= g->dev.n) return BC_ERR_ARG;
+  return BC_OK;
+}
+
+// ---- scheduler ----------------------------------------------------------------
+
+void scheduler_loop(bc_ctx *ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  while (true) {
+    if (ctx->stop && ctx->pending.empty() && ctx->running.empty()) break;
+    bool progressed = false;
+    // admit pending jobs in arrival order while a slot and memory are free
+    while (!ctx->pending.empty()) {
+      JobRec *j = ctx->pending.front();
+      int slot = -1;
+      for (int i = 0; i < kMaxSlots; ++i)
+        if (!ctx->slot_busy[i]) {
+          slot = i;
+          break;
+        }
+      if (slot < 0) break;
+      if (ctx->used + j->footprint > ctx->budget && !ctx->running.empty()) break;
+      ctx->pending.pop_front();
+      ctx->slot_busy[slot] = true;
+      j->slot = slot;
+      j->st = ctx->slot_stream[slot];
+      lk.unlock();
+      bc_status s = job_launch(ctx, j, j->h_out, nullptr);
+      lk.lock();
+      if (s != BC_OK) {
+        lk.unlock();
+        cudaStreamSynchronize(j->st);
+        if (j->ws) {
+          j->ws->dirty = true;
+          ws_release(ctx, std::move(j->ws));
+        }
+        job_free_buffers(j);
+        lk.lock();
+        j->status = s;
+        j->done = true;
+        j->g->active_jobs--;
+        ctx->slot_busy[slot] = false;
+      } else {
+        ctx->running.push_back(j);
+      }
+      progressed = true;
+    }
+    // retire finished jobs
+    for (size_t i = 0; i < ctx->running.size();) {
+      JobRec *j = ctx->running[i];
+      if (cudaEventQuery(j->evdone) == cudaSuccess) {
+        lk.unlock();
+        bc_status s = job_finish(ctx, j);
+        lk.lock();
+        j->status = s;
+        j->done = true;
+        j->g->active_jobs--;
+        ctx->slot_busy[j->slot] = false;
+        ctx->running.erase(ctx->running.begin() + (ptrdiff_t)i);
+        progressed = true;
+      } else {
+        ++i;
+      }
+    }
+    if (progressed) ctx->cv.notify_all();
+    if (ctx->pending.empty() && ctx->running.empty()) {
+      if (ctx->stop) break;
+      ctx->cv.wait(lk);
+    } else if (!progressed) {
+      ctx->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+  }
+}
+
+} // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+const char *bc_status_str(bc_status s) {
+  switch (s) {
+    case BC_OK: return "ok";
+    case BC_PENDING: return "pending";
+    case BC_ERR_ARG: return "invalid argument";
+    case BC_ERR_GRAPH: return "malformed graph or unknown graph handle";
+    case BC_ERR_OOM: return "out of memory";
+    case BC_ERR_CUDA: return "CUDA runtime error";
+    case BC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case BC_ERR_SIGMA_OVERFLOW: return "shortest-path count reached 2^64";
+    case BC_ERR_NOT_FOUND: return "unknown or consumed job handle";
+    case BC_ERR_ADMISSION: return "job does not fit the HBM budget";
+    case BC_ERR_INTERNAL: return "device capacity check failed";
+  }
+  return "unknown status";
+}
+
+bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx **out) {
+  if (!out) return BC_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return BC_ERR_CUDA;
+  DeviceGuard dg(device);
+  std::unique_ptr<bc_ctx> ctx(new (std::nothrow) bc_ctx());
+  if (!ctx) return BC_ERR_OOM;
+  ctx->device = device;
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    BC_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  size_t freeb = 0, totalb = 0;
+  BC_TRY(cudaMemGetInfo(&freeb, &totalb));
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)freeb);
+  BC_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+  for (int f = 0; f < 2; ++f) {
+    ctx->grid_batch[f] = max_grid_batch(f != 0, device);
+    ctx->grid_plain[f] = max_grid_plain(f != 0, device);
+    if (ctx->grid_batch[f] <= 0 || ctx->grid_plain[f] <= 0) return BC_ERR_CUDA;
+  }
+  for (int i = 0; i < kMaxSlots; ++i)
+    BC_TRY(cudaStreamCreateWithFlags(&ctx->slot_stream[i], cudaStreamNonBlocking));
+  bc_ctx *raw = ctx.get();
+  ctx->sched = std::thread(scheduler_loop, raw);
+  *out = ctx.release();
+  return BC_OK;
+}
+
+bc_status bc_shutdown(bc_ctx *ctx) {
+  if (!ctx) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stop = true;
+  }
+  ctx->cv.notify_all();
+  if (ctx->sched.joinable()) ctx->sched.join();
+  cudaDeviceSynchronize();
+  for (auto &kv : ctx->jobs) {
+    if (kv.second->h_out) cudaFreeHost(kv.second->h_out);
+  }
+  ctx->jobs.clear();
+  for (auto &w : ctx->free_ws) cudaFree(w->mem);
+  ctx->free_ws.clear();
+  for (auto &kv : ctx->graphs) cudaFree(kv.second->mem);
+  ctx->graphs.clear();
+  for (int i = 0; i < kMaxSlots; ++i)
+    if (ctx->slot_stream[i]) cudaStreamDestroy(ctx->slot_stream[i]);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return BC_OK;
+}
+
+bc_status bc_create_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx,
+                          int32_t n, int64_t m, bc_graph *out, int64_t *m_effective) {
+  if (!ctx || !out) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  std::unique_ptr<GraphRec> g;
+  bc_status s = build_graph(ctx, row_ptr, col_idx, n, m, g, m_effective);
+  if (s != BC_OK) return s;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  g->handle = ctx->next_graph++;
+  *out = g->handle;
+  ctx->graphs.emplace(g->handle, std::move(g));
+  return BC_OK;
+}
+
+bc_status bc_destroy_graph(bc_ctx *ctx, bc_graph h) {
+  if (!ctx) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  std::unique_ptr<GraphRec> g;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->graphs.find(h);
+    if (it == ctx->graphs.end()) return BC_ERR_GRAPH;
+    if (it->second->active_jobs > 0) return BC_ERR_ARG;
+    g = std::move(it->second);
+    ctx->graphs.erase(it);
+  }
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(g->mem);
+  ctx->used -= g->bytes;
+  return BC_OK;
+}
+
+bc_status bc_exact(bc_ctx *ctx, bc_graph h, const bc_opts *opts, double *bc_out) {
+  if (!ctx || !bc_out) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  GraphRec *g;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    g = find_graph(ctx, h);
+  }
+  if (!g) return BC_ERR_GRAPH;
+  return run_sync(ctx, g, nullptr, g->dev.n, true, opts, bc_out, nullptr);
+}
+
+bc_status bc_sources(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, const bc_opts *opts,
+                     double *bc_out) {
+  if (!ctx || !bc_out) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  GraphRec *g;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    g = find_graph(ctx, h);
+  }
+  if (!g) return BC_ERR_GRAPH;
+  bc_status s = check_sources(g, src, k);
+  if (s != BC_OK) return s;
+  return run_sync(ctx, g, src, k, false, opts, bc_out, nullptr);
+}
+
+bc_status bc_submit(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, const bc_opts *opts,
+                    bc_job *out) {
+  if (!ctx || !out) return BC_ERR_ARG;
+  bc_opts o = opts ? *opts : default_opts();
+  if (!opts_valid(o) || o.out_device) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  auto j = std::make_unique<JobRec>();
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    GraphRec *g = find_graph(ctx, h);
+    if (!g) return BC_ERR_GRAPH;
+    j->g = g;
+  }
+  if (src) {
+    bc_status s = check_sources(j->g, src, k);
+    if (s != BC_OK) return s;
+    j->src.assign(src, src + k);
+    j->k = k;
+  } else {
+    j->all_sources = true;
+    j->k = j->g->dev.n;
+  }
+  j->opts = o;
+  const int sched = resolve_schedule(o, j->g->dev);
+  j->footprint = job_footprint(j->g->dev, sched, resolve_batch_k(o), j->k);
+  if (j->footprint > ctx->budget) return BC_ERR_ADMISSION;
+  if (cudaMallocHost(&j->h_out, sizeof(double) * (size_t)std::max<int32_t>(j->g->dev.n, 1)) !=
+      cudaSuccess)
+    return BC_ERR_OOM;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->stop) {
+    cudaFreeHost(j->h_out);
+    return BC_ERR_ARG;
+  }
+  j->handle = ctx->next_job++;
+  *out = j->handle;
+  j->g->active_jobs++;
+  ctx->pending.push_back(j.get());
+  ctx->jobs.emplace(j->handle, std::move(j));
+  ctx->cv.notify_all();
+  return BC_OK;
+}
+
+static bc_status take_result(bc_ctx *ctx, std::map<int64_t, std::unique_ptr<JobRec>>::iterator it,
+                             double *bc_out, bc_stats *stats) {
+  JobRec *j = it->second.get();
+  if (bc_out && j->g) std::memcpy(bc_out, j->h_out, sizeof(double) * (size_t)j->g->dev.n);
+  if (stats) *stats = j->stats;
+  bc_status s = j->status;
+  cudaFreeHost(j->h_out);
+  ctx->jobs.erase(it);
+  return s;
+}
+
+bc_status bc_poll(bc_ctx *ctx, bc_job job, double *bc_out, bc_stats *stats) {
+  if (!ctx) return BC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->jobs.find(job);
+  if (it == ctx->jobs.end()) return BC_ERR_NOT_FOUND;
+  if (!it->second->done) return BC_PENDING;
+  return take_result(ctx, it, bc_out, stats);
+}
+
+bc_status bc_wait(bc_ctx *ctx, bc_job job, int64_t timeout_ms, double *bc_out, bc_stats *stats) {
+  if (!ctx) return BC_ERR_ARG;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto it = ctx->jobs.find(job);
+  if (it == ctx->jobs.end()) return BC_ERR_NOT_FOUND;
+  JobRec *j = it->second.get();
+  auto ready = [&] { return j->done; };
+  if (timeout_ms < 0) {
+    ctx->cv.wait(lk, ready);
+  } else if (!ctx->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+    return BC_ERR_TIMEOUT;
+  }
+  return take_result(ctx, ctx->jobs.find(job), bc_out, stats);
+}
+
+bc_status bc_last_stats(bc_ctx *ctx, bc_stats *stats) {
+  if (!ctx || !stats) return BC_ERR_ARG;
+  *stats = ctx->last;
+  return BC_OK;
+}
+
+bc_status bc_debug_sources(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k,
+                           const bc_opts *opts, int32_t *d_out, uint64_t *sigma_out,
+                           double *delta_out) {
+  if (!ctx) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  GraphRec *g;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    g = find_graph(ctx, h);
+  }
+  if (!g) return BC_ERR_GRAPH;
+  bc_status s = check_sources(g, src, k);
+  if (s != BC_OK) return s;
+  bc_opts o = opts ? *opts : default_opts();
+  o.out_device = 0;
+  const size_t cells = (size_t)k * (size_t)g->dev.n;
+  DebugOut dbg;
+  cudaStream_t st = ctx->stream;
+  BC_TRY(cudaMallocAsync(&dbg.d, sizeof(int32_t) * std::max<size_t>(cells, 1), st));
+  BC_TRY(cudaMallocAsync(&dbg.sigma, sizeof(uint64_t) * std::max<size_t>(cells, 1), st));
+  BC_TRY(cudaMallocAsync(&dbg.delta, sizeof(double) * std::max<size_t>(cells, 1), st));
+  BC_TRY(cudaMemsetAsync(dbg.d, 0xff, sizeof(int32_t) * cells, st));
+  BC_TRY(cudaMemsetAsync(dbg.sigma, 0, sizeof(uint64_t) * cells, st));
+  BC_TRY(cudaMemsetAsync(dbg.delta, 0, sizeof(double) * cells, st));
+  std::vector<double> tmp((size_t)std::max<int32_t>(g->dev.n, 1));
+  s = run_sync(ctx, g, src, k, false, &o, tmp.data(), &dbg);
+  if (s == BC_OK || s == BC_ERR_SIGMA_OVERFLOW) {
+    cudaError_t e = cudaSuccess;
+    if (d_out && cells) e = cudaMemcpyAsync(d_out, dbg.d, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && sigma_out && cells) e = cudaMemcpyAsync(sigma_out, dbg.sigma, sizeof(uint64_t) * cells, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && delta_out && cells) e = cudaMemcpyAsync(delta_out, dbg.delta, sizeof(double) * cells, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e);
+  }
+  cudaFreeAsync(dbg.d, st);
+  cudaFreeAsync(dbg.sigma, st);
+  cudaFreeAsync(dbg.delta, st);
+  cudaStreamSynchronize(st);
+  return s;
+}
+
+bc_status bc_debug_source(bc_ctx *ctx, bc_graph h, int32_t s, int32_t *d_out, uint64_t *sigma_out,
+                          double *delta_out) {
+  bc_opts o = default_opts();
+  o.schedule = BC_SCHED_PLAIN;
+  o.delta_fp64 = 1;
+  return bc_debug_sources(ctx, h, &s, 1, &o, d_out, sigma_out, delta_out);
+}
+
+bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, const bc_opts *opts,
+                        double *bc_out) {
+  if (!ctx || (count > 0 && (!graphs || !bc_out)) || count < 0) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  bc_opts o = opts ? *opts : default_opts();
+  if (!opts_valid(o)) return BC_ERR_ARG;
+  int64_t off = 0;
+  bc_stats total{};
+  for (int32_t i = 0; i < count; ++i) {
+    GraphRec *g;
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      g = find_graph(ctx, graphs[i]);
+    }
+    if (!g) return BC_ERR_GRAPH;
+    bc_status s = run_sync(ctx, g, nullptr, g->dev.n, true, &o, bc_out + off, nullptr);
+    if (s != BC_OK) return s;
+    off += g->dev.n;
+    total.n += ctx->last.n;
+    total.m += ctx->last.m;
+    total.sources += ctx->last.sources;
+    total.batches += ctx->last.batches;
+    total.kernel_launches += ctx->last.kernel_launches;
+    total.device_ms += ctx->last.device_ms;
+    total.max_levels = std::max(total.max_levels, ctx->last.max_levels);
+  }
+  ctx->last = total;
+  return BC_OK;
+}
+
+bc_status bc_debug_inject_barrier_skip(bc_ctx *ctx, int32_t block, int32_t timeout_ms) {
+  if (!ctx || timeout_ms < 0) return BC_ERR_ARG;
+  ctx->inject_block = block;
+  ctx->inject_timeout_ms = timeout_ms;
+  return BC_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations of the GB300 betweenness-centrality library: device
+// control block, graph and workspace descriptors, kernel parameters and the
+// host-side launchers.  Not part of the C ABI (see include/bc_gb300.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bcgpu {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;                    // threads per CTA of the persistent kernels
+constexpr int kWarpsPerBlock = kBlock / kWarp; // 8
+constexpr int kK = 64;                         // sources per batch (one bit each in a u64 mask)
+constexpr int kChunk = 256;                    // edges per work chunk of a high-degree vertex
+
+// Device-side error codes (sticky in Ctl::err).
+enum : int {
+  KERR_NONE = 0,
+  KERR_TIMEOUT = 1,  // a grid-barrier wait ran out
+  KERR_QUEUE = 2,    // frontier queue capacity exceeded
+  KERR_HEAVY = 3,    // heavy-entry list capacity exceeded
+  KERR_CHUNKS = 4,   // heavy chunk scratch exceeded
+};
+
+// Job-level counters (uint64 each), accumulated by the kernels.
+enum : int {
+  CNT_ENTRIES = 0,   // (vertex, level) frontier entries
+  CNT_OUT_EDGES = 1, // out-edges scanned (discovery + backward)
+  CNT_IN_EDGES = 2,  // in-edges scanned (path-count pull)
+  CNT_DAG = 3,       // (source, DAG edge) pairs
+  CNT_REACHED = 4,   // (source, reached vertex) pairs
+  CNT_HEAVY = 5,     // heavy chunks processed (forward + backward)
+  CNT_MAXLEV = 6,    // max level count (atomicMax)
+  CNT_N = 8
+};
+
+// Per-workspace control block; the host zeroes it once per job.
+struct Ctl {
+  unsigned int bar_count; // grid barrier arrivals
+  unsigned int bar_gen;   // grid barrier generation
+  int err;                // first device error (KERR_*), sticky for the job
+  int nlevels;            // levels of the current batch
+  unsigned long long tail; // frontier queue tail (entries)
+  unsigned long long ovf;  // batch: sources (bits) whose count reached 2^64; plain: 0/1
+};
+
+// A resident graph: out-CSR, in-CSR and the per-vertex chunk count
+// (0 = light vertex handled by one warp, else ceil((in+out)/kChunk)).
+struct GraphDev {
+  int32_t n = 0;
+  int64_t m = 0;
+  const int32_t *row_ptr = nullptr;
+  const int32_t *col_idx = nullptr;
+  const int32_t *in_ptr = nullptr;
+  const int32_t *in_idx = nullptr;
+  const int32_t *nchunks = nullptr;
+  int64_t heavy_vertices = 0; // vertices with nchunks > 0
+  int64_t heavy_chunks = 0;   // sum of nchunks
+};
+
+// Device workspace of one in-flight batch (or one plain source).
+struct Work {
+  int32_t n = 0;
+  int32_t k_max = 0;          // 64 for the batch kernel, 1 for plain
+  uint64_t *vis = nullptr;    // batch: [n] visited masks
+  uint64_t *fr = nullptr;     // batch: [4][n] rotating dense frontier masks
+  int32_t *d = nullptr;       // plain: [n] depth (-1 unreached)
+  int32_t *qv = nullptr;      // [cap] frontier entries (vertex ids), levels back to back
+  uint64_t *qm = nullptr;     // batch: [cap] entry masks
+  int64_t cap = 0;
+  int64_t *qoff = nullptr;    // [n+3] start of each level in qv
+  unsigned long long *hpack = nullptr; // [n+3] per level: (heavy count << 32) | chunk total
+  int64_t *hoff = nullptr;    // [n+3] start of each level's heavy list
+  int64_t *hq_e = nullptr;    // [hcap] queue position of each heavy entry
+  int64_t *hq_c = nullptr;    // [hcap] first chunk of each heavy entry within its level
+  unsigned *harrive = nullptr; // [hcap] chunk arrivals per heavy entry
+  int64_t hcap = 0;
+  void *partial = nullptr;    // [chunk_cap][k_max] chunk partial sums (u64 or float type)
+  uint64_t *partial_ovf = nullptr; // [chunk_cap] overflow bits of forward partials
+  int64_t chunk_cap = 0;
+  uint64_t *sigma = nullptr;  // [n][k_max] path counts
+  void *cdep = nullptr;       // [n][k_max] (1 + delta) / sigma, float or double
+  Ctl *ctl = nullptr;
+};
+
+struct KParams {
+  GraphDev g;
+  Work w;
+  const int32_t *src = nullptr; // device [k] sources of this batch
+  int32_t k = 0;
+  int64_t src_base = 0;         // position of src[0] in the job's source list
+  double *bc = nullptr;         // [n] accumulator (float64)
+  int8_t *ovf_flags = nullptr;  // [job sources] 1 = count reached 2^64
+  unsigned long long *job_cnt = nullptr; // [CNT_N]
+  int32_t *dbg_d = nullptr;     // [k][n] or null
+  uint64_t *dbg_sigma = nullptr;
+  double *dbg_delta = nullptr;
+  long long timeout_ns = 2000000000LL;
+  int32_t skip_block = -1;      // failure-injection hook (-1: none)
+};
+
+// Host launchers (bc_kernels.cu).  Return a cudaError_t.
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
+int max_grid_batch(bool fp64, int device);
+int max_grid_plain(bool fp64, int device);
+
+} // namespace bcgpu

@@ -1,0 +1,919 @@
+// Device kernels of the GB300 exact betweenness-centrality library.
+//
+// Both kernels run Brandes' two sweeps (paper, Section I; the GPU designs it
+// studies are in Section II.A) as ONE persistent cooperative launch per
+// batch of sources, with levels separated by a software grid barrier whose
+// waits are bounded in time:
+//
+//   forward step l  (one barrier per level)
+//     - every frontier entry w of level l pulls its path counts from its
+//       in-neighbours at level l-1:  sigma[w] = sum sigma[u]   (no atomics);
+//     - and pushes discovery to its out-neighbours: bits new to a vertex x
+//       are OR-ed into visited[x] and into the dense next-level mask, and x
+//       is appended to the level-(l+1) queue on its first touch;
+//   backward step l (one barrier per level, l = L-1 .. 0)
+//     - every entry v of level l pulls from its successors x (edge v->x with
+//       x one level deeper for that source):
+//           delta[v] = sigma[v] * sum c[x],   c[x] = (1 + delta[x]) / sigma[x]
+//       which is Brandes' dependency sum with sigma[v] factored out; no
+//       atomics on delta, fixed reduction order, so results are
+//       deterministic;
+//     - BC[v] += sum over sources j with s_j != v of delta_j[v].
+//
+// The batched kernel advances up to 64 sources together: frontiers and
+// visited sets are u64 bitsets (bit j = source j), per-vertex state is laid
+// out source-innermost ([n][64]) so a warp touches one contiguous row, lane
+// j owning sources j and j+32.  The plain kernel is the one-source baseline
+// (the paper's multi-block-per-source design, Section II.A, with the level
+// loop moved on-device), lanes spread over edges.
+//
+// High-degree vertices (in+out degree > kChunk) are split into chunks that
+// different warps process; partial sums meet in scratch and the last
+// arriving warp (ticket counter) reduces them in chunk order, which keeps
+// the result deterministic.  Memory written during a launch by another SM is
+// always read through L2 (ld.global.cg), never a possibly stale L1 line.
+#include "bc_internal.cuh"
+
+#include <cstdio>
+
+namespace bcgpu {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void set_err(Ctl *ctl, int code) { atomicCAS(&ctl->err, 0, code); }
+
+__device__ __forceinline__ int read_err(const Ctl *ctl) {
+  return *reinterpret_cast<const volatile int *>(&ctl->err);
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// wait is bounded by timeout_ns; on expiry the CTA records KERR_TIMEOUT and
+// continues, and every CTA then leaves the kernel at its next error check.
+// When snap_dst is given, the last CTA to arrive copies the queue tail there
+// before releasing the others: once every CTA has arrived no enqueue of the
+// finished level can still be in flight, so the copy is that level's final
+// end, and unlike the live tail (which the next level's enqueues advance) it
+// reads the same in every CTA.  Returns false when the job is in an error
+// state.
+__device__ bool grid_sync(Ctl *ctl, long long timeout_ns, int64_t *snap_dst = nullptr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *genp = &ctl->bar_gen;
+    const unsigned gen = *genp;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      if (snap_dst) *snap_dst = (int64_t)atomicAdd(&ctl->tail, 0ull);
+      ctl->bar_count = 0;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*genp == gen) {
+        if (read_err(ctl)) break;
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+          set_err(ctl, KERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return read_err(ctl) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// batched kernel: up to 64 sources, bitset frontiers
+// ---------------------------------------------------------------------------
+
+template <typename DT> __device__ __forceinline__ DT u64_to(uint64_t x);
+template <> __device__ __forceinline__ float u64_to<float>(uint64_t x) { return __ull2float_rn(x); }
+template <> __device__ __forceinline__ double u64_to<double>(uint64_t x) { return __ull2double_rn(x); }
+
+// saturating add: on carry the sum pins at 2^64-1 and the flag is raised
+__device__ __forceinline__ void sat_add(uint64_t &acc, uint64_t x, bool &ovf) {
+  uint64_t s = acc + x;
+  if (s < x) {
+    s = ~0ull;
+    ovf = true;
+  }
+  acc = s;
+}
+
+struct LevelView {
+  int lvl;
+  int64_t lo, hi;        // queue range of this level
+  int64_t hoff;          // first heavy entry of this level
+  int64_t nheavy;        // heavy entries of this level
+  int64_t nhc;           // heavy chunks of this level
+  int64_t hoff_next;     // first heavy entry of the next level (forward)
+};
+
+// Index of the heavy entry that owns chunk `item` (binary search over the
+// level's chunk prefixes, which increase with the entry index).
+__device__ __forceinline__ int64_t find_heavy(const int64_t *hq_c, int64_t base, int64_t cnt,
+                                              int64_t item) {
+  int64_t lo = 0, hi = cnt; // invariant: hq_c[base+lo] <= item < hq_c[base+hi] (virtual end)
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (ldcg(hq_c + base + mid) <= item) lo = mid; else hi = mid;
+  }
+  return base + lo;
+}
+
+// Arrival ticket of a heavy-entry chunk: every lane's partial writes are
+// fenced, the warp converges, lane 0 takes the ticket, and after the
+// broadcast every lane fences again so the last arriver reads all partials.
+__device__ __forceinline__ unsigned chunk_ticket(unsigned *arrive, int lane) {
+  __threadfence();
+  __syncwarp();
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(arrive, 1u);
+  t = __shfl_sync(kFull, t, 0);
+  __threadfence();
+  return t;
+}
+
+struct Counters {
+  unsigned long long entries = 0, out_e = 0, in_e = 0, dag = 0, reached = 0, heavy = 0;
+};
+
+// Warp-aggregated append of newly discovered vertices to the next level.
+__device__ __forceinline__ void enqueue_new(const KParams &p, const LevelView &lv, bool isnew,
+                                            int x, int lane) {
+  const unsigned bal = __ballot_sync(kFull, isnew);
+  if (!bal) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&p.w.ctl->tail, (unsigned long long)__popc(bal));
+  base = __shfl_sync(kFull, base, 0);
+  if (!isnew) return;
+  const long long pos = (long long)base + __popc(bal & lanemask_lt());
+  if (pos >= p.w.cap) {
+    set_err(p.w.ctl, KERR_QUEUE);
+    return;
+  }
+  p.w.qv[pos] = x;
+  const int nch = __ldg(p.g.nchunks + x);
+  if (nch > 0) {
+    const unsigned long long h =
+        atomicAdd(&p.w.hpack[lv.lvl + 1], (1ull << 32) | (unsigned long long)nch);
+    const int64_t hidx = lv.hoff_next + (int64_t)(h >> 32);
+    const int64_t cpre = (int64_t)(h & 0xffffffffull);
+    if (hidx >= p.w.hcap) {
+      set_err(p.w.ctl, KERR_HEAVY);
+      return;
+    }
+    if (cpre + nch > p.w.chunk_cap) {
+      set_err(p.w.ctl, KERR_CHUNKS);
+      return;
+    }
+    p.w.hq_e[hidx] = pos;
+    p.w.hq_c[hidx] = cpre;
+  }
+}
+
+// Batch: discovery push over out-edges [eb, ee) of a frontier vertex with mask F.
+__device__ __forceinline__ void batch_discover(const KParams &p, const LevelView &lv, uint64_t F,
+                                               int64_t eb, int64_t ee, uint64_t *Bn, int lane) {
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    bool isnew = false;
+    int x = 0;
+    if (e < ee) {
+      x = __ldg(p.g.col_idx + e);
+      const uint64_t m = F & ~ldcg(p.w.vis + x);
+      if (m) {
+        const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(p.w.vis + x), m);
+        const uint64_t nb = m & ~old;
+        if (nb) {
+          const uint64_t oldB = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb);
+          isnew = (oldB == 0);
+        }
+      }
+    }
+    enqueue_new(p, lv, isnew, x, lane);
+  }
+}
+
+// Batch: path-count pull over in-edges [eb, ee) of entry w (mask F) from the
+// level l-1 dense mask Pm.  Lane owns sources lane and lane+32.
+__device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, int64_t eb,
+                                                 int64_t ee, const uint64_t *Pm, int lane,
+                                                 uint64_t &s0, uint64_t &s1, bool &o0, bool &o1,
+                                                 unsigned long long &dag) {
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    int u = 0;
+    uint64_t P = 0;
+    if (e < ee) {
+      u = __ldg(p.g.in_idx + e);
+      P = ldcg(Pm + u) & F;
+    }
+    unsigned bal = __ballot_sync(kFull, P != 0);
+    while (bal) {
+      const int l = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int uu = __shfl_sync(kFull, u, l);
+      const uint64_t PP = __shfl_sync(kFull, P, l);
+      const uint64_t *row = p.w.sigma + (size_t)uu * kK;
+      if ((PP >> lane) & 1ull) sat_add(s0, ldcg(row + lane), o0);
+      if ((PP >> (lane + 32)) & 1ull) sat_add(s1, ldcg(row + 32 + lane), o1);
+      if (lane == 0) dag += __popcll(PP);
+    }
+  }
+}
+
+// Batch: dependency pull over out-edges [eb, ee) of entry v (mask F) from
+// the level l+1 dense mask Dn.
+template <typename DT>
+__device__ __forceinline__ void batch_pull_delta(const KParams &p, uint64_t F, int64_t eb,
+                                                 int64_t ee, const uint64_t *Dn, int lane,
+                                                 DT &a0, DT &a1) {
+  const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    int x = 0;
+    uint64_t S = 0;
+    if (e < ee) {
+      x = __ldg(p.g.col_idx + e);
+      S = ldcg(Dn + x) & F;
+    }
+    unsigned bal = __ballot_sync(kFull, S != 0);
+    while (bal) {
+      const int l = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int xx = __shfl_sync(kFull, x, l);
+      const uint64_t SS = __shfl_sync(kFull, S, l);
+      const DT *row = cdep + (size_t)xx * kK;
+      if ((SS >> lane) & 1ull) a0 += ldcg(row + lane);
+      if ((SS >> (lane + 32)) & 1ull) a1 += ldcg(row + 32 + lane);
+    }
+  }
+}
+
+// Batch: writes the path counts of entry w (mask F) and records overflow.
+__device__ __forceinline__ void batch_store_sigma(const KParams &p, int w, uint64_t F,
+                                                  uint64_t s0, uint64_t s1, bool o0, bool o1,
+                                                  int lane) {
+  uint64_t *row = p.w.sigma + (size_t)w * kK;
+  if ((F >> lane) & 1ull) row[lane] = s0;
+  if ((F >> (lane + 32)) & 1ull) row[32 + lane] = s1;
+  const uint64_t ob =
+      ((uint64_t)__ballot_sync(kFull, o0) | ((uint64_t)__ballot_sync(kFull, o1) << 32)) & F;
+  if (ob && lane == 0) atomicOr(&p.w.ctl->ovf, (unsigned long long)ob);
+}
+
+// Batch: closes entry v (mask F) at level l of the backward sweep given the
+// lane's successor sums a0/a1: dependencies, coefficients, BC, resets.
+template <typename DT>
+__device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, uint64_t F, DT a0,
+                                             DT a1, uint64_t *Wn, int s_lo, int s_hi,
+                                             int lane) {
+  uint64_t *srow = p.w.sigma + (size_t)v * kK;
+  DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * kK;
+  double contrib = 0.0;
+  const int n = p.g.n;
+  if ((F >> lane) & 1ull) {
+    const uint64_t sg = ldcg(srow + lane);
+    const DT sf = u64_to<DT>(sg);
+    const DT dl = sf * a0;
+    crow[lane] = (DT(1) + dl) / sf;
+    srow[lane] = 0;
+    if (s_lo != v) contrib += (double)dl;
+    if (p.dbg_d) {
+      const size_t o = (size_t)lane * n + v;
+      p.dbg_d[o] = lvl;
+      p.dbg_sigma[o] = sg;
+      p.dbg_delta[o] = (double)dl;
+    }
+  }
+  if ((F >> (lane + 32)) & 1ull) {
+    const uint64_t sg = ldcg(srow + 32 + lane);
+    const DT sf = u64_to<DT>(sg);
+    const DT dl = sf * a1;
+    crow[32 + lane] = (DT(1) + dl) / sf;
+    srow[32 + lane] = 0;
+    if (s_hi != v) contrib += (double)dl;
+    if (p.dbg_d) {
+      const size_t o = (size_t)(lane + 32) * n + v;
+      p.dbg_d[o] = lvl;
+      p.dbg_sigma[o] = sg;
+      p.dbg_delta[o] = (double)dl;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(kFull, contrib, off);
+  if (lane == 0) {
+    if (contrib != 0.0) p.bc[v] = ldcg(p.bc + v) + contrib;
+    p.w.vis[v] = 0;
+    if (Wn) Wn[v] = F;
+  }
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * kBlock;
+  Ctl *ctl = p.w.ctl;
+  const int n = p.g.n;
+  uint64_t *const fr = p.w.fr;
+  Counters cnt;
+
+  if (read_err(ctl)) return;
+  // sources owned by this lane (for excluding s from its own BC)
+  const int s_lo = lane < p.k ? __ldg(p.src + lane) : -1;
+  const int s_hi = lane + 32 < p.k ? __ldg(p.src + lane + 32) : -1;
+
+  // ---- init: level 0 = the sources (block 0) ------------------------------
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      ctl->tail = 0;
+      ctl->ovf = 0;
+      ctl->nlevels = 0;
+      p.w.hpack[0] = 0;
+      p.w.hpack[1] = 0;
+      p.w.qoff[0] = 0;
+      p.w.hoff[0] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < p.k) {
+      const int j = threadIdx.x;
+      const int s = __ldg(p.src + j);
+      atomicOr(reinterpret_cast<unsigned long long *>(p.w.vis + s), 1ull << j);
+      const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(fr + s), 1ull << j);
+      if (old == 0) {
+        const unsigned long long pos = atomicAdd(&ctl->tail, 1ull);
+        p.w.qv[pos] = s;
+        const int nch = __ldg(p.g.nchunks + s);
+        if (nch > 0) {
+          const unsigned long long h =
+              atomicAdd(&p.w.hpack[0], (1ull << 32) | (unsigned long long)nch);
+          p.w.hq_e[h >> 32] = (int64_t)pos;
+          p.w.hq_c[h >> 32] = (int64_t)(h & 0xffffffffull);
+        }
+      }
+    }
+  }
+  if (p.skip_block == (int)blockIdx.x) return; // failure-injection hook: never arrives
+  if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + 1)) return;
+
+  // ---- forward sweep -------------------------------------------------------
+  LevelView lv;
+  lv.lvl = 0;
+  lv.lo = 0;
+  lv.hi = ldcg(p.w.qoff + 1);
+  lv.hoff = 0;
+  int64_t lo_m2 = 0; // start of level l-2
+  int64_t lo_m1 = 0; // start of level l-1
+  int L = 0;
+  while (true) {
+    const int l = lv.lvl;
+    uint64_t *Bn = fr + (size_t)((l + 1) & 3) * n;      // level l+1 (being built)
+    const uint64_t *A = fr + (size_t)(l & 3) * n;       // level l
+    const uint64_t *Pm = fr + (size_t)((l + 3) & 3) * n; // level l-1
+    uint64_t *Z = fr + (size_t)((l + 2) & 3) * n;       // level l-2 (cleared now)
+    const unsigned long long hp = ldcg(p.w.hpack + l);
+    lv.nheavy = (int64_t)(hp >> 32);
+    lv.nhc = (int64_t)(hp & 0xffffffffull);
+    lv.hoff_next = lv.hoff + lv.nheavy;
+    if (gtid == 0) {
+      p.w.hoff[l] = lv.hoff;
+      p.w.hpack[l + 2] = 0;
+    }
+    if (l >= 2)
+      for (int64_t i = lo_m2 + gtid; i < lo_m1; i += nthr) Z[ldcg(p.w.qv + i)] = 0;
+
+    const int64_t nlight = lv.hi - lv.lo;
+    for (int64_t item = gwarp; item < lv.nhc + nlight; item += nwarps) {
+      if (item < lv.nhc) {
+        // one chunk of a heavy entry
+        const int64_t h = find_heavy(p.w.hq_c, lv.hoff, lv.nheavy, item);
+        const int64_t e = ldcg(p.w.hq_e + h);
+        const int w = ldcg(p.w.qv + e);
+        const uint64_t F = ldcg(A + w);
+        const int nch = __ldg(p.g.nchunks + w);
+        const int64_t c = item - ldcg(p.w.hq_c + h);
+        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+        const int64_t indeg = ie - is, tot = indeg + (re - rs);
+        const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
+        uint64_t s0 = 0, s1 = 0;
+        bool o0 = false, o1 = false;
+        if (l > 0 && a < indeg)
+          batch_pull_sigma(p, F, is + a, is + (b < indeg ? b : indeg), Pm, lane, s0, s1, o0, o1,
+                           cnt.dag);
+        if (b > indeg)
+          batch_discover(p, lv, F, rs + (a > indeg ? a - indeg : 0), rs + (b - indeg), Bn, lane);
+        if (lane == 0) {
+          cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
+          cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
+          cnt.heavy++;
+        }
+        uint64_t *part = reinterpret_cast<uint64_t *>(p.w.partial) + (size_t)item * kK;
+        part[lane] = s0;
+        part[32 + lane] = s1;
+        const uint64_t ob = (uint64_t)__ballot_sync(kFull, o0) |
+                            ((uint64_t)__ballot_sync(kFull, o1) << 32);
+        if (lane == 0) p.w.partial_ovf[item] = ob;
+        const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
+        if (ticket == (unsigned)(nch - 1)) {
+          const int64_t c0 = ldcg(p.w.hq_c + h);
+          uint64_t t0 = 0, t1 = 0;
+          bool q0 = false, q1 = false;
+          uint64_t ovb = 0;
+          if (l == 0) {
+            t0 = 1;
+            t1 = 1;
+          } else {
+            const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
+            for (int64_t cc = c0; cc < c0 + nch; ++cc) {
+              sat_add(t0, ldcg(pp + (size_t)cc * kK + lane), q0);
+              sat_add(t1, ldcg(pp + (size_t)cc * kK + 32 + lane), q1);
+              ovb |= ldcg(p.w.partial_ovf + cc);
+            }
+          }
+          batch_store_sigma(p, w, F, t0, t1, q0 || ((ovb >> lane) & 1ull),
+                            q1 || ((ovb >> (lane + 32)) & 1ull), lane);
+          if (lane == 0) {
+            p.w.harrive[h] = 0;
+            p.w.qm[e] = F;
+            cnt.entries++;
+            cnt.reached += __popcll(F);
+          }
+        }
+      } else {
+        const int64_t e = lv.lo + (item - lv.nhc);
+        const int w = ldcg(p.w.qv + e);
+        if (__ldg(p.g.nchunks + w) > 0) continue; // handled as chunks
+        const uint64_t F = ldcg(A + w);
+        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+        uint64_t s0 = 0, s1 = 0;
+        bool o0 = false, o1 = false;
+        if (l == 0) {
+          s0 = 1;
+          s1 = 1;
+        } else {
+          batch_pull_sigma(p, F, is, ie, Pm, lane, s0, s1, o0, o1, cnt.dag);
+        }
+        batch_store_sigma(p, w, F, s0, s1, o0, o1, lane);
+        batch_discover(p, lv, F, rs, re, Bn, lane);
+        if (lane == 0) {
+          p.w.qm[e] = F;
+          cnt.entries++;
+          cnt.reached += __popcll(F);
+          cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
+          cnt.out_e += (uint64_t)(re - rs);
+        }
+      }
+    }
+    if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    const int64_t nh = ldcg(p.w.qoff + l + 2);
+    if (nh == lv.hi) {
+      L = l + 1;
+      break;
+    }
+    lo_m2 = lo_m1;
+    lo_m1 = lv.lo;
+    lv.lo = lv.hi;
+    lv.hi = nh;
+    lv.hoff = lv.hoff_next;
+    lv.lvl = l + 1;
+  }
+
+  if (gtid == 0) {
+    ctl->nlevels = L;
+    atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
+    const uint64_t ob = ldcg(&ctl->ovf);
+    for (int j = 0; j < p.k; ++j)
+      if ((ob >> j) & 1ull) p.ovf_flags[p.src_base + j] = 1;
+  }
+
+  // ---- backward sweep ------------------------------------------------------
+  for (int l = L - 1; l >= 0; --l) {
+    const uint64_t *Dn = fr + (size_t)((l + 1) & 3) * n; // level l+1 masks
+    uint64_t *Wn = l > 0 ? fr + (size_t)(l & 3) * n : nullptr; // level l masks for step l-1
+    uint64_t *Z = fr + (size_t)((l + 2) & 3) * n;        // level l+2 (cleared now)
+    const int64_t lo = ldcg(p.w.qoff + l), hi = ldcg(p.w.qoff + l + 1);
+    const unsigned long long hp = ldcg(p.w.hpack + l);
+    const int64_t nheavy = (int64_t)(hp >> 32), nhc = (int64_t)(hp & 0xffffffffull);
+    const int64_t hoff = ldcg(p.w.hoff + l);
+    if (l + 2 <= L - 1) {
+      const int64_t zlo = ldcg(p.w.qoff + l + 2), zhi = ldcg(p.w.qoff + l + 3);
+      for (int64_t i = zlo + gtid; i < zhi; i += nthr) Z[ldcg(p.w.qv + i)] = 0;
+    }
+    const bool deepest = (l == L - 1);
+    for (int64_t item = gwarp; item < nhc + (hi - lo); item += nwarps) {
+      if (item < nhc) {
+        const int64_t h = find_heavy(p.w.hq_c, hoff, nheavy, item);
+        const int64_t e = ldcg(p.w.hq_e + h);
+        const int v = ldcg(p.w.qv + e);
+        const uint64_t F = ldcg(p.w.qm + e);
+        const int nch = __ldg(p.g.nchunks + v);
+        const int64_t c = item - ldcg(p.w.hq_c + h);
+        const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
+        const int64_t od = re - rs;
+        const int64_t a = c * od / nch, b = (c + 1) * od / nch;
+        DT a0 = 0, a1 = 0;
+        if (!deepest) batch_pull_delta<DT>(p, F, rs + a, rs + b, Dn, lane, a0, a1);
+        if (lane == 0) {
+          cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
+          cnt.heavy++;
+        }
+        DT *part = reinterpret_cast<DT *>(p.w.partial) + (size_t)item * kK;
+        part[lane] = a0;
+        part[32 + lane] = a1;
+        const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
+        if (ticket == (unsigned)(nch - 1)) {
+          const int64_t c0 = ldcg(p.w.hq_c + h);
+          const DT *pp = reinterpret_cast<const DT *>(p.w.partial);
+          DT t0 = 0, t1 = 0;
+          for (int64_t cc = c0; cc < c0 + nch; ++cc) {
+            t0 += ldcg(pp + (size_t)cc * kK + lane);
+            t1 += ldcg(pp + (size_t)cc * kK + 32 + lane);
+          }
+          batch_finish<DT>(p, l, v, F, t0, t1, Wn, s_lo, s_hi, lane);
+          if (lane == 0) p.w.harrive[h] = 0;
+        }
+      } else {
+        const int64_t e = lo + (item - nhc);
+        const int v = ldcg(p.w.qv + e);
+        if (__ldg(p.g.nchunks + v) > 0) continue;
+        const uint64_t F = ldcg(p.w.qm + e);
+        DT a0 = 0, a1 = 0;
+        if (!deepest) {
+          const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
+          batch_pull_delta<DT>(p, F, rs, re, Dn, lane, a0, a1);
+          if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
+        }
+        batch_finish<DT>(p, l, v, F, a0, a1, Wn, s_lo, s_hi, lane);
+      }
+    }
+    if (!grid_sync(ctl, p.timeout_ns)) return;
+  }
+
+  // ---- leave the workspace clean for the next batch ------------------------
+  {
+    const int64_t q1 = ldcg(p.w.qoff + 1);
+    const int64_t q2 = L >= 2 ? ldcg(p.w.qoff + 2) : q1;
+    for (int64_t i = gtid; i < q1; i += nthr) fr[ldcg(p.w.qv + i)] = 0;
+    for (int64_t i = q1 + gtid; i < q2; i += nthr) fr[(size_t)n + ldcg(p.w.qv + i)] = 0;
+  }
+  if (lane == 0) {
+    atomicAdd(p.job_cnt + CNT_ENTRIES, cnt.entries);
+    atomicAdd(p.job_cnt + CNT_OUT_EDGES, cnt.out_e);
+    atomicAdd(p.job_cnt + CNT_IN_EDGES, cnt.in_e);
+    atomicAdd(p.job_cnt + CNT_DAG, cnt.dag);
+    atomicAdd(p.job_cnt + CNT_REACHED, cnt.reached);
+    atomicAdd(p.job_cnt + CNT_HEAVY, cnt.heavy);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plain kernel: one source, lanes over edges
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void warp_sat_sum(uint64_t &v, bool &o) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t w = __shfl_down_sync(kFull, v, off);
+    const bool ow = __shfl_down_sync(kFull, (int)o, off) != 0;
+    o = o || ow;
+    sat_add(v, w, o);
+  }
+}
+
+template <typename DT> __device__ __forceinline__ DT warp_sum(DT v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
+  return v;
+}
+
+__device__ __forceinline__ void plain_discover(const KParams &p, const LevelView &lv, int64_t eb,
+                                               int64_t ee, int lane) {
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    bool isnew = false;
+    int x = 0;
+    if (e < ee) {
+      x = __ldg(p.g.col_idx + e);
+      if (ldcg(p.w.d + x) < 0) isnew = (atomicCAS(p.w.d + x, -1, lv.lvl + 1) == -1);
+    }
+    enqueue_new(p, lv, isnew, x, lane);
+  }
+}
+
+__device__ __forceinline__ void plain_pull_sigma(const KParams &p, int lvl, int64_t eb,
+                                                 int64_t ee, int lane, uint64_t &s, bool &o,
+                                                 unsigned long long &dag) {
+  unsigned long long nd = 0;
+  for (int64_t e = eb + lane; e < ee; e += kWarp) {
+    const int u = __ldg(p.g.in_idx + e);
+    if (ldcg(p.w.d + u) == lvl - 1) {
+      sat_add(s, ldcg(p.w.sigma + u), o);
+      ++nd;
+    }
+  }
+  dag += nd;
+}
+
+template <typename DT>
+__device__ __forceinline__ DT plain_pull_delta(const KParams &p, int lvl, int64_t eb, int64_t ee,
+                                               int lane) {
+  const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
+  DT a = 0;
+  for (int64_t e = eb + lane; e < ee; e += kWarp) {
+    const int x = __ldg(p.g.col_idx + e);
+    if (ldcg(p.w.d + x) == lvl + 1) a += ldcg(cdep + x);
+  }
+  return a;
+}
+
+template <typename DT>
+__device__ __forceinline__ void plain_finish(const KParams &p, int lvl, int v, DT acc, int s) {
+  // lane 0 only
+  const uint64_t sg = ldcg(p.w.sigma + v);
+  const DT sf = u64_to<DT>(sg);
+  const DT dl = sf * acc;
+  reinterpret_cast<DT *>(p.w.cdep)[v] = (DT(1) + dl) / sf;
+  p.w.sigma[v] = 0;
+  if (v != s && dl != DT(0)) p.bc[v] = ldcg(p.bc + v) + (double)dl;
+  if (p.dbg_d) {
+    p.dbg_d[v] = lvl;
+    p.dbg_sigma[v] = sg;
+    p.dbg_delta[v] = (double)dl;
+  }
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * kBlock;
+  Ctl *ctl = p.w.ctl;
+  Counters cnt;
+  if (read_err(ctl)) return;
+  const int s = __ldg(p.src);
+
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->tail = 1;
+    ctl->ovf = 0;
+    p.w.qv[0] = s;
+    p.w.d[s] = 0;
+    p.w.qoff[0] = 0;
+    p.w.qoff[1] = 1;
+    p.w.hoff[0] = 0;
+    p.w.hpack[1] = 0;
+    const int nch = __ldg(p.g.nchunks + s);
+    p.w.hpack[0] = nch > 0 ? ((1ull << 32) | (unsigned long long)nch) : 0ull;
+    if (nch > 0) {
+      p.w.hq_e[0] = 0;
+      p.w.hq_c[0] = 0;
+    }
+  }
+  if (p.skip_block == (int)blockIdx.x) return;
+  if (!grid_sync(ctl, p.timeout_ns)) return;
+
+  LevelView lv;
+  lv.lvl = 0;
+  lv.lo = 0;
+  lv.hi = 1;
+  lv.hoff = 0;
+  int L = 0;
+  while (true) {
+    const int l = lv.lvl;
+    const unsigned long long hp = ldcg(p.w.hpack + l);
+    lv.nheavy = (int64_t)(hp >> 32);
+    lv.nhc = (int64_t)(hp & 0xffffffffull);
+    lv.hoff_next = lv.hoff + lv.nheavy;
+    if (gtid == 0) {
+      p.w.hoff[l] = lv.hoff;
+      p.w.hpack[l + 2] = 0;
+    }
+    for (int64_t item = gwarp; item < lv.nhc + (lv.hi - lv.lo); item += nwarps) {
+      if (item < lv.nhc) {
+        const int64_t h = find_heavy(p.w.hq_c, lv.hoff, lv.nheavy, item);
+        const int64_t e = ldcg(p.w.hq_e + h);
+        const int w = ldcg(p.w.qv + e);
+        const int nch = __ldg(p.g.nchunks + w);
+        const int64_t c = item - ldcg(p.w.hq_c + h);
+        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+        const int64_t indeg = ie - is, tot = indeg + (re - rs);
+        const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
+        uint64_t sv = 0;
+        bool o = false;
+        if (l > 0 && a < indeg)
+          plain_pull_sigma(p, l, is + a, is + (b < indeg ? b : indeg), lane, sv, o, cnt.dag);
+        warp_sat_sum(sv, o);
+        if (b > indeg) plain_discover(p, lv, rs + (a > indeg ? a - indeg : 0), rs + (b - indeg), lane);
+        if (lane == 0) {
+          cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
+          cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
+          cnt.heavy++;
+          uint64_t *part = reinterpret_cast<uint64_t *>(p.w.partial);
+          part[item] = sv;
+          p.w.partial_ovf[item] = o ? 1ull : 0ull;
+        }
+        const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
+        if (ticket == (unsigned)(nch - 1) && lane == 0) {
+          const int64_t c0 = ldcg(p.w.hq_c + h);
+          uint64_t t = 0;
+          bool q = false;
+          if (l == 0) {
+            t = 1;
+          } else {
+            const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
+            for (int64_t cc = c0; cc < c0 + nch; ++cc) {
+              sat_add(t, ldcg(pp + cc), q);
+              q = q || ldcg(p.w.partial_ovf + cc) != 0;
+            }
+          }
+          p.w.sigma[w] = t;
+          if (q) atomicOr(&ctl->ovf, 1ull);
+          p.w.harrive[h] = 0;
+          cnt.entries++;
+          cnt.reached++;
+        }
+      } else {
+        const int64_t e = lv.lo + (item - lv.nhc);
+        const int w = ldcg(p.w.qv + e);
+        if (__ldg(p.g.nchunks + w) > 0) continue;
+        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+        uint64_t sv = 0;
+        bool o = false;
+        if (l > 0) plain_pull_sigma(p, l, is, ie, lane, sv, o, cnt.dag);
+        warp_sat_sum(sv, o);
+        if (lane == 0) {
+          p.w.sigma[w] = (l == 0) ? 1ull : sv;
+          if (o) atomicOr(&ctl->ovf, 1ull);
+          cnt.entries++;
+          cnt.reached++;
+          cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
+          cnt.out_e += (uint64_t)(re - rs);
+        }
+        plain_discover(p, lv, rs, re, lane);
+      }
+    }
+    if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    const int64_t nh = ldcg(p.w.qoff + l + 2);
+    if (nh == lv.hi) {
+      L = l + 1;
+      break;
+    }
+    lv.lo = lv.hi;
+    lv.hi = nh;
+    lv.hoff = lv.hoff_next;
+    lv.lvl = l + 1;
+  }
+  if (gtid == 0) {
+    ctl->nlevels = L;
+    atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
+    if (ldcg(&ctl->ovf)) p.ovf_flags[p.src_base] = 1;
+  }
+
+  for (int l = L - 1; l >= 0; --l) {
+    const int64_t lo = ldcg(p.w.qoff + l), hi = ldcg(p.w.qoff + l + 1);
+    const unsigned long long hp = ldcg(p.w.hpack + l);
+    const int64_t nheavy = (int64_t)(hp >> 32), nhc = (int64_t)(hp & 0xffffffffull);
+    const int64_t hoff = ldcg(p.w.hoff + l);
+    if (l + 2 <= L - 1) {
+      const int64_t zlo = ldcg(p.w.qoff + l + 2), zhi = ldcg(p.w.qoff + l + 3);
+      for (int64_t i = zlo + gtid; i < zhi; i += nthr) p.w.d[ldcg(p.w.qv + i)] = -1;
+    }
+    const bool deepest = (l == L - 1);
+    for (int64_t item = gwarp; item < nhc + (hi - lo); item += nwarps) {
+      if (item < nhc) {
+        const int64_t h = find_heavy(p.w.hq_c, hoff, nheavy, item);
+        const int64_t e = ldcg(p.w.hq_e + h);
+        const int v = ldcg(p.w.qv + e);
+        const int nch = __ldg(p.g.nchunks + v);
+        const int64_t c = item - ldcg(p.w.hq_c + h);
+        const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
+        const int64_t od = re - rs;
+        const int64_t a = c * od / nch, b = (c + 1) * od / nch;
+        DT acc = 0;
+        if (!deepest) acc = plain_pull_delta<DT>(p, l, rs + a, rs + b, lane);
+        acc = warp_sum<DT>(acc);
+        if (lane == 0) {
+          cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
+          cnt.heavy++;
+          reinterpret_cast<DT *>(p.w.partial)[item] = acc;
+        }
+        const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
+        if (ticket == (unsigned)(nch - 1) && lane == 0) {
+          const int64_t c0 = ldcg(p.w.hq_c + h);
+          const DT *pp = reinterpret_cast<const DT *>(p.w.partial);
+          DT t = 0;
+          for (int64_t cc = c0; cc < c0 + nch; ++cc) t += ldcg(pp + cc);
+          plain_finish<DT>(p, l, v, t, s);
+          p.w.harrive[h] = 0;
+        }
+      } else {
+        const int64_t e = lo + (item - nhc);
+        const int v = ldcg(p.w.qv + e);
+        if (__ldg(p.g.nchunks + v) > 0) continue;
+        DT acc = 0;
+        if (!deepest) {
+          const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
+          acc = plain_pull_delta<DT>(p, l, rs, re, lane);
+          if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
+        }
+        acc = warp_sum<DT>(acc);
+        if (lane == 0) plain_finish<DT>(p, l, v, acc, s);
+      }
+    }
+    if (!grid_sync(ctl, p.timeout_ns)) return;
+  }
+  {
+    const int64_t q2 = L >= 2 ? ldcg(p.w.qoff + 2) : ldcg(p.w.qoff + 1);
+    for (int64_t i = gtid; i < q2; i += nthr) p.w.d[ldcg(p.w.qv + i)] = -1;
+  }
+  if (lane == 0) {
+    atomicAdd(p.job_cnt + CNT_ENTRIES, cnt.entries);
+    atomicAdd(p.job_cnt + CNT_OUT_EDGES, cnt.out_e);
+    atomicAdd(p.job_cnt + CNT_IN_EDGES, cnt.in_e);
+    atomicAdd(p.job_cnt + CNT_DAG, cnt.dag);
+    atomicAdd(p.job_cnt + CNT_REACHED, cnt.reached);
+    atomicAdd(p.job_cnt + CNT_HEAVY, cnt.heavy);
+  }
+}
+
+__global__ void scale_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t n,
+                             double factor) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] * factor;
+}
+
+template <typename K> int max_grid_for(K kernel, int device) {
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess)
+    return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+template <typename K> cudaError_t coop_launch(K kernel, const KParams &p, int grid,
+                                              cudaStream_t st) {
+  void *args[] = {const_cast<KParams *>(&p)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kernel), dim3(grid),
+                                     dim3(kBlock), args, 0, st);
+}
+
+} // namespace
+
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st) {
+  return fp64 ? coop_launch(batch_kernel<double>, p, grid, st)
+              : coop_launch(batch_kernel<float>, p, grid, st);
+}
+
+cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st) {
+  return fp64 ? coop_launch(plain_kernel<double>, p, grid, st)
+              : coop_launch(plain_kernel<float>, p, grid, st);
+}
+
+cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor,
+                         cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  scale_kernel<<<grid, 256, 0, st>>>(in, out, n, factor);
+  return cudaGetLastError();
+}
+
+int max_grid_batch(bool fp64, int device) {
+  return fp64 ? max_grid_for(batch_kernel<double>, device)
+              : max_grid_for(batch_kernel<float>, device);
+}
+
+int max_grid_plain(bool fp64, int device) {
+  return fp64 ? max_grid_for(plain_kernel<double>, device)
+              : max_grid_for(plain_kernel<float>, device);
+}
+
+} // namespace bcgpu

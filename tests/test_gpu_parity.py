@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (written here, derived in the design doc):
+  * depths d[] and path counts sigma[]: bit-exact (integers);
+  * BC: where the oracle gives exactly 0 the GPU must give exactly 0;
+    elsewhere relative error <= 1e-12 with FP64 dependencies and <= 1e-4 with
+    FP32 dependencies.
+"""
+import numpy as np
+import pytest
+
+import bcgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {True: 1e-12, False: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1409_7764_gb300 as bc
+    c = bc.Context(0)
+    yield c
+    c.close()
+
+
+def assert_bc_close(got, ref, fp64):
+    got = np.asarray(got)
+    zero = ref == 0
+    assert np.array_equal(got[zero], ref[zero]), "exact zeros differ"
+    nz = ~zero
+    if nz.any():
+        rel = np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])
+        assert rel.max() <= TOL[fp64], f"max rel err {rel.max():.3e}"
+
+
+def graphs_small():
+    return [
+        bcgen.path(37), bcgen.path(16, bidirected=True), bcgen.cycle(21), bcgen.star(40, "bi"),
+        bcgen.star(30, "out"), bcgen.complete(9), bcgen.grid(6, 7), bcgen.rmat(8, 8, seed=1),
+        bcgen.rmat(10, 8, seed=1), bcgen.ba_directed(700, 4, 5, seed=2),
+        bcgen.random_digraph(50, 0.08, 3),
+    ]
+
+
+def hub_graph():
+    """A bidirected star with 3000 leaves (in+out degree 6000 at the hub, so
+    it is split into many chunks), a 40-vertex path hanging off a leaf
+    (many levels) and random extra edges."""
+    n_leaf = 3000
+    hub = 0
+    leaves = np.arange(1, n_leaf + 1)
+    tail = np.arange(n_leaf + 1, n_leaf + 41)
+    src = [np.zeros(n_leaf, int), leaves, [5], tail[:-1]]
+    dst = [leaves, np.zeros(n_leaf, int), [tail[0]], tail[1:]]
+    rs = np.random.default_rng(4)
+    extra_s = rs.integers(0, n_leaf + 41, 2000)
+    extra_d = rs.integers(0, n_leaf + 41, 2000)
+    src = np.concatenate([np.concatenate([np.asarray(x) for x in src]), extra_s])
+    dst = np.concatenate([np.concatenate([np.asarray(x) for x in dst]), extra_d])
+    return bcgen.csr_from_edges(n_leaf + 41, src, dst, name="hub+tail")
+
+
+@pytest.mark.parametrize("schedule", ["plain", "batch"])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_exact_bc_small_graphs(ctx, schedule, fp64):
+    for g in graphs_small():
+        G = ctx.create_graph(g.row_ptr, g.col_idx)
+        ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+        got = ctx.exact(G, schedule=schedule, delta_fp64=fp64)
+        assert_bc_close(got, ref, fp64)
+        ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("schedule", ["plain", "batch"])
+def test_depth_and_counts_bit_exact(ctx, schedule):
+    g = bcgen.rmat(10, 8, seed=1)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    srcs = bcgen.sample_sources(g.n, 100, seed=7)  # 64 + ragged 36
+    d, sig, dl = ctx.debug_sources(G, srcs, schedule=schedule, delta_fp64=True)
+    for j, s in enumerate(srcs):
+        od, osig, odl, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, int(s))
+        np.testing.assert_array_equal(d[j], od)
+        np.testing.assert_array_equal(sig[j], osig)
+        nz = odl != 0
+        assert np.array_equal(dl[j][~nz], odl[~nz])
+        np.testing.assert_allclose(dl[j][nz], odl[nz], rtol=1e-12, atol=0)
+    ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("schedule", ["plain", "batch"])
+def test_high_degree_chunks(ctx, schedule):
+    g = hub_graph()
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    srcs = np.array([0, 1, 2, 3000, 5, 3001, 17, 0], dtype=np.int32)  # hub twice
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    got = ctx.sources(G, srcs, schedule=schedule, delta_fp64=True)
+    assert_bc_close(got, ref, True)
+    assert ctx.last_stats()["heavy_chunks"] > 0
+    d, sig, _ = ctx.debug_sources(G, srcs[:3], schedule=schedule, delta_fp64=True)
+    for j, s in enumerate(srcs[:3]):
+        od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, int(s))
+        np.testing.assert_array_equal(d[j], od)
+        np.testing.assert_array_equal(sig[j], osig)
+    ref_all, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    assert_bc_close(ctx.exact(G, schedule=schedule, delta_fp64=True), ref_all, True)
+    ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("schedule", ["plain", "batch"])
+def test_sigma_overflow(ctx, schedule):
+    import paper_1409_7764_gb300 as bc
+    ok = bcgen.layered_chain(63, 2)
+    G = ctx.create_graph(ok.row_ptr, ok.col_idx)
+    d, sig, _ = ctx.debug_sources(G, [0], schedule=schedule, delta_fp64=True)
+    assert int(sig[0][ok.n - 1]) == 2 ** 63
+    ctx.destroy_graph(G)
+    bad = bcgen.layered_chain(64, 2)
+    G = ctx.create_graph(bad.row_ptr, bad.col_idx)
+    with pytest.raises(bc.BCError) as ei:
+        ctx.sources(G, [0, 1], schedule=schedule)
+    assert ei.value.status == bc.BC_ERR_SIGMA_OVERFLOW
+    assert ei.value.stats["overflow_sources"] == 1
+    # saturated counts still match the oracle's saturating counts bit for bit
+    d, sig, _ = ctx.debug_sources(G, [0], schedule=schedule, delta_fp64=True)
+    od, osig, _, ovf = oracle.single_source(bad.n, bad.row_ptr, bad.col_idx, 0)
+    assert ovf
+    np.testing.assert_array_equal(d[0], od)
+    np.testing.assert_array_equal(sig[0], osig)
+    ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_sampled_sources_ragged_and_duplicates(ctx, fp64):
+    g = bcgen.rmat(12, 16, seed=3)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    srcs = np.concatenate([bcgen.sample_sources(g.n, 150, seed=11), [3, 3, 3]]).astype(np.int32)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    got = ctx.sources(G, srcs, delta_fp64=fp64)
+    assert_bc_close(got, ref, fp64)
+    scaled = ctx.sources(G, srcs, delta_fp64=fp64, scale_sampled=True)
+    np.testing.assert_allclose(scaled, got * g.n / len(srcs), rtol=1e-15)
+    normed = ctx.sources(G, srcs, delta_fp64=fp64, normalize=True)
+    np.testing.assert_allclose(normed, oracle.normalise(got, g.n), rtol=1e-15)
+    ctx.destroy_graph(G)
+
+
+def test_edge_cases(ctx):
+    import paper_1409_7764_gb300 as bc
+    # single vertex, no edges
+    G = ctx.create_graph([0, 0], [])
+    assert ctx.exact(G).tolist() == [0.0]
+    ctx.destroy_graph(G)
+    # edgeless graph
+    G = ctx.create_graph([0] * 6, [])
+    assert ctx.exact(G, schedule="plain").tolist() == [0.0] * 5
+    assert ctx.exact(G, schedule="batch").tolist() == [0.0] * 5
+    ctx.destroy_graph(G)
+    # empty source list
+    g = bcgen.rmat(6, 4, seed=2)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    assert not ctx.sources(G, []).any()
+    with pytest.raises(bc.BCError) as ei:
+        ctx.sources(G, [g.n])
+    assert ei.value.status == bc.BC_ERR_ARG
+    ctx.destroy_graph(G)
+    # malformed CSR
+    with pytest.raises(bc.BCError) as ei:
+        ctx.create_graph([0, 2, 1, 2], [1, 2], n=3)
+    assert ei.value.status == bc.BC_ERR_GRAPH
+    with pytest.raises(bc.BCError) as ei:
+        ctx.create_graph([0, 1, 1, 2], [1, 7], n=3)
+    assert ei.value.status == bc.BC_ERR_GRAPH
+
+
+def test_canonicalisation_in_library(ctx):
+    rs = np.random.default_rng(5)
+    n = 300
+    src = rs.integers(0, n, 3000)
+    dst = rs.integers(0, n, 3000)
+    src = np.concatenate([src, src[:500], np.arange(50)])
+    dst = np.concatenate([dst, dst[:500], np.arange(50)])
+    raw = bcgen.raw_csr_from_edges(n, src, dst)
+    canon = bcgen.csr_from_edges(n, src, dst)
+    G = ctx.create_graph(raw.row_ptr, raw.col_idx)
+    assert G.m == canon.m
+    ref, _ = oracle.bc(n, canon.row_ptr, canon.col_idx)
+    assert_bc_close(ctx.exact(G, delta_fp64=True), ref, True)
+    ctx.destroy_graph(G)
+
+
+def test_deterministic_and_batch_width_independent(ctx):
+    g = bcgen.rmat(11, 16, seed=9)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    a = ctx.exact(G, delta_fp64=False).copy()
+    b = ctx.exact(G, delta_fp64=False).copy()
+    assert np.array_equal(a, b)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    for kb in (1, 7, 32, 64):
+        assert_bc_close(ctx.exact(G, delta_fp64=True, batch_k=kb), ref, True)
+    ctx.destroy_graph(G)
+
+
+def test_device_output(ctx):
+    torch = pytest.importorskip("torch")
+    g = bcgen.rmat(9, 8, seed=4)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    ctx.exact(G, out=out, delta_fp64=True)
+    torch.cuda.synchronize()
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    assert_bc_close(out.cpu().numpy(), ref, True)
+    ctx.destroy_graph(G)
+
+
+def test_failure_injection_times_out_and_recovers(ctx):
+    """One thread block skips its barrier arrival: the others give up after
+    the short limit, the call reports BC_ERR_TIMEOUT, and the next call on
+    the same context is correct."""
+    import paper_1409_7764_gb300 as bc
+    g = bcgen.rmat(9, 8, seed=6)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ctx.inject_barrier_skip(1, 50)
+    with pytest.raises(bc.BCError) as ei:
+        ctx.exact(G, schedule="batch")
+    assert ei.value.status == bc.BC_ERR_TIMEOUT
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    assert_bc_close(ctx.exact(G, schedule="batch", delta_fp64=True), ref, True)
+    ctx.destroy_graph(G)
