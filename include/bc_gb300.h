@@ -184,6 +184,44 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
  * BC_ERR_TIMEOUT and the context stays usable.  block < 0 disables it. */
 bc_status bc_debug_inject_barrier_skip(bc_ctx *ctx, int32_t block, int32_t timeout_ms);
 
+/* Largest vertex count bc_sources_noalloc accepts. */
+#define BC_NOALLOC_MAX_N 8192
+
+/* BC summed over k sources for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment variant of bc_sources.
+ *
+ * Who needs it: code that may not call cudaMalloc when it needs the result,
+ * e.g. a service running under a device-memory budget reserved at start-up,
+ * a framework whose caching allocator owns all device memory, or a callback
+ * where an allocation could stall on device synchronisation.  The call
+ * allocates nothing: no cudaMalloc / cudaFree / cudaMallocAsync and no
+ * allocating library routine.  Its working state is one fixed array of about
+ * 15 MB compiled into the library, which every GPU that loads the library
+ * holds until the process exits; that array bounds n to BC_NOALLOC_MAX_N.
+ *
+ * Inputs: the graph as DEVICE memory owned by the caller, already canonical
+ * (rows sorted, no duplicate edges, no self-loops): out-CSR row_ptr[n+1],
+ * col_idx[m] and its transpose in_ptr[n+1], in_idx[m] (in-neighbours of v are
+ * in_idx[in_ptr[v] .. in_ptr[v+1])); these are not validated beyond their
+ * sizes.  src: HOST int32[k], each in [0, n) (checked).  delta_fp64 as in
+ * bc_opts.  Output: bc_out, DEVICE float64[n], overwritten with raw sums.
+ * cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * The call returns after the result is written.
+ *
+ * Limits and sharing: n > BC_NOALLOC_MAX_N, m >= 2^31, k < 0, a null pointer
+ * or a source out of range give BC_ERR_ARG before any work.  Every call on a
+ * GPU uses the same array and leaves its contents behind; each call clears
+ * what must start at zero, so sequential calls are independent, but calls
+ * that overlap on the GPU (other host threads, other streams) race on the
+ * array and give wrong results.  High-degree vertices are not split across
+ * warps, so hubs run slower than through bc_sources.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and the
+ * kernel's grid size with that device current; make that first call before
+ * any stream capture. */
+bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *in_ptr,
+                             const int32_t *in_idx, int32_t n, int64_t m, const int32_t *src,
+                             int32_t k, int32_t delta_fp64, double *bc_out, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *bc_status_str(bc_status status);
 

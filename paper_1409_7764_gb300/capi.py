@@ -30,8 +30,10 @@ BC_SCHED_BATCH = 2
 EXPORTED = [
     "bc_init", "bc_shutdown", "bc_create_graph", "bc_destroy_graph", "bc_exact", "bc_sources",
     "bc_submit", "bc_poll", "bc_wait", "bc_last_stats", "bc_debug_source", "bc_debug_sources",
-    "bc_exact_many", "bc_debug_inject_barrier_skip", "bc_status_str",
+    "bc_exact_many", "bc_debug_inject_barrier_skip", "bc_status_str", "bc_sources_noalloc",
 ]
+
+BC_NOALLOC_MAX_N = 8192
 
 
 class bc_opts(ctypes.Structure):
@@ -93,6 +95,7 @@ def load(path: str | None = None):
         "bc_exact_many": ([vp, vp, i32, ctypes.POINTER(bc_opts), vp], ctypes.c_int),
         "bc_debug_inject_barrier_skip": ([vp, i32, i32], ctypes.c_int),
         "bc_status_str": ([ctypes.c_int], ctypes.c_char_p),
+        "bc_sources_noalloc": ([vp, vp, vp, vp, i32, i64, vp, i32, i32, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
