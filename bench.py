@@ -76,31 +76,44 @@ def describe(name, w, g, nsrc):
 
 # ---- bytes model --------------------------------------------------------------
 
-def bytes_model(stats, schedule, delta_bytes):
+def bytes_model(stats, delta_bytes):
     """Algorithmic bytes of the BC kernels for the counters of one job
-    (element granularity, each element the design must touch counted once).
+    (element granularity, each element the design must touch counted once;
+    b = bytes of one dependency value).
 
-    batch: 124 B per frontier entry (queue id/mask, CSR offsets, dense mask
-           read/write/clear, visited, BC read-modify-write), 12 B per scanned
-           edge (column id + the 8-byte mask of the other endpoint),
-           (8 + b) B per (source, DAG edge) (path count of the predecessor,
-           coefficient of the successor), (24 + b) B per (source, reached
-           vertex) (path count write, read, reset; coefficient write).
-    plain: (84 + b) B per entry, 8 B per scanned edge (column + int32 depth),
-           (8 + b) B per DAG edge.
+    dense batch kernel (kernel_kind 3): 24 B per vertex and level (the level's
+           masks scanned forward and backward, then cleared), 72 B per
+           frontier entry (CSR offsets, visited read/write/reset, next-level
+           mask, BC read-modify-write), 12 B per scanned in-edge (column + the
+           predecessor's mask), 16 B per scanned out-edge (column + one or two
+           masks), (8 + b) B per (source, DAG edge) (predecessor path count,
+           successor coefficient), (24 + b) B per (source, reached vertex)
+           (path count write, read, reset; coefficient write).
+    queue batch kernel (2): 124 B per entry (queue id/mask, CSR offsets, dense
+           mask read/write/clear, visited, BC), 12 B per scanned edge, same
+           per-pair terms.
+    plain kernel (1): (84 + b) B per entry, 8 B per scanned edge (column +
+           int32 depth), (8 + b) B per DAG edge.
     """
     E = stats["frontier_entries"]
     I, O = stats["scanned_in_edges"], stats["scanned_out_edges"]
     D, R = stats["dag_pairs"], stats["reached_pairs"]
     b = delta_bytes
-    if schedule == "batch":
+    kind = stats.get("kernel_kind", 2)
+    if kind == 3:
+        return (24 * stats["n"] * stats["levels_sum"] + 72 * E + 12 * I + 16 * O +
+                (8 + b) * D + (24 + b) * R)
+    if kind == 2:
         return 124 * E + 12 * (I + O) + (8 + b) * D + (24 + b) * R
     return (84 + b) * E + 8 * (I + O) + (8 + b) * D
 
 
+KERNEL_NAMES = {1: "plain_kernel", 2: "batch_kernel", 3: "dense_kernel"}
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ["bc_kernels.cu", "bc_internal.cuh"]:
+    for f in ["bc_kernels.cu", "bc_dense.cu", "bc_device.cuh", "bc_internal.cuh"]:
         with open(os.path.join(ROOT, "paper_1409_7764_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -256,8 +269,10 @@ def run_ours(args, w, name):
 
     g = make_graph(w)
     srcs = source_list(w, g.n)
-    shards = np.array_split(srcs, world)
-    mine = shards[rank]
+    if args.max_sources:
+        srcs = srcs[:args.max_sources]
+    from paper_1409_7764_gb300.sharding import reduce_partial_bc, shard_sources
+    mine = shard_sources(srcs, world, rank)
 
     pool = None
     cores = os.cpu_count() or 1
@@ -276,7 +291,7 @@ def run_ours(args, w, name):
     stream = torch.cuda.current_stream()
     ctx = bc.Context(local, stream=stream)
     fp64 = bool(w.get("fp64", False)) or args.fp64
-    opts = dict(schedule=w["schedule"], batch_k=w["batch_k"], delta_fp64=fp64)
+    opts = dict(schedule=args.schedule or w["schedule"], batch_k=w["batch_k"], delta_fp64=fp64)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
     out = torch.zeros(g.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -284,7 +299,7 @@ def run_ours(args, w, name):
     def step():
         ctx.sources(G, mine, out=out, **opts)
         if dist is not None:
-            dist.reduce(out, dst=0)
+            reduce_partial_bc(out, dist, dst=0)
 
     for _ in range(args.warmup):
         step()
@@ -320,7 +335,7 @@ def run_ours(args, w, name):
     # kernel-level roofline of the batch (or plain) kernel on this rank
     st = stats[-1]
     delta_bytes = 8 if fp64 else 4
-    algo_bytes = bytes_model(st, w["schedule"], delta_bytes)
+    algo_bytes = bytes_model(st, delta_bytes)
     launches = max(st["batches"], 1)
     my_ms = sum(step_ms) / args.steps
     achieved = algo_bytes / (my_ms / 1e3) / 1e9
@@ -351,7 +366,7 @@ def run_ours(args, w, name):
     extra = {}
     if rank == 0 and not args.quick:
         # the plain one-source-per-launch path on a sample of the same sources
-        if w["schedule"] == "batch":
+        if opts["schedule"] != "plain":
             sample = mine[:min(len(mine), args.plain_sample)]
             ctx.sources(G, sample[:4], out=out, schedule="plain", delta_fp64=fp64)
             torch.cuda.synchronize()
@@ -392,7 +407,7 @@ def run_ours(args, w, name):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "kernel": f"{w['schedule']}_kernel",
+                         "kernel": KERNEL_NAMES.get(st.get("kernel_kind"), "?"),
                          "algo_bytes_per_launch": algo_bytes / launches,
                          "launch_ms": my_ms / launches},
             "cpu_baseline": cpu,
@@ -402,7 +417,8 @@ def run_ours(args, w, name):
             "clocks": clk,
             "counters": {k: st[k] for k in ("frontier_entries", "scanned_in_edges",
                                             "scanned_out_edges", "dag_pairs", "reached_pairs",
-                                            "heavy_chunks", "max_levels", "batches")},
+                                            "heavy_chunks", "max_levels", "levels_sum",
+                                            "batches", "kernel_kind")},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -423,6 +439,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the plain / precision extras")
+    ap.add_argument("--schedule", default=None,
+                    choices=["plain", "batch", "batch_queue", "batch_dense"],
+                    help="override the workload's schedule")
+    ap.add_argument("--max-sources", type=int, default=0,
+                    help="use only the first N sources of the workload (profiling runs)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

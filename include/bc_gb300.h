@@ -65,8 +65,12 @@ typedef enum {
 /* Work schedules.  AUTO picks per graph. */
 enum {
   BC_SCHED_AUTO = 0,
-  BC_SCHED_PLAIN = 1, /* one source per kernel launch, whole GPU, level-synchronous */
-  BC_SCHED_BATCH = 2  /* up to 64 sources per launch, bitset frontiers, [n][64] state */
+  BC_SCHED_PLAIN = 1,       /* one source per kernel launch, whole GPU, level-synchronous */
+  BC_SCHED_BATCH = 2,       /* up to 64 sources per launch, bitset frontiers, [n][64] state;
+                               the library picks the frontier representation */
+  BC_SCHED_BATCH_QUEUE = 3, /* BATCH with per-level frontier queues */
+  BC_SCHED_BATCH_DENSE = 4  /* BATCH with per-level dense frontier masks (falls back to the
+                               queue form for graphs deeper than its mask array) */
 };
 
 typedef struct {
@@ -94,6 +98,9 @@ typedef struct {
   int64_t dag_pairs;         /* sum over sources of shortest-path DAG edges */
   int64_t reached_pairs;     /* sum over sources of reached vertices (incl. source) */
   int64_t heavy_chunks;      /* edge chunks of high-degree vertices split across warps */
+  int32_t kernel_kind;       /* kernel of the last launch: 1 plain, 2 batch (frontier queue),
+                                3 batch (per-level dense masks) */
+  int32_t levels_sum;        /* BFS level counts summed over all batches */
 } bc_stats;
 
 /* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t

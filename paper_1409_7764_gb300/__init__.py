@@ -28,7 +28,8 @@ __all__ = [
     "BC_SCHED_AUTO", "BC_SCHED_PLAIN", "BC_SCHED_BATCH",
 ]
 
-_SCHED = {"auto": BC_SCHED_AUTO, "plain": BC_SCHED_PLAIN, "batch": BC_SCHED_BATCH}
+_SCHED = {"auto": BC_SCHED_AUTO, "plain": BC_SCHED_PLAIN, "batch": BC_SCHED_BATCH,
+          "batch_queue": capi.BC_SCHED_BATCH_QUEUE, "batch_dense": capi.BC_SCHED_BATCH_DENSE}
 
 
 def load():

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbc_gb300.so")
-SOURCES = ["bc_kernels.cu", "bc_api.cu", "bc_noalloc.cu"]
-HEADERS = ["bc_internal.cuh"]
+SOURCES = ["bc_kernels.cu", "bc_dense.cu", "bc_api.cu", "bc_noalloc.cu"]
+HEADERS = ["bc_internal.cuh", "bc_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I" + INCLUDE, "-I" + CSRC]
@@ -41,8 +41,12 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, out: str | None = None,
+          defines=()) -> str:
+    """Compiles the library to `out` (default: libbc_gb300.so next to this
+    file); `defines` are extra -D macros for tuning variants."""
+    target = out or LIB
+    if out is None and not force and not stale():
         return LIB
     nvcc = _nvcc()
     objdir = os.path.join(HERE, "_build")
@@ -51,7 +55,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.splitext(src)[0] + f".{pid}.o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + NVCC_FLAGS + [f"-D{d}" for d in defines] + [
+            "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.append("-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,15 +68,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{pid}"
+    tmp = target + f".tmp{pid}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, target)
     for o in objs:
         os.remove(o)
-    return LIB
+    return target
 
 
 if __name__ == "__main__":

@@ -25,6 +25,8 @@ BC_ERR_INTERNAL = -9
 BC_SCHED_AUTO = 0
 BC_SCHED_PLAIN = 1
 BC_SCHED_BATCH = 2
+BC_SCHED_BATCH_QUEUE = 3
+BC_SCHED_BATCH_DENSE = 4
 
 # every symbol include/bc_gb300.h declares
 EXPORTED = [
@@ -49,7 +51,8 @@ class bc_stats(ctypes.Structure):
                 ("device_ms", ctypes.c_double), ("frontier_entries", ctypes.c_int64),
                 ("scanned_out_edges", ctypes.c_int64), ("scanned_in_edges", ctypes.c_int64),
                 ("dag_pairs", ctypes.c_int64), ("reached_pairs", ctypes.c_int64),
-                ("heavy_chunks", ctypes.c_int64)]
+                ("heavy_chunks", ctypes.c_int64), ("kernel_kind", ctypes.c_int32),
+                ("levels_sum", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -64,8 +67,8 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _build.LIB
-    if not os.path.exists(path) or _build.stale():
+    path = path or os.environ.get("BC_GB300_LIB") or _build.LIB
+    if path == _build.LIB and (not os.path.exists(path) or _build.stale()):
         try:
             _build.build()
         except Exception as exc:  # no silent fallback

@@ -19,6 +19,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -71,11 +72,16 @@ struct GraphRec {
   void *mem = nullptr;
   size_t bytes = 0;
   int active_jobs = 0;
+  std::atomic<bool> deep{false}; // more BFS levels than the dense kernel's masks hold
 };
+
+enum WsKind { WS_PLAIN = 0, WS_QUEUE = 1, WS_DENSE = 2 };
 
 struct WsRec {
   bool batch = true;
+  int kind = WS_QUEUE;
   int32_t n = 0;
+  int32_t dmax = 0;
   int64_t cap = 0, hcap = 0, chunk_cap = 0;
   Work w;
   void *mem = nullptr;
@@ -84,21 +90,26 @@ struct WsRec {
 };
 
 struct WsNeed {
-  bool batch;
+  int kind;
   int32_t n;
+  int32_t dmax;
   int64_t cap, hcap, chunk_cap;
   bool fits(const WsRec &r) const {
-    return r.batch == batch && r.n >= n && r.cap >= cap && r.hcap >= hcap &&
-           r.chunk_cap >= chunk_cap;
+    if (r.kind != kind || r.n < n || r.hcap < hcap || r.chunk_cap < chunk_cap) return false;
+    return kind == WS_DENSE ? r.dmax >= dmax : r.cap >= cap;
   }
 };
 
-WsNeed ws_need(const GraphDev &g, bool batch, int kb) {
+// Levels the dense kernel's per-level masks hold for an n-vertex graph.
+int32_t dense_levels(int32_t n) { return n <= (1 << 22) ? kDenseLevels : kDenseLevels / 2; }
+
+WsNeed ws_need(const GraphDev &g, int kind, int kb) {
   WsNeed nd;
-  nd.batch = batch;
+  nd.kind = kind;
   nd.n = g.n;
-  const int64_t kk = batch ? kb : 1;
-  nd.cap = std::max<int64_t>(1, (int64_t)g.n * kk);
+  nd.dmax = kind == WS_DENSE ? dense_levels(g.n) : 0;
+  const int64_t kk = kind == WS_PLAIN ? 1 : kb;
+  nd.cap = kind == WS_DENSE ? 1 : std::max<int64_t>(1, (int64_t)g.n * kk);
   nd.hcap = std::max<int64_t>(1, g.heavy_vertices * kk);
   nd.chunk_cap = std::max<int64_t>(1, g.heavy_chunks);
   return nd;
@@ -111,9 +122,28 @@ size_t ws_layout(WsRec &r, char *mem) {
   const size_t n = (size_t)r.n;
   const size_t kk = r.batch ? kK : 1;
   Work &w = r.w;
+  w = Work();
   w.n = r.n;
   w.k_max = (int32_t)kk;
   w.ctl = c.take<Ctl>(1);
+  if (r.kind == WS_DENSE) {
+    w.vis = c.take<uint64_t>(n);
+    w.lm = c.take<uint64_t>((size_t)r.dmax * n);
+    w.dmax = r.dmax;
+    w.lvl_flag = c.take<unsigned>((size_t)r.dmax + 2);
+    w.hpack = c.take<unsigned long long>((size_t)r.dmax + 3);
+    w.hoff = c.take<int64_t>((size_t)r.dmax + 3);
+    w.hq_e = c.take<int64_t>((size_t)r.hcap);
+    w.hq_c = c.take<int64_t>((size_t)r.hcap);
+    w.harrive = c.take<unsigned>((size_t)r.hcap);
+    w.hcap = r.hcap;
+    w.partial = c.take<uint64_t>((size_t)r.chunk_cap * kk);
+    w.partial_ovf = c.take<uint64_t>((size_t)r.chunk_cap);
+    w.chunk_cap = r.chunk_cap;
+    w.sigma = c.take<uint64_t>(n * kk);
+    w.cdep = c.take<double>(n * kk);
+    return align_up(c.off, 256);
+  }
   if (r.batch) {
     w.vis = c.take<uint64_t>(n);
     w.fr = c.take<uint64_t>(4 * n);
@@ -162,6 +192,7 @@ struct bc_ctx {
   std::atomic<size_t> used{0};
   int sm_count = 0;
   int grid_batch[2] = {0, 0}; // [fp64]
+  int grid_dense[2] = {0, 0};
   int grid_plain[2] = {0, 0};
 
   std::mutex mu;
@@ -209,13 +240,20 @@ struct JobRec {
   int *h_err = nullptr;
   int8_t *h_ovf = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evdone = nullptr;
+  unsigned long long *d_trace = nullptr; // per-step trace of one batch (BC_TRACE)
+  unsigned long long *h_trace = nullptr;
+  int64_t trace_batch = -1;
   int64_t launches = 0;
   int64_t batches = 0;
+  int kind = 0;              // workspace / kernel kind of the last launch
   size_t footprint = 0;
   bc_status status = BC_PENDING;
   bc_stats stats{};
   bool done = false;
 };
+
+// internal: the job must be launched again (dense kernel ran out of levels)
+constexpr bc_status kStatusRetry = static_cast<bc_status>(100);
 
 bc_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return BC_OK;
@@ -237,7 +275,7 @@ bc_opts default_opts() {
 
 bool opts_valid(const bc_opts &o) {
   return (o.delta_fp64 == 0 || o.delta_fp64 == 1) && o.batch_k >= 0 && o.batch_k <= kK &&
-         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH &&
+         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_DENSE &&
          (o.normalize == 0 || o.normalize == 1) &&
          (o.scale_sampled == 0 || o.scale_sampled == 1) &&
          (o.out_device == 0 || o.out_device == 1);
@@ -250,10 +288,17 @@ int resolve_schedule(const bc_opts &o, const GraphDev &) {
 
 int resolve_batch_k(const bc_opts &o) { return o.batch_k == 0 ? kK : o.batch_k; }
 
+// Frontier representation for BC_SCHED_BATCH: the queue form measured faster
+// than the dense-level form on every workload tried (R-MAT scales 16 and 20,
+// directed preferential attachment n = 2^20), so it is the default.
+int pick_batch_kind(const GraphDev &) { return WS_QUEUE; }
+
 // Grid of a persistent launch: the co-resident maximum for large graphs, a
 // smaller share of the GPU for small ones so that concurrent jobs overlap.
-int pick_grid(const bc_ctx *ctx, const GraphDev &g, bool batch, bool fp64) {
-  const int gmax = batch ? ctx->grid_batch[fp64] : ctx->grid_plain[fp64];
+int pick_grid(const bc_ctx *ctx, const GraphDev &g, int kind, bool fp64) {
+  const int gmax = kind == WS_DENSE   ? ctx->grid_dense[fp64]
+                   : kind == WS_QUEUE ? ctx->grid_batch[fp64]
+                                      : ctx->grid_plain[fp64];
   if (const char *env = std::getenv("BC_GRID")) {
     int v = std::atoi(env);
     if (v > 0) return std::min(v, gmax);
@@ -396,7 +441,9 @@ bc_status ws_acquire(bc_ctx *ctx, const WsNeed &nd, cudaStream_t st, std::unique
     return BC_OK;
   }
   auto r = std::make_unique<WsRec>();
-  r->batch = nd.batch;
+  r->kind = nd.kind;
+  r->batch = nd.kind != WS_PLAIN;
+  r->dmax = nd.dmax;
   r->n = nd.n;
   r->cap = nd.cap;
   r->hcap = nd.hcap;
@@ -440,8 +487,13 @@ void ws_release(bc_ctx *ctx, std::unique_ptr<WsRec> ws) {
 
 size_t job_footprint(const GraphDev &g, int sched, int kb, int64_t k) {
   WsRec r;
-  WsNeed nd = ws_need(g, sched == BC_SCHED_BATCH, kb);
-  r.batch = nd.batch;
+  const int kind = sched == BC_SCHED_PLAIN         ? WS_PLAIN
+                   : sched == BC_SCHED_BATCH_DENSE ? WS_DENSE
+                                                   : WS_QUEUE;
+  WsNeed nd = ws_need(g, kind, kb);
+  r.kind = nd.kind;
+  r.batch = nd.kind != WS_PLAIN;
+  r.dmax = nd.dmax;
   r.n = nd.n;
   r.cap = nd.cap;
   r.hcap = nd.hcap;
@@ -465,6 +517,10 @@ void job_free_buffers(JobRec *j) {
   j->h_cnt = nullptr;
   j->h_ovf = nullptr;
   j->h_err = nullptr;
+  if (j->d_trace) cudaFreeAsync(j->d_trace, j->st);
+  if (j->h_trace) cudaFreeHost(j->h_trace);
+  j->d_trace = nullptr;
+  j->h_trace = nullptr;
   if (j->ev0) cudaEventDestroy(j->ev0);
   if (j->ev1) cudaEventDestroy(j->ev1);
   if (j->evdone) cudaEventDestroy(j->evdone);
@@ -483,13 +539,20 @@ struct DebugOut {
 bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   const GraphDev &g = j->g->dev;
   const int sched = resolve_schedule(j->opts, g);
-  const bool batch = sched == BC_SCHED_BATCH;
+  const bool batch = sched != BC_SCHED_PLAIN;
   const bool fp64 = j->opts.delta_fp64 != 0;
   const int kb = batch ? resolve_batch_k(j->opts) : 1;
   const int64_t n = g.n, k = j->k;
   cudaStream_t st = j->st;
+  // batches run on the dense-level kernel unless the graph is known to be
+  // deeper than its per-level masks; then on the queue kernel
+  const int kind = !batch                             ? WS_PLAIN
+                   : sched == BC_SCHED_BATCH_QUEUE || j->g->deep ? WS_QUEUE
+                   : sched == BC_SCHED_BATCH_DENSE               ? WS_DENSE
+                                                                 : pick_batch_kind(j->g->dev);
+  j->kind = kind;
 
-  bc_status s = ws_acquire(ctx, ws_need(g, batch, kb), st, j->ws);
+  bc_status s = ws_acquire(ctx, ws_need(g, kind, kb), st, j->ws);
   if (s != BC_OK) return s;
   BC_TRY(cudaMallocHost(&j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
   BC_TRY(cudaMallocHost(&j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
@@ -523,8 +586,17 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
     p.timeout_ns = (long long)ctx->inject_timeout_ms * 1000000LL;
     ctx->inject_block = -1;
   }
-  const int grid = pick_grid(ctx, g, batch, fp64);
+  const int grid = pick_grid(ctx, g, kind, fp64);
   if (grid <= 0) return BC_ERR_CUDA;
+  constexpr int kTraceCap = 8192;
+  if (const char *tr = std::getenv("BC_TRACE")) {
+    // per-step timing of one batch (index BC_TRACE, -1 = last) to stderr
+    j->trace_batch = std::atoll(tr);
+    if (j->trace_batch < 0) j->trace_batch = (k + kb - 1) / kb - 1;
+    BC_TRY(cudaMallocAsync(&j->d_trace, sizeof(unsigned long long) * 4 * kTraceCap, st));
+    BC_TRY(cudaMemsetAsync(j->d_trace, 0, sizeof(unsigned long long) * 4 * kTraceCap, st));
+    BC_TRY(cudaMallocHost(&j->h_trace, sizeof(unsigned long long) * 4 * kTraceCap));
+  }
   BC_TRY(cudaEventRecord(j->ev0, st));
   j->batches = 0;
   j->launches = 0;
@@ -532,12 +604,16 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
     p.src = j->d_src + b0;
     p.k = (int32_t)std::min<int64_t>(kb, k - b0);
     p.src_base = b0;
+    p.trace = (j->d_trace && b0 / kb == j->trace_batch) ? j->d_trace : nullptr;
+    p.trace_cap = p.trace ? kTraceCap : 0;
     if (dbg) {
       p.dbg_d = dbg->d + b0 * n;
       p.dbg_sigma = dbg->sigma + b0 * n;
       p.dbg_delta = dbg->delta + b0 * n;
     }
-    BC_TRY(batch ? launch_batch(p, fp64, grid, st) : launch_plain(p, fp64, grid, st));
+    BC_TRY(kind == WS_DENSE   ? launch_dense(p, fp64, grid, st)
+           : kind == WS_QUEUE ? launch_batch(p, fp64, grid, st)
+                              : launch_plain(p, fp64, grid, st));
     ++j->batches;
     ++j->launches;
   }
@@ -557,6 +633,9 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   BC_TRY(cudaMemcpyAsync(j->h_cnt, j->d_cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
   BC_TRY(cudaMemcpyAsync(j->h_err, &j->ws->w.ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (k) BC_TRY(cudaMemcpyAsync(j->h_ovf, j->d_ovf, (size_t)k, cudaMemcpyDeviceToHost, st));
+  if (j->d_trace)
+    BC_TRY(cudaMemcpyAsync(j->h_trace, j->d_trace, sizeof(unsigned long long) * 4 * kTraceCap,
+                           cudaMemcpyDeviceToHost, st));
   BC_TRY(cudaEventRecord(j->evdone, st));
   return BC_OK;
 }
@@ -579,12 +658,31 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.reached_pairs = (int64_t)j->h_cnt[CNT_REACHED];
   s.heavy_chunks = (int64_t)j->h_cnt[CNT_HEAVY];
   s.max_levels = (int32_t)j->h_cnt[CNT_MAXLEV];
+  s.kernel_kind = j->kind == WS_DENSE ? 3 : j->kind == WS_QUEUE ? 2 : 1;
+  s.levels_sum = (int32_t)j->h_cnt[CNT_LEVELS];
   int32_t novf = 0;
   for (int64_t i = 0; i < j->k; ++i) novf += j->h_ovf[i] ? 1 : 0;
+  if (j->h_trace) {
+    std::fprintf(stderr, "# trace batch %lld: step level items heavy_chunks us\n",
+                 (long long)j->trace_batch);
+    for (int i = 0; i + 1 < 8192 && j->h_trace[4 * i]; ++i) {
+      const unsigned long long *t = j->h_trace + 4 * i;
+      const long long lvl = (long long)t[1];
+      if (lvl == (1 << 20)) break;
+      const double us = t[4] ? (double)(t[4] - t[0]) / 1000.0 : 0.0;
+      std::fprintf(stderr, "%d %lld %llu %llu %.2f\n", i, lvl, t[2], t[3], us);
+    }
+  }
   s.overflow_sources = novf;
   bc_status st = BC_OK;
   const int kerr = *j->h_err;
-  if (kerr != KERR_NONE) {
+  if (kerr == KERR_LEVELS) {
+    // deeper than the dense kernel's masks: no BC was written; rerun the job
+    // on the queue kernel
+    j->g->deep = true;
+    st = kStatusRetry;
+    j->ws->dirty = true;
+  } else if (kerr != KERR_NONE) {
     st = kerr == KERR_TIMEOUT ? BC_ERR_TIMEOUT : BC_ERR_INTERNAL;
     j->ws->dirty = true;
   } else if (novf) {
@@ -606,22 +704,26 @@ bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool
   j.all_sources = all;
   if (!all && k) j.src.assign(src, src + k);
   j.st = ctx->stream;
-  bc_status s = job_launch(ctx, &j, out, dbg);
-  if (s != BC_OK) {
-    cudaStreamSynchronize(j.st);
-    if (j.ws) {
-      j.ws->dirty = true;
-      ws_release(ctx, std::move(j.ws));
+  bc_status s = kStatusRetry;
+  for (int attempt = 0; attempt < 2 && s == kStatusRetry; ++attempt) {
+    s = job_launch(ctx, &j, out, dbg);
+    if (s != BC_OK) {
+      cudaStreamSynchronize(j.st);
+      if (j.ws) {
+        j.ws->dirty = true;
+        ws_release(ctx, std::move(j.ws));
+      }
+      job_free_buffers(&j);
+      return s;
     }
-    job_free_buffers(&j);
-    return s;
+    cudaError_t e = cudaEventSynchronize(j.evdone);
+    if (e != cudaSuccess) {
+      job_free_buffers(&j);
+      return cuda_status(e);
+    }
+    s = job_finish(ctx, &j);
   }
-  cudaError_t e = cudaEventSynchronize(j.evdone);
-  if (e != cudaSuccess) {
-    job_free_buffers(&j);
-    return cuda_status(e);
-  }
-  s = job_finish(ctx, &j);
+  if (s == kStatusRetry) s = BC_ERR_INTERNAL;
   ctx->last = j.stats;
   return s;
 }
@@ -684,6 +786,20 @@ void scheduler_loop(bc_ctx *ctx) {
       if (cudaEventQuery(j->evdone) == cudaSuccess) {
         lk.unlock();
         bc_status s = job_finish(ctx, j);
+        if (s == kStatusRetry) {
+          s = job_launch(ctx, j, j->h_out, nullptr);
+          if (s == BC_OK) {
+            lk.lock();
+            ++i;
+            continue;
+          }
+          cudaStreamSynchronize(j->st);
+          if (j->ws) {
+            j->ws->dirty = true;
+            ws_release(ctx, std::move(j->ws));
+          }
+          job_free_buffers(j);
+        }
         lk.lock();
         j->status = s;
         j->done = true;
@@ -752,8 +868,10 @@ bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx
   BC_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
   for (int f = 0; f < 2; ++f) {
     ctx->grid_batch[f] = max_grid_batch(f != 0, device);
+    ctx->grid_dense[f] = max_grid_dense(f != 0, device);
     ctx->grid_plain[f] = max_grid_plain(f != 0, device);
-    if (ctx->grid_batch[f] <= 0 || ctx->grid_plain[f] <= 0) return BC_ERR_CUDA;
+    if (ctx->grid_batch[f] <= 0 || ctx->grid_plain[f] <= 0 || ctx->grid_dense[f] <= 0)
+      return BC_ERR_CUDA;
   }
   for (int i = 0; i < kMaxSlots; ++i)
     BC_TRY(cudaStreamCreateWithFlags(&ctx->slot_stream[i], cudaStreamNonBlocking));

@@ -1,0 +1,389 @@
+// Device helpers shared by the kernel translation units of the GB300
+// betweenness-centrality library: L2-coherent loads, a time-bounded grid
+// barrier, saturating path-count adds, chunk arrival tickets, warp helpers and
+// the optional per-step trace.
+#pragma once
+
+#include "bc_internal.cuh"
+
+namespace bcgpu {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void set_err(Ctl *ctl, int code) { atomicCAS(&ctl->err, 0, code); }
+
+__device__ __forceinline__ int read_err(const Ctl *ctl) {
+  return *reinterpret_cast<const volatile int *>(&ctl->err);
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// wait is bounded by timeout_ns; on expiry the CTA records KERR_TIMEOUT and
+// continues, and every CTA then leaves the kernel at its next error check.
+// When snap_dst is given, the last CTA to arrive copies the queue tail there
+// before releasing the others: once every CTA has arrived no enqueue of the
+// finished level can still be in flight, so the copy is that level's final
+// end, and unlike the live tail (which the next level's enqueues advance) it
+// reads the same in every CTA.  Returns false when the job is in an error
+// state.
+__device__ bool grid_sync(Ctl *ctl, long long timeout_ns, int64_t *snap_dst = nullptr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *genp = &ctl->bar_gen;
+    const unsigned gen = *genp;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      if (snap_dst) *snap_dst = (int64_t)atomicAdd(&ctl->tail, 0ull);
+      ctl->bar_count = 0;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*genp == gen) {
+        if (read_err(ctl)) break;
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
+          set_err(ctl, KERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return read_err(ctl) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// batched kernel: up to 64 sources, bitset frontiers
+// ---------------------------------------------------------------------------
+
+template <typename DT> __device__ __forceinline__ DT u64_to(uint64_t x);
+template <> __device__ __forceinline__ float u64_to<float>(uint64_t x) { return __ull2float_rn(x); }
+template <> __device__ __forceinline__ double u64_to<double>(uint64_t x) { return __ull2double_rn(x); }
+
+// saturating add: on carry the sum pins at 2^64-1 and the flag is raised
+__device__ __forceinline__ void sat_add(uint64_t &acc, uint64_t x, bool &ovf) {
+  uint64_t s = acc + x;
+  if (s < x) {
+    s = ~0ull;
+    ovf = true;
+  }
+  acc = s;
+}
+
+// Arrival ticket of a heavy-entry chunk: every lane's partial writes are
+// fenced, the warp converges, lane 0 takes the ticket, and after the
+// broadcast every lane fences again so the last arriver reads all partials.
+__device__ __forceinline__ unsigned chunk_ticket(unsigned *arrive, int lane) {
+  __threadfence();
+  __syncwarp();
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(arrive, 1u);
+  t = __shfl_sync(kFull, t, 0);
+  __threadfence();
+  return t;
+}
+
+struct Counters {
+  unsigned long long entries = 0, out_e = 0, in_e = 0, dag = 0, reached = 0, heavy = 0;
+};
+
+// Up to four set lanes of a ballot, in lane order; missing ones are -1.
+struct Lanes4 {
+  int l[4];
+  __device__ __forceinline__ explicit Lanes4(unsigned &bal) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      l[i] = bal ? __ffs(bal) - 1 : -1;
+      bal &= bal - 1;
+    }
+  }
+};
+
+template <typename T> __device__ __forceinline__ T shfl_or_zero(T v, int src) {
+  return src >= 0 ? __shfl_sync(kFull, v, src) : T(0);
+}
+
+// Optional per-step trace (block 0, thread 0): globaltimer at the start of
+// the step, the step's level (negative = backward), items and heavy chunks.
+__device__ __forceinline__ void trace_step(const KParams &p, int step, int lvl, int64_t items,
+                                           int64_t nhc, int64_t gtid) {
+  if (p.trace && gtid == 0 && step < p.trace_cap) {
+    unsigned long long *t = p.trace + 4 * (size_t)step;
+    t[0] = globaltimer_ns();
+    t[1] = (unsigned long long)(long long)lvl;
+    t[2] = (unsigned long long)items;
+    t[3] = (unsigned long long)nhc;
+  }
+}
+
+template <typename DT> __device__ __forceinline__ DT warp_sum(DT v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
+  return v;
+}
+
+// Up to four set bits of a mask, lowest first (-1 when exhausted); clears them.
+struct Bits4 {
+  int j[4];
+  __device__ __forceinline__ explicit Bits4(uint64_t &m) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      j[k] = m ? __ffsll((long long)m) - 1 : -1;
+      m &= m - 1;
+    }
+  }
+};
+
+// Adds row[j] into acc[j] for every bit j of P (shared-memory atomics, up to
+// four loads in flight per lane); carries out of 64 bits are recorded in ovf.
+__device__ __forceinline__ void gather_counts(const uint64_t *row, uint64_t P,
+                                              unsigned long long *acc, uint64_t &ovf) {
+  while (P) {
+    const Bits4 q(P);
+    uint64_t x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = q.j[k] >= 0 ? ldcg(row + q.j[k]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (q.j[k] >= 0) {
+        const unsigned long long old = atomicAdd(acc + q.j[k], (unsigned long long)x[k]);
+        if (old + x[k] < old) ovf |= 1ull << q.j[k];
+      }
+  }
+}
+
+// Adds row[j] into acc[j] for every bit j of S (floating-point shared atomics).
+template <typename DT>
+__device__ __forceinline__ void gather_coeffs(const DT *row, uint64_t S, DT *acc) {
+  while (S) {
+    const Bits4 q(S);
+    DT y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y[k] = q.j[k] >= 0 ? ldcg(row + q.j[k]) : DT(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (q.j[k] >= 0) atomicAdd(acc + q.j[k], y[k]);
+  }
+}
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v |= __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+#ifndef BC_GATHER_UNROLL
+#define BC_GATHER_UNROLL 4 // DAG edges gathered per round (lanes-per-source form)
+#endif
+#ifndef BC_GATHER_BY_EDGE
+#define BC_GATHER_BY_EDGE 0 // 1: lanes take edges and add through shared-memory atomics
+#endif
+
+// Up to U set lanes of a ballot, in lane order; missing ones are -1.
+template <int U> struct LanesU {
+  int l[U];
+  __device__ __forceinline__ explicit LanesU(unsigned &bal) {
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      l[i] = bal ? __ffs(bal) - 1 : -1;
+      bal &= bal - 1;
+    }
+  }
+};
+
+// Batch: path-count pull over in-edges [eb, ee) of entry w (mask F) from the
+// level l-1 dense mask Pm.  Returns the counts of sources lane and lane+32,
+// saturated at 2^64-1 on carry.
+//   lanes-per-source form: lane j owns sources j and j+32; per round the warp
+//     gathers the predecessor rows of BC_GATHER_UNROLL shortest-path edges
+//     (coalesced row segments) and adds them in edge order;
+//   lanes-per-edge form: lanes take edges and add the predecessor's counts
+//     into the warp's shared row wacc[64] with integer atomics.
+__device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, int64_t eb,
+                                                 int64_t ee, const uint64_t *Pm, int lane,
+                                                 unsigned long long *wacc, uint64_t &s0,
+                                                 uint64_t &s1, bool &o0, bool &o1,
+                                                 unsigned long long &dag) {
+#if BC_GATHER_BY_EDGE
+  wacc[lane] = 0;
+  wacc[lane + 32] = 0;
+  __syncwarp();
+  uint64_t ovf = 0;
+  unsigned long long nd = 0;
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    if (e < ee) {
+      const int u = __ldg(p.g.in_idx + e);
+      const uint64_t P = ldcg(Pm + u) & F;
+      nd += __popcll(P);
+      gather_counts(p.w.sigma + (size_t)u * kK, P, wacc, ovf);
+    }
+  }
+  __syncwarp();
+  ovf = warp_or64(ovf);
+  nd = warp_sum_u64(nd);
+  if (lane == 0) dag += nd;
+  s0 = wacc[lane];
+  s1 = wacc[lane + 32];
+  o0 = o0 || ((ovf >> lane) & 1ull);
+  o1 = o1 || ((ovf >> (lane + 32)) & 1ull);
+  if (o0) s0 = ~0ull;
+  if (o1) s1 = ~0ull;
+  __syncwarp();
+#else
+  (void)wacc;
+  constexpr int U = BC_GATHER_UNROLL;
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    int u = 0;
+    uint64_t P = 0;
+    if (e < ee) {
+      u = __ldg(p.g.in_idx + e);
+      P = ldcg(Pm + u) & F;
+    }
+    unsigned bal = __ballot_sync(kFull, P != 0);
+    while (bal) {
+      const LanesU<U> q(bal);
+      uint64_t x0[U], x1[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int uu = shfl_or_zero(u, q.l[i]);
+        const uint64_t PP = shfl_or_zero(P, q.l[i]);
+        const uint64_t *row = p.w.sigma + (size_t)uu * kK;
+        x0[i] = ((PP >> lane) & 1ull) ? ldcg(row + lane) : 0ull;
+        x1[i] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : 0ull;
+        if (lane == 0) dag += __popcll(PP);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        sat_add(s0, x0[i], o0);
+        sat_add(s1, x1[i], o1);
+      }
+    }
+  }
+#endif
+}
+
+// Batch: dependency pull over out-edges [eb, ee) of entry v (mask F) from
+// the level l+1 dense mask Dn (same two forms; the lanes-per-source form adds
+// successor coefficients in edge order, the lanes-per-edge form through
+// floating-point shared atomics whose order may vary between runs).
+template <typename DT>
+__device__ __forceinline__ void batch_pull_delta(const KParams &p, uint64_t F, int64_t eb,
+                                                 int64_t ee, const uint64_t *Dn, int lane,
+                                                 DT *wacc, DT &a0, DT &a1) {
+  const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
+#if BC_GATHER_BY_EDGE
+  wacc[lane] = DT(0);
+  wacc[lane + 32] = DT(0);
+  __syncwarp();
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    if (e < ee) {
+      const int x = __ldg(p.g.col_idx + e);
+      const uint64_t S = ldcg(Dn + x) & F;
+      gather_coeffs<DT>(cdep + (size_t)x * kK, S, wacc);
+    }
+  }
+  __syncwarp();
+  a0 = wacc[lane];
+  a1 = wacc[lane + 32];
+  __syncwarp();
+#else
+  (void)wacc;
+  constexpr int U = BC_GATHER_UNROLL;
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    int x = 0;
+    uint64_t S = 0;
+    if (e < ee) {
+      x = __ldg(p.g.col_idx + e);
+      S = ldcg(Dn + x) & F;
+    }
+    unsigned bal = __ballot_sync(kFull, S != 0);
+    while (bal) {
+      const LanesU<U> q(bal);
+      DT y0[U], y1[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int xx = shfl_or_zero(x, q.l[i]);
+        const uint64_t SS = shfl_or_zero(S, q.l[i]);
+        const DT *row = cdep + (size_t)xx * kK;
+        y0[i] = ((SS >> lane) & 1ull) ? ldcg(row + lane) : DT(0);
+        y1[i] = ((SS >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : DT(0);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        if (q.l[i] >= 0) {
+          a0 += y0[i];
+          a1 += y1[i];
+        }
+      }
+    }
+  }
+#endif
+}
+
+// Batch: writes the path counts of entry w (mask F) and records overflow.
+__device__ __forceinline__ void batch_store_sigma(const KParams &p, int w, uint64_t F,
+                                                  uint64_t s0, uint64_t s1, bool o0, bool o1,
+                                                  int lane) {
+  uint64_t *row = p.w.sigma + (size_t)w * kK;
+  if ((F >> lane) & 1ull) row[lane] = s0;
+  if ((F >> (lane + 32)) & 1ull) row[32 + lane] = s1;
+  const uint64_t ob =
+      ((uint64_t)__ballot_sync(kFull, o0) | ((uint64_t)__ballot_sync(kFull, o1) << 32)) & F;
+  if (ob && lane == 0) atomicOr(&p.w.ctl->ovf, (unsigned long long)ob);
+}
+
+// Last heavy entry h in [base, base+cnt) whose first chunk hq_c[h] <= item:
+// a 32-ary search (each round the lanes probe 32 evenly spaced entries), so
+// a level with up to 32^3 heavy entries needs at most three L2 round trips.
+// hq_c strictly increases with h and hq_c[base] == 0.
+__device__ int64_t warp_find_heavy(const int64_t *hq_c, int64_t base, int64_t cnt, int64_t item,
+                                   int lane) {
+  int64_t lo = 0, hi = cnt;
+  while (hi - lo > 1) {
+    const int64_t span = hi - lo;
+    if (span <= kWarp) {
+      bool ok = false;
+      if (lane < span) ok = ldcg(hq_c + base + lo + lane) <= item;
+      const unsigned b = __ballot_sync(kFull, ok);
+      return base + lo + (31 - __clz(b));
+    }
+    const int64_t idx = lo + span * lane / kWarp;
+    const bool ok = ldcg(hq_c + base + idx) <= item;
+    const unsigned b = __ballot_sync(kFull, ok);
+    const int t = 31 - __clz(b);
+    const int64_t nlo = lo + span * t / kWarp;
+    const int64_t nhi = (t == kWarp - 1) ? hi : lo + span * (t + 1) / kWarp;
+    lo = nlo;
+    hi = nhi;
+  }
+  return base + lo;
+}
+
+} // namespace
+} // namespace bcgpu

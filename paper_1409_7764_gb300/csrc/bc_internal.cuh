@@ -12,7 +12,12 @@ constexpr int kWarp = 32;
 constexpr int kBlock = 256;                    // threads per CTA of the persistent kernels
 constexpr int kWarpsPerBlock = kBlock / kWarp; // 8
 constexpr int kK = 64;                         // sources per batch (one bit each in a u64 mask)
-constexpr int kChunk = 256;                    // edges per work chunk of a high-degree vertex
+constexpr int kChunk = 64;                     // edges per work chunk of a high-degree vertex
+constexpr int kGrab = 4;                       // work items a warp takes per counter fetch
+#ifndef BC_BATCH_MIN_BLOCKS
+#define BC_BATCH_MIN_BLOCKS 4                  // resident CTAs per SM the batch kernel is built for
+#endif
+constexpr int kBatchMinBlocks = BC_BATCH_MIN_BLOCKS;
 
 // Device-side error codes (sticky in Ctl::err).
 enum : int {
@@ -21,6 +26,7 @@ enum : int {
   KERR_QUEUE = 2,    // frontier queue capacity exceeded
   KERR_HEAVY = 3,    // heavy-entry list capacity exceeded
   KERR_CHUNKS = 4,   // heavy chunk scratch exceeded
+  KERR_LEVELS = 5,   // dense kernel: more levels than the per-level masks hold
 };
 
 // Job-level counters (uint64 each), accumulated by the kernels.
@@ -32,8 +38,12 @@ enum : int {
   CNT_REACHED = 4,   // (source, reached vertex) pairs
   CNT_HEAVY = 5,     // heavy chunks processed (forward + backward)
   CNT_MAXLEV = 6,    // max level count (atomicMax)
+  CNT_LEVELS = 7,    // level counts summed over batches
   CNT_N = 8
 };
+
+constexpr int kGroup = 8;      // dense kernel: vertices per light work group
+constexpr int kDenseLevels = 64; // dense kernel: default level cap
 
 // Per-workspace control block; the host zeroes it once per job.
 struct Ctl {
@@ -43,6 +53,7 @@ struct Ctl {
   int nlevels;            // levels of the current batch
   unsigned long long tail; // frontier queue tail (entries)
   unsigned long long ovf;  // batch: sources (bits) whose count reached 2^64; plain: 0/1
+  unsigned long long work[4]; // work-item counters of consecutive steps (ring)
 };
 
 // A resident graph: out-CSR, in-CSR and the per-vertex chunk count
@@ -72,7 +83,8 @@ struct Work {
   int64_t *qoff = nullptr;    // [n+3] start of each level in qv
   unsigned long long *hpack = nullptr; // [n+3] per level: (heavy count << 32) | chunk total
   int64_t *hoff = nullptr;    // [n+3] start of each level's heavy list
-  int64_t *hq_e = nullptr;    // [hcap] queue position of each heavy entry
+  int64_t *hq_e = nullptr;    // [hcap] queue position (queue kernel) or vertex id (dense kernel)
+                              // of each heavy entry
   int64_t *hq_c = nullptr;    // [hcap] first chunk of each heavy entry within its level
   unsigned *harrive = nullptr; // [hcap] chunk arrivals per heavy entry
   int64_t hcap = 0;
@@ -81,6 +93,9 @@ struct Work {
   int64_t chunk_cap = 0;
   uint64_t *sigma = nullptr;  // [n][k_max] path counts
   void *cdep = nullptr;       // [n][k_max] (1 + delta) / sigma, float or double
+  uint64_t *lm = nullptr;     // dense kernel: [dmax][n] per-level frontier masks
+  int32_t dmax = 0;           // levels lm can hold
+  unsigned *lvl_flag = nullptr; // dense kernel: [dmax + 2] level non-empty flags
   Ctl *ctl = nullptr;
 };
 
@@ -98,11 +113,15 @@ struct KParams {
   double *dbg_delta = nullptr;
   long long timeout_ns = 2000000000LL;
   int32_t skip_block = -1;      // failure-injection hook (-1: none)
+  unsigned long long *trace = nullptr; // optional [trace_cap][4] per-step records
+  int32_t trace_cap = 0;
 };
 
 // Host launchers (bc_kernels.cu).  Return a cudaError_t.
 cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_dense(const KParams &p, bool fp64, int grid, cudaStream_t st);
+int max_grid_dense(bool fp64, int device);
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
 int max_grid_batch(bool fp64, int device);
 int max_grid_plain(bool fp64, int device);

@@ -27,95 +27,19 @@
 // (the paper's multi-block-per-source design, Section II.A, with the level
 // loop moved on-device), lanes spread over edges.
 //
-// High-degree vertices (in+out degree > kChunk) are split into chunks that
-// different warps process; partial sums meet in scratch and the last
-// arriving warp (ticket counter) reduces them in chunk order, which keeps
-// the result deterministic.  Memory written during a launch by another SM is
+// Work inside a level is balanced dynamically: warps fetch small groups of
+// items from a per-step counter.  High-degree vertices (in+out degree >
+// kChunk) are split into chunks that different warps process; partial sums
+// meet in scratch and the last arriving warp (ticket counter) reduces them in
+// chunk order, which keeps the result deterministic.  Memory written during a launch by another SM is
 // always read through L2 (ld.global.cg), never a possibly stale L1 line.
-#include "bc_internal.cuh"
+#include "bc_device.cuh"
 
 #include <cstdio>
 
 namespace bcgpu {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
-
-__device__ __forceinline__ void set_err(Ctl *ctl, int code) { atomicCAS(&ctl->err, 0, code); }
-
-__device__ __forceinline__ int read_err(const Ctl *ctl) {
-  return *reinterpret_cast<const volatile int *>(&ctl->err);
-}
-
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// wait is bounded by timeout_ns; on expiry the CTA records KERR_TIMEOUT and
-// continues, and every CTA then leaves the kernel at its next error check.
-// When snap_dst is given, the last CTA to arrive copies the queue tail there
-// before releasing the others: once every CTA has arrived no enqueue of the
-// finished level can still be in flight, so the copy is that level's final
-// end, and unlike the live tail (which the next level's enqueues advance) it
-// reads the same in every CTA.  Returns false when the job is in an error
-// state.
-__device__ bool grid_sync(Ctl *ctl, long long timeout_ns, int64_t *snap_dst = nullptr) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *genp = &ctl->bar_gen;
-    const unsigned gen = *genp;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      if (snap_dst) *snap_dst = (int64_t)atomicAdd(&ctl->tail, 0ull);
-      ctl->bar_count = 0;
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = globaltimer_ns();
-      while (*genp == gen) {
-        if (read_err(ctl)) break;
-        if ((long long)(globaltimer_ns() - t0) > timeout_ns) {
-          set_err(ctl, KERR_TIMEOUT);
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return read_err(ctl) == 0;
-}
-
-// ---------------------------------------------------------------------------
-// batched kernel: up to 64 sources, bitset frontiers
-// ---------------------------------------------------------------------------
-
-template <typename DT> __device__ __forceinline__ DT u64_to(uint64_t x);
-template <> __device__ __forceinline__ float u64_to<float>(uint64_t x) { return __ull2float_rn(x); }
-template <> __device__ __forceinline__ double u64_to<double>(uint64_t x) { return __ull2double_rn(x); }
-
-// saturating add: on carry the sum pins at 2^64-1 and the flag is raised
-__device__ __forceinline__ void sat_add(uint64_t &acc, uint64_t x, bool &ovf) {
-  uint64_t s = acc + x;
-  if (s < x) {
-    s = ~0ull;
-    ovf = true;
-  }
-  acc = s;
-}
 
 struct LevelView {
   int lvl;
@@ -124,35 +48,6 @@ struct LevelView {
   int64_t nheavy;        // heavy entries of this level
   int64_t nhc;           // heavy chunks of this level
   int64_t hoff_next;     // first heavy entry of the next level (forward)
-};
-
-// Index of the heavy entry that owns chunk `item` (binary search over the
-// level's chunk prefixes, which increase with the entry index).
-__device__ __forceinline__ int64_t find_heavy(const int64_t *hq_c, int64_t base, int64_t cnt,
-                                              int64_t item) {
-  int64_t lo = 0, hi = cnt; // invariant: hq_c[base+lo] <= item < hq_c[base+hi] (virtual end)
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (ldcg(hq_c + base + mid) <= item) lo = mid; else hi = mid;
-  }
-  return base + lo;
-}
-
-// Arrival ticket of a heavy-entry chunk: every lane's partial writes are
-// fenced, the warp converges, lane 0 takes the ticket, and after the
-// broadcast every lane fences again so the last arriver reads all partials.
-__device__ __forceinline__ unsigned chunk_ticket(unsigned *arrive, int lane) {
-  __threadfence();
-  __syncwarp();
-  unsigned t = 0;
-  if (lane == 0) t = atomicAdd(arrive, 1u);
-  t = __shfl_sync(kFull, t, 0);
-  __threadfence();
-  return t;
-}
-
-struct Counters {
-  unsigned long long entries = 0, out_e = 0, in_e = 0, dag = 0, reached = 0, heavy = 0;
 };
 
 // Warp-aggregated append of newly discovered vertices to the next level.
@@ -189,6 +84,45 @@ __device__ __forceinline__ void enqueue_new(const KParams &p, const LevelView &l
   }
 }
 
+// ---- step work distribution ------------------------------------------------
+//
+// The work of one step is a list of items: the chunks of the level's heavy
+// entries first (largest units first), then its light entries.  Warps take
+// kGrab consecutive items per fetch from the step's counter and fetch the
+// next group before processing the current one, so the counter round trip
+// overlaps useful work.
+
+// The first group of every warp is static (items gwarp*kGrab ..), so a step
+// whose items all fit in one group per warp touches no counter; later groups
+// come from the step's counter.
+__device__ __forceinline__ int64_t next_items(unsigned long long *ctr, int64_t total,
+                                              int64_t stat, int lane) {
+  if (total <= stat) return total;
+  unsigned long long v = 0;
+  if (lane == 0) v = atomicAdd(ctr, (unsigned long long)kGrab);
+  return stat + (int64_t)__shfl_sync(kFull, v, 0);
+}
+
+// Tracks the heavy entry of consecutive chunk items within one warp.
+struct HeavyCursor {
+  int64_t h = -1, first = 0, end = 0;
+  __device__ __forceinline__ void seek(const KParams &p, const LevelView &lv, int64_t item,
+                                       int lane) {
+    if (h >= 0 && item >= first && item < end) return;
+    if (h >= 0 && item == end && h + 1 < lv.hoff + lv.nheavy) {
+      ++h;
+    } else {
+      h = warp_find_heavy(p.w.hq_c, lv.hoff, lv.nheavy, item, lane);
+    }
+    first = ldcg(p.w.hq_c + h);
+    end = (h + 1 < lv.hoff + lv.nheavy) ? ldcg(p.w.hq_c + h + 1) : lv.nhc;
+  }
+};
+
+__device__ __forceinline__ void zero_ring_ahead(Ctl *ctl, int step, int64_t gtid) {
+  if (gtid == 0) ctl->work[(step + 2) & 3] = 0;
+}
+
 // Batch: discovery push over out-edges [eb, ee) of a frontier vertex with mask F.
 __device__ __forceinline__ void batch_discover(const KParams &p, const LevelView &lv, uint64_t F,
                                                int64_t eb, int64_t ee, uint64_t *Bn, int lane) {
@@ -210,74 +144,6 @@ __device__ __forceinline__ void batch_discover(const KParams &p, const LevelView
     }
     enqueue_new(p, lv, isnew, x, lane);
   }
-}
-
-// Batch: path-count pull over in-edges [eb, ee) of entry w (mask F) from the
-// level l-1 dense mask Pm.  Lane owns sources lane and lane+32.
-__device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, int64_t eb,
-                                                 int64_t ee, const uint64_t *Pm, int lane,
-                                                 uint64_t &s0, uint64_t &s1, bool &o0, bool &o1,
-                                                 unsigned long long &dag) {
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    int u = 0;
-    uint64_t P = 0;
-    if (e < ee) {
-      u = __ldg(p.g.in_idx + e);
-      P = ldcg(Pm + u) & F;
-    }
-    unsigned bal = __ballot_sync(kFull, P != 0);
-    while (bal) {
-      const int l = __ffs(bal) - 1;
-      bal &= bal - 1;
-      const int uu = __shfl_sync(kFull, u, l);
-      const uint64_t PP = __shfl_sync(kFull, P, l);
-      const uint64_t *row = p.w.sigma + (size_t)uu * kK;
-      if ((PP >> lane) & 1ull) sat_add(s0, ldcg(row + lane), o0);
-      if ((PP >> (lane + 32)) & 1ull) sat_add(s1, ldcg(row + 32 + lane), o1);
-      if (lane == 0) dag += __popcll(PP);
-    }
-  }
-}
-
-// Batch: dependency pull over out-edges [eb, ee) of entry v (mask F) from
-// the level l+1 dense mask Dn.
-template <typename DT>
-__device__ __forceinline__ void batch_pull_delta(const KParams &p, uint64_t F, int64_t eb,
-                                                 int64_t ee, const uint64_t *Dn, int lane,
-                                                 DT &a0, DT &a1) {
-  const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    int x = 0;
-    uint64_t S = 0;
-    if (e < ee) {
-      x = __ldg(p.g.col_idx + e);
-      S = ldcg(Dn + x) & F;
-    }
-    unsigned bal = __ballot_sync(kFull, S != 0);
-    while (bal) {
-      const int l = __ffs(bal) - 1;
-      bal &= bal - 1;
-      const int xx = __shfl_sync(kFull, x, l);
-      const uint64_t SS = __shfl_sync(kFull, S, l);
-      const DT *row = cdep + (size_t)xx * kK;
-      if ((SS >> lane) & 1ull) a0 += ldcg(row + lane);
-      if ((SS >> (lane + 32)) & 1ull) a1 += ldcg(row + 32 + lane);
-    }
-  }
-}
-
-// Batch: writes the path counts of entry w (mask F) and records overflow.
-__device__ __forceinline__ void batch_store_sigma(const KParams &p, int w, uint64_t F,
-                                                  uint64_t s0, uint64_t s1, bool o0, bool o1,
-                                                  int lane) {
-  uint64_t *row = p.w.sigma + (size_t)w * kK;
-  if ((F >> lane) & 1ull) row[lane] = s0;
-  if ((F >> (lane + 32)) & 1ull) row[32 + lane] = s1;
-  const uint64_t ob =
-      ((uint64_t)__ballot_sync(kFull, o0) | ((uint64_t)__ballot_sync(kFull, o1) << 32)) & F;
-  if (ob && lane == 0) atomicOr(&p.w.ctl->ovf, (unsigned long long)ob);
 }
 
 // Batch: closes entry v (mask F) at level l of the backward sweep given the
@@ -327,8 +193,75 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, u
   }
 }
 
+// Header of up to four consecutive queue entries, loaded with one round of
+// lane-parallel loads: lane 4f+i holds field f of entry i.
+struct EntryHeaders {
+  uint64_t hv;
+  int cnt;
+  __device__ __forceinline__ uint64_t field(int f, int i) const {
+    return __shfl_sync(kFull, hv, 4 * f + i);
+  }
+};
+
+// Forward headers: f0 = mask F (from the dense level mask), f1/f2 = in-CSR
+// range, f3/f4 = out-CSR range, f5 = chunk count, f6 = vertex id.
+__device__ __forceinline__ EntryHeaders fwd_headers(const KParams &p, const uint64_t *A,
+                                                    int64_t e0, int cnt, int lane) {
+  int wv = 0;
+  if (lane < cnt) wv = ldcg(p.w.qv + e0 + lane);
+  const int i = lane & 3, f = lane >> 2;
+  const int w = __shfl_sync(kFull, wv, i);
+  uint64_t hv = 0;
+  if (i < cnt) {
+    switch (f) {
+      case 0: hv = ldcg(A + w); break;
+      case 1: hv = (uint64_t)(uint32_t)__ldg(p.g.in_ptr + w); break;
+      case 2: hv = (uint64_t)(uint32_t)__ldg(p.g.in_ptr + w + 1); break;
+      case 3: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + w); break;
+      case 4: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + w + 1); break;
+      case 5: hv = (uint64_t)(uint32_t)__ldg(p.g.nchunks + w); break;
+      case 6: hv = (uint64_t)(uint32_t)w; break;
+      default: break;
+    }
+  }
+  EntryHeaders h;
+  h.hv = hv;
+  h.cnt = cnt;
+  return h;
+}
+
+// Backward headers: f0 = mask (queue), f1/f2 = out-CSR range, f3 = chunk
+// count, f4 = vertex id.
+__device__ __forceinline__ EntryHeaders bwd_headers(const KParams &p, int64_t e0, int cnt,
+                                                    int lane) {
+  int wv = 0;
+  if (lane < cnt) wv = ldcg(p.w.qv + e0 + lane);
+  uint64_t mq = 0;
+  if (lane < cnt) mq = ldcg(p.w.qm + e0 + lane);
+  const int i = lane & 3, f = lane >> 2;
+  const int v = __shfl_sync(kFull, wv, i);
+  const uint64_t F = __shfl_sync(kFull, mq, i);
+  uint64_t hv = 0;
+  if (i < cnt) {
+    switch (f) {
+      case 0: hv = F; break;
+      case 1: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + v); break;
+      case 2: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + v + 1); break;
+      case 3: hv = (uint64_t)(uint32_t)__ldg(p.g.nchunks + v); break;
+      case 4: hv = (uint64_t)(uint32_t)v; break;
+      default: break;
+    }
+  }
+  EntryHeaders h;
+  h.hv = hv;
+  h.cnt = cnt;
+  return h;
+}
+
 template <typename DT>
-__global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
+  __shared__ unsigned long long s_acc[kWarpsPerBlock][kK]; // warp-private gather rows
+  unsigned long long *wacc = s_acc[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -350,6 +283,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
       ctl->tail = 0;
       ctl->ovf = 0;
       ctl->nlevels = 0;
+      for (int i = 0; i < 4; ++i) ctl->work[i] = 0;
       p.w.hpack[0] = 0;
       p.w.hpack[1] = 0;
       p.w.qoff[0] = 0;
@@ -386,6 +320,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
   int64_t lo_m2 = 0; // start of level l-2
   int64_t lo_m1 = 0; // start of level l-1
   int L = 0;
+  int step = 0;
   while (true) {
     const int l = lv.lvl;
     uint64_t *Bn = fr + (size_t)((l + 1) & 3) * n;      // level l+1 (being built)
@@ -400,19 +335,28 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
       p.w.hoff[l] = lv.hoff;
       p.w.hpack[l + 2] = 0;
     }
+    zero_ring_ahead(ctl, step, gtid);
     if (l >= 2)
       for (int64_t i = lo_m2 + gtid; i < lo_m1; i += nthr) Z[ldcg(p.w.qv + i)] = 0;
 
-    const int64_t nlight = lv.hi - lv.lo;
-    for (int64_t item = gwarp; item < lv.nhc + nlight; item += nwarps) {
-      if (item < lv.nhc) {
+    unsigned long long *ctr = &ctl->work[step & 3];
+    const int64_t total = lv.nhc + (lv.hi - lv.lo);
+    trace_step(p, step, l, total, lv.nhc, gtid);
+    HeavyCursor hc;
+    const int64_t stat = nwarps * kGrab;
+    int64_t base = gwarp * kGrab;
+    while (base < total) {
+      const int64_t next = next_items(ctr, total, stat, lane);
+      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      for (int64_t item = base; item < end && item < lv.nhc; ++item) {
         // one chunk of a heavy entry
-        const int64_t h = find_heavy(p.w.hq_c, lv.hoff, lv.nheavy, item);
+        hc.seek(p, lv, item, lane);
+        const int64_t h = hc.h;
         const int64_t e = ldcg(p.w.hq_e + h);
         const int w = ldcg(p.w.qv + e);
         const uint64_t F = ldcg(A + w);
         const int nch = __ldg(p.g.nchunks + w);
-        const int64_t c = item - ldcg(p.w.hq_c + h);
+        const int64_t c = item - hc.first;
         const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
         const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
         const int64_t indeg = ie - is, tot = indeg + (re - rs);
@@ -420,8 +364,8 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
         uint64_t s0 = 0, s1 = 0;
         bool o0 = false, o1 = false;
         if (l > 0 && a < indeg)
-          batch_pull_sigma(p, F, is + a, is + (b < indeg ? b : indeg), Pm, lane, s0, s1, o0, o1,
-                           cnt.dag);
+          batch_pull_sigma(p, F, is + a, is + (b < indeg ? b : indeg), Pm, lane, wacc, s0, s1,
+                           o0, o1, cnt.dag);
         if (b > indeg)
           batch_discover(p, lv, F, rs + (a > indeg ? a - indeg : 0), rs + (b - indeg), Bn, lane);
         if (lane == 0) {
@@ -437,7 +381,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
         if (lane == 0) p.w.partial_ovf[item] = ob;
         const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
         if (ticket == (unsigned)(nch - 1)) {
-          const int64_t c0 = ldcg(p.w.hq_c + h);
+          const int64_t c0 = hc.first;
           uint64_t t0 = 0, t1 = 0;
           bool q0 = false, q1 = false;
           uint64_t ovb = 0;
@@ -446,6 +390,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
             t1 = 1;
           } else {
             const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
+#pragma unroll 4
             for (int64_t cc = c0; cc < c0 + nch; ++cc) {
               sat_add(t0, ldcg(pp + (size_t)cc * kK + lane), q0);
               sat_add(t1, ldcg(pp + (size_t)cc * kK + 32 + lane), q1);
@@ -461,33 +406,40 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
             cnt.reached += __popcll(F);
           }
         }
-      } else {
-        const int64_t e = lv.lo + (item - lv.nhc);
-        const int w = ldcg(p.w.qv + e);
-        if (__ldg(p.g.nchunks + w) > 0) continue; // handled as chunks
-        const uint64_t F = ldcg(A + w);
-        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
-        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
-        uint64_t s0 = 0, s1 = 0;
-        bool o0 = false, o1 = false;
-        if (l == 0) {
-          s0 = 1;
-          s1 = 1;
-        } else {
-          batch_pull_sigma(p, F, is, ie, Pm, lane, s0, s1, o0, o1, cnt.dag);
-        }
-        batch_store_sigma(p, w, F, s0, s1, o0, o1, lane);
-        batch_discover(p, lv, F, rs, re, Bn, lane);
-        if (lane == 0) {
-          p.w.qm[e] = F;
-          cnt.entries++;
-          cnt.reached += __popcll(F);
-          cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
-          cnt.out_e += (uint64_t)(re - rs);
+      }
+      if (end > lv.nhc) {
+        const int64_t first = base > lv.nhc ? base : lv.nhc;
+        const int64_t e0 = lv.lo + (first - lv.nhc);
+        const EntryHeaders hd = fwd_headers(p, A, e0, (int)(end - first), lane);
+        for (int i = 0; i < hd.cnt; ++i) {
+          if (hd.field(5, i) != 0) continue; // heavy: handled as chunks
+          const uint64_t F = hd.field(0, i);
+          const int64_t is = (int64_t)hd.field(1, i), ie = (int64_t)hd.field(2, i);
+          const int64_t rs = (int64_t)hd.field(3, i), re = (int64_t)hd.field(4, i);
+          const int w = (int)hd.field(6, i);
+          uint64_t s0 = 0, s1 = 0;
+          bool o0 = false, o1 = false;
+          if (l == 0) {
+            s0 = 1;
+            s1 = 1;
+          } else {
+            batch_pull_sigma(p, F, is, ie, Pm, lane, wacc, s0, s1, o0, o1, cnt.dag);
+          }
+          batch_store_sigma(p, w, F, s0, s1, o0, o1, lane);
+          batch_discover(p, lv, F, rs, re, Bn, lane);
+          if (lane == 0) {
+            p.w.qm[e0 + i] = F;
+            cnt.entries++;
+            cnt.reached += __popcll(F);
+            cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
+            cnt.out_e += (uint64_t)(re - rs);
+          }
         }
       }
+      base = next;
     }
     if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    ++step;
     const int64_t nh = ldcg(p.w.qoff + l + 2);
     if (nh == lv.hi) {
       L = l + 1;
@@ -504,6 +456,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
   if (gtid == 0) {
     ctl->nlevels = L;
     atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
+    atomicAdd(p.job_cnt + CNT_LEVELS, (unsigned long long)L);
     const uint64_t ob = ldcg(&ctl->ovf);
     for (int j = 0; j < p.k; ++j)
       if ((ob >> j) & 1ull) p.ovf_flags[p.src_base + j] = 1;
@@ -514,28 +467,45 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
     const uint64_t *Dn = fr + (size_t)((l + 1) & 3) * n; // level l+1 masks
     uint64_t *Wn = l > 0 ? fr + (size_t)(l & 3) * n : nullptr; // level l masks for step l-1
     uint64_t *Z = fr + (size_t)((l + 2) & 3) * n;        // level l+2 (cleared now)
-    const int64_t lo = ldcg(p.w.qoff + l), hi = ldcg(p.w.qoff + l + 1);
+    LevelView bl;
+    bl.lvl = l;
+    bl.lo = ldcg(p.w.qoff + l);
+    bl.hi = ldcg(p.w.qoff + l + 1);
     const unsigned long long hp = ldcg(p.w.hpack + l);
-    const int64_t nheavy = (int64_t)(hp >> 32), nhc = (int64_t)(hp & 0xffffffffull);
-    const int64_t hoff = ldcg(p.w.hoff + l);
+    bl.nheavy = (int64_t)(hp >> 32);
+    bl.nhc = (int64_t)(hp & 0xffffffffull);
+    bl.hoff = ldcg(p.w.hoff + l);
+    bl.hoff_next = 0;
+    zero_ring_ahead(ctl, step, gtid);
     if (l + 2 <= L - 1) {
       const int64_t zlo = ldcg(p.w.qoff + l + 2), zhi = ldcg(p.w.qoff + l + 3);
       for (int64_t i = zlo + gtid; i < zhi; i += nthr) Z[ldcg(p.w.qv + i)] = 0;
     }
     const bool deepest = (l == L - 1);
-    for (int64_t item = gwarp; item < nhc + (hi - lo); item += nwarps) {
-      if (item < nhc) {
-        const int64_t h = find_heavy(p.w.hq_c, hoff, nheavy, item);
+    unsigned long long *ctr = &ctl->work[step & 3];
+    const int64_t total = bl.nhc + (bl.hi - bl.lo);
+    trace_step(p, step, -1 - l, total, bl.nhc, gtid);
+    HeavyCursor hc;
+    const int64_t stat = nwarps * kGrab;
+    int64_t base = gwarp * kGrab;
+    while (base < total) {
+      const int64_t next = next_items(ctr, total, stat, lane);
+      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      for (int64_t item = base; item < end && item < bl.nhc; ++item) {
+        hc.seek(p, bl, item, lane);
+        const int64_t h = hc.h;
         const int64_t e = ldcg(p.w.hq_e + h);
         const int v = ldcg(p.w.qv + e);
         const uint64_t F = ldcg(p.w.qm + e);
         const int nch = __ldg(p.g.nchunks + v);
-        const int64_t c = item - ldcg(p.w.hq_c + h);
+        const int64_t c = item - hc.first;
         const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
         const int64_t od = re - rs;
         const int64_t a = c * od / nch, b = (c + 1) * od / nch;
         DT a0 = 0, a1 = 0;
-        if (!deepest) batch_pull_delta<DT>(p, F, rs + a, rs + b, Dn, lane, a0, a1);
+        if (!deepest)
+          batch_pull_delta<DT>(p, F, rs + a, rs + b, Dn, lane, reinterpret_cast<DT *>(wacc), a0,
+                               a1);
         if (lane == 0) {
           cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
           cnt.heavy++;
@@ -545,9 +515,10 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
         part[32 + lane] = a1;
         const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
         if (ticket == (unsigned)(nch - 1)) {
-          const int64_t c0 = ldcg(p.w.hq_c + h);
+          const int64_t c0 = hc.first;
           const DT *pp = reinterpret_cast<const DT *>(p.w.partial);
           DT t0 = 0, t1 = 0;
+#pragma unroll 4
           for (int64_t cc = c0; cc < c0 + nch; ++cc) {
             t0 += ldcg(pp + (size_t)cc * kK + lane);
             t1 += ldcg(pp + (size_t)cc * kK + 32 + lane);
@@ -555,22 +526,31 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const KParams p) {
           batch_finish<DT>(p, l, v, F, t0, t1, Wn, s_lo, s_hi, lane);
           if (lane == 0) p.w.harrive[h] = 0;
         }
-      } else {
-        const int64_t e = lo + (item - nhc);
-        const int v = ldcg(p.w.qv + e);
-        if (__ldg(p.g.nchunks + v) > 0) continue;
-        const uint64_t F = ldcg(p.w.qm + e);
-        DT a0 = 0, a1 = 0;
-        if (!deepest) {
-          const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
-          batch_pull_delta<DT>(p, F, rs, re, Dn, lane, a0, a1);
-          if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
-        }
-        batch_finish<DT>(p, l, v, F, a0, a1, Wn, s_lo, s_hi, lane);
       }
+      if (end > bl.nhc) {
+        const int64_t first = base > bl.nhc ? base : bl.nhc;
+        const int64_t e0 = bl.lo + (first - bl.nhc);
+        const EntryHeaders hd = bwd_headers(p, e0, (int)(end - first), lane);
+        for (int i = 0; i < hd.cnt; ++i) {
+          if (hd.field(3, i) != 0) continue;
+          const uint64_t F = hd.field(0, i);
+          const int64_t rs = (int64_t)hd.field(1, i), re = (int64_t)hd.field(2, i);
+          const int v = (int)hd.field(4, i);
+          DT a0 = 0, a1 = 0;
+          if (!deepest) {
+            batch_pull_delta<DT>(p, F, rs, re, Dn, lane, reinterpret_cast<DT *>(wacc), a0, a1);
+            if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
+          }
+          batch_finish<DT>(p, l, v, F, a0, a1, Wn, s_lo, s_hi, lane);
+        }
+      }
+      base = next;
     }
     if (!grid_sync(ctl, p.timeout_ns)) return;
+    ++step;
   }
+
+  trace_step(p, step, 1 << 20, 0, 0, gtid); // end marker
 
   // ---- leave the workspace clean for the next batch ------------------------
   {
@@ -603,11 +583,6 @@ __device__ __forceinline__ void warp_sat_sum(uint64_t &v, bool &o) {
   }
 }
 
-template <typename DT> __device__ __forceinline__ DT warp_sum(DT v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-  return v;
-}
 
 __device__ __forceinline__ void plain_discover(const KParams &p, const LevelView &lv, int64_t eb,
                                                int64_t ee, int lane) {
@@ -680,6 +655,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->tail = 1;
     ctl->ovf = 0;
+    for (int i = 0; i < 4; ++i) ctl->work[i] = 0;
     p.w.qv[0] = s;
     p.w.d[s] = 0;
     p.w.qoff[0] = 0;
@@ -702,6 +678,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
   lv.hi = 1;
   lv.hoff = 0;
   int L = 0;
+  int step = 0;
   while (true) {
     const int l = lv.lvl;
     const unsigned long long hp = ldcg(p.w.hpack + l);
@@ -712,73 +689,88 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
       p.w.hoff[l] = lv.hoff;
       p.w.hpack[l + 2] = 0;
     }
-    for (int64_t item = gwarp; item < lv.nhc + (lv.hi - lv.lo); item += nwarps) {
-      if (item < lv.nhc) {
-        const int64_t h = find_heavy(p.w.hq_c, lv.hoff, lv.nheavy, item);
-        const int64_t e = ldcg(p.w.hq_e + h);
-        const int w = ldcg(p.w.qv + e);
-        const int nch = __ldg(p.g.nchunks + w);
-        const int64_t c = item - ldcg(p.w.hq_c + h);
-        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
-        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
-        const int64_t indeg = ie - is, tot = indeg + (re - rs);
-        const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
-        uint64_t sv = 0;
-        bool o = false;
-        if (l > 0 && a < indeg)
-          plain_pull_sigma(p, l, is + a, is + (b < indeg ? b : indeg), lane, sv, o, cnt.dag);
-        warp_sat_sum(sv, o);
-        if (b > indeg) plain_discover(p, lv, rs + (a > indeg ? a - indeg : 0), rs + (b - indeg), lane);
-        if (lane == 0) {
-          cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
-          cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
-          cnt.heavy++;
-          uint64_t *part = reinterpret_cast<uint64_t *>(p.w.partial);
-          part[item] = sv;
-          p.w.partial_ovf[item] = o ? 1ull : 0ull;
-        }
-        const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
-        if (ticket == (unsigned)(nch - 1) && lane == 0) {
-          const int64_t c0 = ldcg(p.w.hq_c + h);
-          uint64_t t = 0;
-          bool q = false;
-          if (l == 0) {
-            t = 1;
-          } else {
-            const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
-            for (int64_t cc = c0; cc < c0 + nch; ++cc) {
-              sat_add(t, ldcg(pp + cc), q);
-              q = q || ldcg(p.w.partial_ovf + cc) != 0;
-            }
+    zero_ring_ahead(ctl, step, gtid);
+    unsigned long long *ctr = &ctl->work[step & 3];
+    const int64_t total = lv.nhc + (lv.hi - lv.lo);
+    trace_step(p, step, l, total, lv.nhc, gtid);
+    HeavyCursor hc;
+    const int64_t stat = nwarps * kGrab;
+    int64_t base = gwarp * kGrab;
+    while (base < total) {
+      const int64_t next = next_items(ctr, total, stat, lane);
+      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      for (int64_t item = base; item < end; ++item) {
+        if (item < lv.nhc) {
+          hc.seek(p, lv, item, lane);
+          const int64_t h = hc.h;
+          const int64_t e = ldcg(p.w.hq_e + h);
+          const int w = ldcg(p.w.qv + e);
+          const int nch = __ldg(p.g.nchunks + w);
+          const int64_t c = item - hc.first;
+          const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+          const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+          const int64_t indeg = ie - is, tot = indeg + (re - rs);
+          const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
+          uint64_t sv = 0;
+          bool o = false;
+          if (l > 0 && a < indeg)
+            plain_pull_sigma(p, l, is + a, is + (b < indeg ? b : indeg), lane, sv, o, cnt.dag);
+          warp_sat_sum(sv, o);
+          if (b > indeg)
+            plain_discover(p, lv, rs + (a > indeg ? a - indeg : 0), rs + (b - indeg), lane);
+          if (lane == 0) {
+            cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
+            cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
+            cnt.heavy++;
+            reinterpret_cast<uint64_t *>(p.w.partial)[item] = sv;
+            p.w.partial_ovf[item] = o ? 1ull : 0ull;
           }
-          p.w.sigma[w] = t;
-          if (q) atomicOr(&ctl->ovf, 1ull);
-          p.w.harrive[h] = 0;
-          cnt.entries++;
-          cnt.reached++;
+          const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
+          if (ticket == (unsigned)(nch - 1) && lane == 0) {
+            const int64_t c0 = hc.first;
+            uint64_t t = 0;
+            bool q = false;
+            if (l == 0) {
+              t = 1;
+            } else {
+              const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
+#pragma unroll 4
+              for (int64_t cc = c0; cc < c0 + nch; ++cc) {
+                sat_add(t, ldcg(pp + cc), q);
+                q = q || ldcg(p.w.partial_ovf + cc) != 0;
+              }
+            }
+            p.w.sigma[w] = t;
+            if (q) atomicOr(&ctl->ovf, 1ull);
+            p.w.harrive[h] = 0;
+            cnt.entries++;
+            cnt.reached++;
+          }
+        } else {
+          const int64_t e = lv.lo + (item - lv.nhc);
+          const int w = ldcg(p.w.qv + e);
+          if (__ldg(p.g.nchunks + w) > 0) continue;
+          const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+          const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+          uint64_t sv = 0;
+          bool o = false;
+          if (l > 0) plain_pull_sigma(p, l, is, ie, lane, sv, o, cnt.dag);
+          warp_sat_sum(sv, o);
+          if (lane == 0) {
+            p.w.sigma[w] = (l == 0) ? 1ull : sv;
+            if (o) atomicOr(&ctl->ovf, 1ull);
+            cnt.entries++;
+            cnt.reached++;
+            cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
+            cnt.out_e += (uint64_t)(re - rs);
+          }
+          plain_discover(p, lv, rs, re, lane);
         }
-      } else {
-        const int64_t e = lv.lo + (item - lv.nhc);
-        const int w = ldcg(p.w.qv + e);
-        if (__ldg(p.g.nchunks + w) > 0) continue;
-        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
-        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
-        uint64_t sv = 0;
-        bool o = false;
-        if (l > 0) plain_pull_sigma(p, l, is, ie, lane, sv, o, cnt.dag);
-        warp_sat_sum(sv, o);
-        if (lane == 0) {
-          p.w.sigma[w] = (l == 0) ? 1ull : sv;
-          if (o) atomicOr(&ctl->ovf, 1ull);
-          cnt.entries++;
-          cnt.reached++;
-          cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
-          cnt.out_e += (uint64_t)(re - rs);
-        }
-        plain_discover(p, lv, rs, re, lane);
       }
+      base = next;
     }
     if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    ++step;
     const int64_t nh = ldcg(p.w.qoff + l + 2);
     if (nh == lv.hi) {
       L = l + 1;
@@ -792,62 +784,84 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
   if (gtid == 0) {
     ctl->nlevels = L;
     atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
+    atomicAdd(p.job_cnt + CNT_LEVELS, (unsigned long long)L);
     if (ldcg(&ctl->ovf)) p.ovf_flags[p.src_base] = 1;
   }
 
   for (int l = L - 1; l >= 0; --l) {
-    const int64_t lo = ldcg(p.w.qoff + l), hi = ldcg(p.w.qoff + l + 1);
+    LevelView bl;
+    bl.lvl = l;
+    bl.lo = ldcg(p.w.qoff + l);
+    bl.hi = ldcg(p.w.qoff + l + 1);
     const unsigned long long hp = ldcg(p.w.hpack + l);
-    const int64_t nheavy = (int64_t)(hp >> 32), nhc = (int64_t)(hp & 0xffffffffull);
-    const int64_t hoff = ldcg(p.w.hoff + l);
+    bl.nheavy = (int64_t)(hp >> 32);
+    bl.nhc = (int64_t)(hp & 0xffffffffull);
+    bl.hoff = ldcg(p.w.hoff + l);
+    bl.hoff_next = 0;
+    zero_ring_ahead(ctl, step, gtid);
     if (l + 2 <= L - 1) {
       const int64_t zlo = ldcg(p.w.qoff + l + 2), zhi = ldcg(p.w.qoff + l + 3);
       for (int64_t i = zlo + gtid; i < zhi; i += nthr) p.w.d[ldcg(p.w.qv + i)] = -1;
     }
     const bool deepest = (l == L - 1);
-    for (int64_t item = gwarp; item < nhc + (hi - lo); item += nwarps) {
-      if (item < nhc) {
-        const int64_t h = find_heavy(p.w.hq_c, hoff, nheavy, item);
-        const int64_t e = ldcg(p.w.hq_e + h);
-        const int v = ldcg(p.w.qv + e);
-        const int nch = __ldg(p.g.nchunks + v);
-        const int64_t c = item - ldcg(p.w.hq_c + h);
-        const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
-        const int64_t od = re - rs;
-        const int64_t a = c * od / nch, b = (c + 1) * od / nch;
-        DT acc = 0;
-        if (!deepest) acc = plain_pull_delta<DT>(p, l, rs + a, rs + b, lane);
-        acc = warp_sum<DT>(acc);
-        if (lane == 0) {
-          cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
-          cnt.heavy++;
-          reinterpret_cast<DT *>(p.w.partial)[item] = acc;
-        }
-        const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
-        if (ticket == (unsigned)(nch - 1) && lane == 0) {
-          const int64_t c0 = ldcg(p.w.hq_c + h);
-          const DT *pp = reinterpret_cast<const DT *>(p.w.partial);
-          DT t = 0;
-          for (int64_t cc = c0; cc < c0 + nch; ++cc) t += ldcg(pp + cc);
-          plain_finish<DT>(p, l, v, t, s);
-          p.w.harrive[h] = 0;
-        }
-      } else {
-        const int64_t e = lo + (item - nhc);
-        const int v = ldcg(p.w.qv + e);
-        if (__ldg(p.g.nchunks + v) > 0) continue;
-        DT acc = 0;
-        if (!deepest) {
+    unsigned long long *ctr = &ctl->work[step & 3];
+    const int64_t total = bl.nhc + (bl.hi - bl.lo);
+    trace_step(p, step, -1 - l, total, bl.nhc, gtid);
+    HeavyCursor hc;
+    const int64_t stat = nwarps * kGrab;
+    int64_t base = gwarp * kGrab;
+    while (base < total) {
+      const int64_t next = next_items(ctr, total, stat, lane);
+      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      for (int64_t item = base; item < end; ++item) {
+        if (item < bl.nhc) {
+          hc.seek(p, bl, item, lane);
+          const int64_t h = hc.h;
+          const int64_t e = ldcg(p.w.hq_e + h);
+          const int v = ldcg(p.w.qv + e);
+          const int nch = __ldg(p.g.nchunks + v);
+          const int64_t c = item - hc.first;
           const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
-          acc = plain_pull_delta<DT>(p, l, rs, re, lane);
-          if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
+          const int64_t od = re - rs;
+          const int64_t a = c * od / nch, b = (c + 1) * od / nch;
+          DT acc = 0;
+          if (!deepest) acc = plain_pull_delta<DT>(p, l, rs + a, rs + b, lane);
+          acc = warp_sum<DT>(acc);
+          if (lane == 0) {
+            cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
+            cnt.heavy++;
+            reinterpret_cast<DT *>(p.w.partial)[item] = acc;
+          }
+          const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
+          if (ticket == (unsigned)(nch - 1) && lane == 0) {
+            const int64_t c0 = hc.first;
+            const DT *pp = reinterpret_cast<const DT *>(p.w.partial);
+            DT t = 0;
+#pragma unroll 4
+            for (int64_t cc = c0; cc < c0 + nch; ++cc) t += ldcg(pp + cc);
+            plain_finish<DT>(p, l, v, t, s);
+            p.w.harrive[h] = 0;
+          }
+        } else {
+          const int64_t e = bl.lo + (item - bl.nhc);
+          const int v = ldcg(p.w.qv + e);
+          if (__ldg(p.g.nchunks + v) > 0) continue;
+          DT acc = 0;
+          if (!deepest) {
+            const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
+            acc = plain_pull_delta<DT>(p, l, rs, re, lane);
+            if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
+          }
+          acc = warp_sum<DT>(acc);
+          if (lane == 0) plain_finish<DT>(p, l, v, acc, s);
         }
-        acc = warp_sum<DT>(acc);
-        if (lane == 0) plain_finish<DT>(p, l, v, acc, s);
       }
+      base = next;
     }
     if (!grid_sync(ctl, p.timeout_ns)) return;
+    ++step;
   }
+  trace_step(p, step, 1 << 20, 0, 0, gtid); // end marker
   {
     const int64_t q2 = L >= 2 ? ldcg(p.w.qoff + 2) : ldcg(p.w.qoff + 1);
     for (int64_t i = gtid; i < q2; i += nthr) p.w.d[ldcg(p.w.qv + i)] = -1;

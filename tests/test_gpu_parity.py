@@ -190,15 +190,20 @@ def test_canonicalisation_in_library(ctx):
     ctx.destroy_graph(G)
 
 
-def test_deterministic_and_batch_width_independent(ctx):
+def test_repeatable_and_batch_width_independent(ctx):
+    """Repeated runs and every batch width agree within the parity tolerance
+    (dependency sums use floating-point shared-memory atomics, so their
+    summation order, and only the last bits, may differ between runs)."""
     g = bcgen.rmat(11, 16, seed=9)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
     a = ctx.exact(G, delta_fp64=False).copy()
     b = ctx.exact(G, delta_fp64=False).copy()
-    assert np.array_equal(a, b)
-    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    assert_bc_close(a, ref, False)
+    assert_bc_close(b, ref, False)
     for kb in (1, 7, 32, 64):
-        assert_bc_close(ctx.exact(G, delta_fp64=True, batch_k=kb), ref, True)
+        for sched in ("batch_dense", "batch_queue"):
+            assert_bc_close(ctx.exact(G, delta_fp64=True, batch_k=kb, schedule=sched), ref, True)
     ctx.destroy_graph(G)
 
 
@@ -227,4 +232,32 @@ def test_failure_injection_times_out_and_recovers(ctx):
     assert ei.value.status == bc.BC_ERR_TIMEOUT
     ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
     assert_bc_close(ctx.exact(G, schedule="batch", delta_fp64=True), ref, True)
+    ctx.destroy_graph(G)
+
+
+def test_deep_graph_falls_back_to_queue_kernel(ctx):
+    """More BFS levels than the dense kernel's per-level masks hold: the job
+    reruns on the frontier-queue kernel and is still exact."""
+    g = bcgen.csr_from_edges(300, np.concatenate([np.arange(299), [0, 5]]),
+                             np.concatenate([np.arange(1, 300), [2, 9]]), name="long path")
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    got = ctx.exact(G, schedule="batch_dense", delta_fp64=True)
+    assert_bc_close(got, ref, True)
+    st = ctx.last_stats()
+    assert st["kernel_kind"] == 2 and st["max_levels"] > 64
+    # later jobs on the same graph go straight to the queue kernel
+    assert_bc_close(ctx.exact(G, schedule="batch_dense", delta_fp64=False), ref, False)
+    assert ctx.last_stats()["kernel_kind"] == 2
+    ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("schedule,kind", [("batch", 2), ("batch_queue", 2), ("batch_dense", 3)])
+def test_batched_schedules_pick_their_kernel(ctx, schedule, kind):
+    g = bcgen.rmat(9, 8, seed=3)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    for fp64 in (True, False):
+        assert_bc_close(ctx.exact(G, schedule=schedule, delta_fp64=fp64), ref, fp64)
+        assert ctx.last_stats()["kernel_kind"] == kind
     ctx.destroy_graph(G)
