@@ -177,11 +177,15 @@ bc_status bc_debug_sources(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t 
                            const bc_opts *opts, int32_t *d_out, uint64_t *sigma_out,
                            double *delta_out);
 
-/* Exact BC of `count` resident graphs in one persistent launch: each graph's
- * sources run in batches of up to 64 inside thread blocks that loop over a
- * queue of (graph, batch) items.  bc_out receives the graphs' vectors back to
- * back (graph i at offset sum_{j<i} n_j).  Intended for many small graphs
- * (n <= 65536 each); larger graphs return BC_ERR_ARG. */
+/* Exact BC of `count` resident graphs.  Graphs of up to 8192 vertices run in
+ * ONE persistent launch: each thread block takes the next graph (largest
+ * n*(m+n) first), runs all of its source batches (opts.batch_k sources each,
+ * default 64) with block-level barriers between BFS levels and writes that
+ * graph's BC itself; larger graphs run one after another through the
+ * grid-wide batched kernel.  bc_out receives the vectors back to back (graph
+ * i at offset sum_{j<i} n_j), host or device memory per opts.out_device;
+ * normalize applies per graph, scale_sampled has no effect (all sources).
+ * BC_ERR_ADMISSION when the per-block workspaces do not fit the budget. */
 bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, const bc_opts *opts,
                         double *bc_out);
 

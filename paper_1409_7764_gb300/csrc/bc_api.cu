@@ -193,6 +193,7 @@ struct bc_ctx {
   int sm_count = 0;
   int grid_batch[2] = {0, 0}; // [fp64]
   int grid_dense[2] = {0, 0};
+  int grid_many[2] = {0, 0};
   int grid_plain[2] = {0, 0};
 
   std::mutex mu;
@@ -226,6 +227,7 @@ struct JobRec {
   bool all_sources = false;
   bc_opts opts{};
   int64_t k = 0;            // number of sources
+  int64_t n = 0;            // vertices of the graph (result length)
   // run state
   int slot = -1;
   cudaStream_t st = nullptr;
@@ -869,6 +871,7 @@ bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx
   for (int f = 0; f < 2; ++f) {
     ctx->grid_batch[f] = max_grid_batch(f != 0, device);
     ctx->grid_dense[f] = max_grid_dense(f != 0, device);
+    ctx->grid_many[f] = max_grid_many(f != 0, device);
     ctx->grid_plain[f] = max_grid_plain(f != 0, device);
     if (ctx->grid_batch[f] <= 0 || ctx->grid_plain[f] <= 0 || ctx->grid_dense[f] <= 0)
       return BC_ERR_CUDA;
@@ -988,6 +991,7 @@ bc_status bc_submit(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, cons
     j->k = j->g->dev.n;
   }
   j->opts = o;
+  j->n = j->g->dev.n;
   const int sched = resolve_schedule(o, j->g->dev);
   j->footprint = job_footprint(j->g->dev, sched, resolve_batch_k(o), j->k);
   if (j->footprint > ctx->budget) return BC_ERR_ADMISSION;
@@ -1011,7 +1015,8 @@ bc_status bc_submit(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, cons
 static bc_status take_result(bc_ctx *ctx, std::map<int64_t, std::unique_ptr<JobRec>>::iterator it,
                              double *bc_out, bc_stats *stats) {
   JobRec *j = it->second.get();
-  if (bc_out && j->g) std::memcpy(bc_out, j->h_out, sizeof(double) * (size_t)j->g->dev.n);
+  // the graph may be gone by now (destroyed after the job finished)
+  if (bc_out && j->n) std::memcpy(bc_out, j->h_out, sizeof(double) * (size_t)j->n);
   if (stats) *stats = j->stats;
   bc_status s = j->status;
   cudaFreeHost(j->h_out);
@@ -1104,28 +1109,211 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
   DeviceGuard dg(ctx->device);
   bc_opts o = opts ? *opts : default_opts();
   if (!opts_valid(o)) return BC_ERR_ARG;
-  int64_t off = 0;
-  bc_stats total{};
-  for (int32_t i = 0; i < count; ++i) {
-    GraphRec *g;
-    {
-      std::lock_guard<std::mutex> lk(ctx->mu);
-      g = find_graph(ctx, graphs[i]);
-    }
-    if (!g) return BC_ERR_GRAPH;
-    bc_status s = run_sync(ctx, g, nullptr, g->dev.n, true, &o, bc_out + off, nullptr);
-    if (s != BC_OK) return s;
-    off += g->dev.n;
-    total.n += ctx->last.n;
-    total.m += ctx->last.m;
-    total.sources += ctx->last.sources;
-    total.batches += ctx->last.batches;
-    total.kernel_launches += ctx->last.kernel_launches;
-    total.device_ms += ctx->last.device_ms;
-    total.max_levels = std::max(total.max_levels, ctx->last.max_levels);
+  std::vector<GraphRec *> gs((size_t)count);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (int32_t i = 0; i < count; ++i)
+      if (!(gs[(size_t)i] = find_graph(ctx, graphs[i]))) return BC_ERR_GRAPH;
   }
+  const bool fp64 = o.delta_fp64 != 0;
+  const int kb = resolve_batch_k(o);
+  std::vector<int64_t> off((size_t)count + 1, 0);
+  for (int32_t i = 0; i < count; ++i) off[(size_t)i + 1] = off[(size_t)i] + gs[(size_t)i]->dev.n;
+  const int64_t total_n = off[(size_t)count];
+  // schedule per graph: graphs up to kManyMaxN vertices share the persistent
+  // many-graph launch; larger ones use the grid-wide batched kernel
+  constexpr int32_t kManyMaxN = 8192;
+  std::vector<int32_t> small, big;
+  int32_t max_n = 1;
+  int64_t max_hv = 1, max_hc = 1;
+  for (int32_t i = 0; i < count; ++i) {
+    const GraphDev &gd = gs[(size_t)i]->dev;
+    if (gd.n <= kManyMaxN) {
+      small.push_back(i);
+      max_n = std::max(max_n, gd.n);
+      max_hv = std::max(max_hv, gd.heavy_vertices);
+      max_hc = std::max(max_hc, gd.heavy_chunks);
+    } else {
+      big.push_back(i);
+    }
+  }
+  // largest work first (longest-processing-time order)
+  std::sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
+    const GraphDev &x = gs[(size_t)a]->dev, &y = gs[(size_t)b]->dev;
+    return (double)x.n * (double)(x.m + x.n) > (double)y.n * (double)(y.m + y.n);
+  });
+  cudaStream_t st = ctx->stream;
+  double *d_out = nullptr;
+  int8_t *d_ovf = nullptr;
+  unsigned long long *d_cnt = nullptr;
+  BC_TRY(cudaMallocAsync(&d_out, sizeof(double) * (size_t)std::max<int64_t>(total_n, 1), st));
+  BC_TRY(cudaMallocAsync(&d_ovf, (size_t)std::max<int64_t>(total_n, 1), st));
+  BC_TRY(cudaMallocAsync(&d_cnt, sizeof(unsigned long long) * (CNT_N + 1), st));
+  BC_TRY(cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)std::max<int64_t>(total_n, 1), st));
+  BC_TRY(cudaMemsetAsync(d_ovf, 0, (size_t)std::max<int64_t>(total_n, 1), st));
+  BC_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * (CNT_N + 1), st));
+  bc_stats total{};
+  total.kernel_kind = 2;
+  float many_ms = 0.f;
+  bc_status status = BC_OK;
+  void *ws_mem = nullptr;
+  Work *d_works = nullptr;
+  GraphDev *d_graphs = nullptr;
+  int32_t *d_order = nullptr, *d_iota = nullptr;
+  int64_t *d_off = nullptr;
+  unsigned *d_next = nullptr;
+  if (!small.empty()) {
+    // one workspace per thread block, sized for the largest small graph
+    WsRec proto;
+    proto.kind = WS_QUEUE;
+    proto.batch = true;
+    proto.n = max_n;
+    proto.cap = (int64_t)max_n * kb;
+    proto.hcap = max_hv * kb;
+    proto.chunk_cap = max_hc;
+    const size_t stride = ws_layout(proto, nullptr);
+    int grid = ctx->grid_many[fp64];
+    const size_t ws_budget = (ctx->budget > ctx->used ? ctx->budget - ctx->used : 0) / 2;
+    grid = (int)std::min<int64_t>(grid, std::max<int64_t>(1, (int64_t)(ws_budget / stride)));
+    grid = (int)std::min<int64_t>(grid, (int64_t)small.size());
+    if (grid < 1 || stride * (size_t)grid > ws_budget) return BC_ERR_ADMISSION;
+    BC_TRY(cudaMalloc(&ws_mem, stride * (size_t)grid));
+    std::vector<Work> works((size_t)grid);
+    for (int c = 0; c < grid; ++c) {
+      WsRec r = proto;
+      ws_layout(r, static_cast<char *>(ws_mem) + stride * (size_t)c);
+      works[(size_t)c] = r.w;
+    }
+    std::vector<GraphDev> table((size_t)count);
+    for (int32_t i = 0; i < count; ++i) table[(size_t)i] = gs[(size_t)i]->dev;
+    std::vector<int32_t> iota((size_t)max_n);
+    for (int32_t i = 0; i < max_n; ++i) iota[(size_t)i] = i;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+      if (e == cudaSuccess) e = cudaMallocAsync(ptr, std::max<size_t>(bytes, 1), st);
+    };
+    alloc(reinterpret_cast<void **>(&d_works), sizeof(Work) * works.size());
+    alloc(reinterpret_cast<void **>(&d_graphs), sizeof(GraphDev) * table.size());
+    alloc(reinterpret_cast<void **>(&d_order), sizeof(int32_t) * small.size());
+    alloc(reinterpret_cast<void **>(&d_iota), sizeof(int32_t) * iota.size());
+    alloc(reinterpret_cast<void **>(&d_off), sizeof(int64_t) * off.size());
+    alloc(reinterpret_cast<void **>(&d_next), sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws_mem, 0, stride * (size_t)grid, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_works, works.data(), sizeof(Work) * works.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_graphs, table.data(), sizeof(GraphDev) * table.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, small.data(), sizeof(int32_t) * small.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_iota, iota.data(), sizeof(int32_t) * iota.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(unsigned), st);
+    ManyParams mp;
+    mp.base.ovf_flags = d_ovf;
+    mp.base.job_cnt = d_cnt;
+    mp.graphs = d_graphs;
+    mp.order = d_order;
+    mp.out_off = d_off;
+    mp.count = (int32_t)small.size();
+    mp.works = d_works;
+    mp.iota = d_iota;
+    mp.out = d_out;
+    mp.next = d_next;
+    mp.kb = kb;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_many(mp, fp64, grid, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    // the block workspaces' control words carry any device error
+    std::vector<int> errs((size_t)grid, 0);
+    for (int c = 0; c < grid && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(&errs[(size_t)c], &works[(size_t)c].ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) cudaEventElapsedTime(&many_ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) status = cuda_status(e);
+    for (int c = 0; c < grid && status == BC_OK; ++c)
+      if (errs[(size_t)c]) status = BC_ERR_INTERNAL;
+    total.batches += 0;
+    for (int32_t i : small) total.batches += (gs[(size_t)i]->dev.n + kb - 1) / kb;
+    total.kernel_launches += 1;
+  }
+  // larger graphs, one grid-wide job each, straight into the device result
+  for (int32_t i : big) {
+    if (status != BC_OK) break;
+    bc_opts od = o;
+    od.out_device = 1;
+    od.normalize = 0;
+    od.schedule = BC_SCHED_BATCH;
+    status = run_sync(ctx, gs[(size_t)i], nullptr, gs[(size_t)i]->dev.n, true, &od,
+                      d_out + off[(size_t)i], nullptr);
+    if (status == BC_OK) {
+      total.batches += ctx->last.batches;
+      total.kernel_launches += ctx->last.kernel_launches;
+      total.device_ms += ctx->last.device_ms;
+      total.max_levels = std::max(total.max_levels, ctx->last.max_levels);
+      total.frontier_entries += ctx->last.frontier_entries;
+      total.scanned_out_edges += ctx->last.scanned_out_edges;
+      total.scanned_in_edges += ctx->last.scanned_in_edges;
+      total.dag_pairs += ctx->last.dag_pairs;
+      total.reached_pairs += ctx->last.reached_pairs;
+      total.heavy_chunks += ctx->last.heavy_chunks;
+      total.levels_sum += ctx->last.levels_sum;
+    }
+  }
+  // per-graph normalisation, result copy, counters of the persistent launch
+  std::vector<unsigned long long> cnt(CNT_N + 1, 0);
+  std::vector<int8_t> ovf((size_t)std::max<int64_t>(total_n, 1), 0);
+  if (status == BC_OK) {
+    cudaError_t e = cudaSuccess;
+    if (o.normalize)
+      for (int32_t i = 0; i < count && e == cudaSuccess; ++i) {
+        const int64_t n = gs[(size_t)i]->dev.n;
+        if (n > 2)
+          e = launch_scale(d_out + off[(size_t)i], d_out + off[(size_t)i], n,
+                           1.0 / ((double)(n - 1) * (double)(n - 2)), st);
+      }
+    if (e == cudaSuccess && total_n)
+      e = cudaMemcpyAsync(bc_out, d_out, sizeof(double) * (size_t)total_n,
+                          o.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && total_n)
+      e = cudaMemcpyAsync(ovf.data(), d_ovf, (size_t)total_n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) status = cuda_status(e);
+  }
+  cudaFreeAsync(d_out, st);
+  cudaFreeAsync(d_ovf, st);
+  cudaFreeAsync(d_cnt, st);
+  if (d_works) cudaFreeAsync(d_works, st);
+  if (d_graphs) cudaFreeAsync(d_graphs, st);
+  if (d_order) cudaFreeAsync(d_order, st);
+  if (d_iota) cudaFreeAsync(d_iota, st);
+  if (d_off) cudaFreeAsync(d_off, st);
+  if (d_next) cudaFreeAsync(d_next, st);
+  cudaStreamSynchronize(st);
+  if (ws_mem) cudaFree(ws_mem);
+  if (status != BC_OK) return status;
+  for (int32_t i = 0; i < count; ++i) {
+    total.n += gs[(size_t)i]->dev.n;
+    total.m += gs[(size_t)i]->dev.m;
+  }
+  total.sources = total_n;
+  total.device_ms += many_ms;
+  total.frontier_entries += (int64_t)cnt[CNT_ENTRIES];
+  total.scanned_out_edges += (int64_t)cnt[CNT_OUT_EDGES];
+  total.scanned_in_edges += (int64_t)cnt[CNT_IN_EDGES];
+  total.dag_pairs += (int64_t)cnt[CNT_DAG];
+  total.reached_pairs += (int64_t)cnt[CNT_REACHED];
+  total.heavy_chunks += (int64_t)cnt[CNT_HEAVY];
+  total.levels_sum += (int32_t)cnt[CNT_LEVELS];
+  total.max_levels = std::max(total.max_levels, (int32_t)cnt[CNT_MAXLEV]);
+  int32_t novf = 0;
+  for (int64_t i = 0; i < total_n; ++i) novf += ovf[(size_t)i] ? 1 : 0;
+  total.overflow_sources += novf;
   ctx->last = total;
-  return BC_OK;
+  return novf ? BC_ERR_SIGMA_OVERFLOW : BC_OK;
 }
 
 bc_status bc_debug_inject_barrier_skip(bc_ctx *ctx, int32_t block, int32_t timeout_ms) {

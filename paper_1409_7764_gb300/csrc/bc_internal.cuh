@@ -117,7 +117,24 @@ struct KParams {
   int32_t trace_cap = 0;
 };
 
+// Parameters of the many-small-graphs launch: one thread block per graph at a
+// time, graphs taken from *next in the order given.
+struct ManyParams {
+  KParams base;                   // counters, flags, timeout (graph/batch fields unused)
+  const GraphDev *graphs = nullptr; // [count]
+  const int32_t *order = nullptr; // [count] graph indices, largest work first
+  const int64_t *out_off = nullptr; // [count] offset of each graph's BC (and source flags)
+  int32_t count = 0;
+  const Work *works = nullptr;    // [grid] one workspace per thread block
+  const int32_t *iota = nullptr;  // [max n] 0, 1, 2, ...: the sources of exact BC
+  double *out = nullptr;          // [sum of n]
+  unsigned *next = nullptr;       // graph counter
+  int32_t kb = kK;                // sources per batch
+};
+
 // Host launchers (bc_kernels.cu).  Return a cudaError_t.
+cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st);
+int max_grid_many(bool fp64, int device);
 cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_dense(const KParams &p, bool fp64, int grid, cudaStream_t st);

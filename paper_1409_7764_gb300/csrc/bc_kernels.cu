@@ -258,19 +258,61 @@ __device__ __forceinline__ EntryHeaders bwd_headers(const KParams &p, int64_t e0
   return h;
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
-  __shared__ unsigned long long s_acc[kWarpsPerBlock][kK]; // warp-private gather rows
-  unsigned long long *wacc = s_acc[threadIdx.x >> 5];
+// Synchronisation scope of one batch: the whole grid of a cooperative launch
+// (levels separated by the time-bounded grid barrier) ...
+struct GridScope {
+  static constexpr bool kGrid = true;
+  __device__ __forceinline__ int rank() const { return (int)blockIdx.x; }
+  __device__ __forceinline__ int size() const { return (int)gridDim.x; }
+  __device__ __forceinline__ bool sync(Ctl *ctl, long long timeout_ns,
+                                       int64_t *snap = nullptr) const {
+    return grid_sync(ctl, timeout_ns, snap);
+  }
+};
+
+// ... or one thread block that owns the whole batch (CTA barriers; used for
+// many small graphs in one launch).  The snapshot of the queue tail is taken
+// by thread 0 between two barriers, as the grid barrier's last arriver does.
+struct CtaScope {
+  static constexpr bool kGrid = false;
+  __device__ __forceinline__ int rank() const { return 0; }
+  __device__ __forceinline__ int size() const { return 1; }
+  __device__ __forceinline__ bool sync(Ctl *ctl, long long, int64_t *snap = nullptr) const {
+    __syncthreads();
+    if (snap && threadIdx.x == 0)
+      *snap = (int64_t)*reinterpret_cast<volatile unsigned long long *>(&ctl->tail);
+    __syncthreads();
+    return read_err(ctl) == 0;
+  }
+};
+
+// Flushes a warp's counters into the job counters (lane 0 holds them).
+__device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, const Counters &cnt,
+                                               int lane) {
+  if (lane == 0) {
+    atomicAdd(job_cnt + CNT_ENTRIES, cnt.entries);
+    atomicAdd(job_cnt + CNT_OUT_EDGES, cnt.out_e);
+    atomicAdd(job_cnt + CNT_IN_EDGES, cnt.in_e);
+    atomicAdd(job_cnt + CNT_DAG, cnt.dag);
+    atomicAdd(job_cnt + CNT_REACHED, cnt.reached);
+    atomicAdd(job_cnt + CNT_HEAVY, cnt.heavy);
+  }
+}
+
+// One batch of up to 64 sources through both sweeps, in the given scope.
+// Returns early (leaving the workspace dirty) when the job is in an error
+// state.  Warp counters accumulate into cnt.
+template <typename DT, typename Scope>
+__device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
+                                           unsigned long long *wacc, Counters &cnt) {
   const int lane = threadIdx.x & 31;
-  const int64_t gwarp = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-  const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const int64_t nthr = (int64_t)gridDim.x * kBlock;
+  const int64_t gwarp = (int64_t)sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)sc.size() * kWarpsPerBlock;
+  const int64_t gtid = (int64_t)sc.rank() * kBlock + threadIdx.x;
+  const int64_t nthr = (int64_t)sc.size() * kBlock;
   Ctl *ctl = p.w.ctl;
   const int n = p.g.n;
   uint64_t *const fr = p.w.fr;
-  Counters cnt;
 
   if (read_err(ctl)) return;
   // sources owned by this lane (for excluding s from its own BC)
@@ -278,7 +320,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
   const int s_hi = lane + 32 < p.k ? __ldg(p.src + lane + 32) : -1;
 
   // ---- init: level 0 = the sources (block 0) ------------------------------
-  if (blockIdx.x == 0) {
+  if (sc.rank() == 0) {
     if (threadIdx.x == 0) {
       ctl->tail = 0;
       ctl->ovf = 0;
@@ -308,8 +350,8 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
       }
     }
   }
-  if (p.skip_block == (int)blockIdx.x) return; // failure-injection hook: never arrives
-  if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + 1)) return;
+  if (Scope::kGrid && p.skip_block == sc.rank()) return; // failure-injection hook
+  if (!sc.sync(ctl, p.timeout_ns, p.w.qoff + 1)) return;
 
   // ---- forward sweep -------------------------------------------------------
   LevelView lv;
@@ -438,7 +480,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
       }
       base = next;
     }
-    if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    if (!sc.sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
     ++step;
     const int64_t nh = ldcg(p.w.qoff + l + 2);
     if (nh == lv.hi) {
@@ -546,7 +588,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
       }
       base = next;
     }
-    if (!grid_sync(ctl, p.timeout_ns)) return;
+    if (!sc.sync(ctl, p.timeout_ns)) return;
     ++step;
   }
 
@@ -559,14 +601,47 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
     for (int64_t i = gtid; i < q1; i += nthr) fr[ldcg(p.w.qv + i)] = 0;
     for (int64_t i = q1 + gtid; i < q2; i += nthr) fr[(size_t)n + ldcg(p.w.qv + i)] = 0;
   }
-  if (lane == 0) {
-    atomicAdd(p.job_cnt + CNT_ENTRIES, cnt.entries);
-    atomicAdd(p.job_cnt + CNT_OUT_EDGES, cnt.out_e);
-    atomicAdd(p.job_cnt + CNT_IN_EDGES, cnt.in_e);
-    atomicAdd(p.job_cnt + CNT_DAG, cnt.dag);
-    atomicAdd(p.job_cnt + CNT_REACHED, cnt.reached);
-    atomicAdd(p.job_cnt + CNT_HEAVY, cnt.heavy);
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
+  __shared__ unsigned long long s_acc[kWarpsPerBlock][kK]; // warp-private gather rows
+  Counters cnt;
+  batch_body<DT>(p, GridScope(), s_acc[threadIdx.x >> 5], cnt);
+  flush_counters(p.job_cnt, cnt, threadIdx.x & 31);
+}
+
+// Exact BC of many small graphs in one launch: each thread block takes the
+// next graph from a shared counter (largest work first) and runs all of that
+// graph's source batches itself, with CTA barriers between levels, so every
+// graph's BC is written by one block without atomics.
+template <typename DT>
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const ManyParams mp) {
+  __shared__ unsigned long long s_acc[kWarpsPerBlock][kK];
+  __shared__ int s_item;
+  Counters cnt;
+  KParams p = mp.base;
+  p.w = mp.works[blockIdx.x];
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(mp.next, 1u);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= mp.count || read_err(p.w.ctl)) break;
+    const int gi = __ldg(mp.order + it);
+    p.g = mp.graphs[gi];
+    const int64_t off = __ldg(mp.out_off + gi);
+    p.bc = mp.out + off;
+    for (int b0 = 0; b0 < p.g.n; b0 += mp.kb) {
+      p.src = mp.iota + b0;
+      p.k = p.g.n - b0 < mp.kb ? p.g.n - b0 : mp.kb;
+      p.src_base = off + b0;
+      batch_body<DT>(p, CtaScope(), s_acc[threadIdx.x >> 5], cnt);
+      __syncthreads();
+      if (read_err(p.w.ctl)) break;
+    }
   }
+  flush_counters(p.job_cnt, cnt, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -918,6 +993,17 @@ cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor
   if (grid > 4096) grid = 4096;
   scale_kernel<<<grid, 256, 0, st>>>(in, out, n, factor);
   return cudaGetLastError();
+}
+
+cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st) {
+  if (fp64) many_kernel<double><<<grid, kBlock, 0, st>>>(mp);
+  else many_kernel<float><<<grid, kBlock, 0, st>>>(mp);
+  return cudaGetLastError();
+}
+
+int max_grid_many(bool fp64, int device) {
+  return fp64 ? max_grid_for(many_kernel<double>, device)
+              : max_grid_for(many_kernel<float>, device);
 }
 
 int max_grid_batch(bool fp64, int device) {
