@@ -427,13 +427,193 @@ def run_ours(args, w, name):
         dist.destroy_process_group()
 
 
+# ---- many small graphs in one launch ----------------------------------------------
+
+def many_graphs(count, seed=1):
+    """`count` R-MAT graphs, scale uniform in [6, 12], edge factor uniform in
+    [4, 16], graph i seeded by splitmix64(seed ^ i)."""
+    return [bcgen.rmat(s, ef, sd) for s, ef, sd in bcgen.small_rmat_specs(count, master_seed=seed)]
+
+
+def _oracle_graphs(args):
+    import oracle
+    done = 0
+    for n, rp, ci in args:
+        oracle.bc(n, rp, ci)
+        done += 1
+    return done
+
+
+def run_many(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    graphs = many_graphs(args.many_count)
+    work = sum(g.n * g.m for g in graphs)
+    cores = os.cpu_count() or 1
+    pool = None
+    if not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_oracle_chunk, [(graphs[0].n, graphs[0].row_ptr, graphs[0].col_idx,
+                                  np.arange(1, dtype=np.int32))] * cores)
+    import torch
+    import paper_1409_7764_gb300 as bc
+    stream = torch.cuda.current_stream()
+    ctx = bc.Context(0, stream=stream)
+    fp64 = args.fp64
+    hs = [ctx.create_graph(g.row_ptr, g.col_idx) for g in graphs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.exact_many(hs, delta_fp64=fp64)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms, stats = [], None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        ctx.exact_many(hs, delta_fp64=fp64)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(s.elapsed_time(e))
+        stats = ctx.last_stats()
+    clk = clocks.stop()
+    ms_step = statistics.mean(ms)
+    value = work / (ms_step / 1e3) / 1e9
+    algo = bytes_model(stats, 8 if fp64 else 4)
+    peak, peak_kind = peaks()
+    # end to end: host CSR in, host BC out, for all graphs
+    e2e = []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = [ctx.create_graph(g.row_ptr, g.col_idx) for g in graphs]
+        ctx.exact_many(h2, delta_fp64=fp64)
+        for h in h2:
+            ctx.destroy_graph(h)
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e)
+    cpu = None
+    if pool is not None:
+        # the oracle on the first graphs of the list, about cpu_seconds of work
+        t0 = time.perf_counter()
+        _oracle_graphs([(graphs[0].n, graphs[0].row_ptr, graphs[0].col_idx)])
+        t1 = max(time.perf_counter() - t0, 1e-4)
+        per = graphs[0].n * graphs[0].m
+        budget = args.cpu_seconds * cores / t1 * per
+        sample, acc = [], 0
+        for g in graphs:
+            if acc >= budget:
+                break
+            sample.append(g)
+            acc += g.n * g.m
+        parts = [[(g.n, g.row_ptr, g.col_idx) for g in sample[i::cores]] for i in range(cores)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_graphs, [p for p in parts if p])
+        wall = time.perf_counter() - t0
+        pool.close()
+        cpu = {"value": acc / wall / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+               "sample": f"exact BC of the first {len(sample)} of the {len(graphs)} graphs, "
+                         f"one process per core"}
+    line = {
+        "metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "u64+f64" if fp64 else "u64+f32", "data": "synthetic",
+        "config": {"workload": "rmat-many10k", "graphs": len(graphs),
+                   "scales": "6..12 uniform", "edge_factors": "4..16 uniform",
+                   "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs)),
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "schedule": "one persistent launch, one block per graph, 64 sources/batch"},
+        "roofline": {"bound": "hbm", "achieved": algo / (ms_step / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": algo / (ms_step / 1e3) / 1e9 / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "many_kernel"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": work / e2e_s / 1e9, "unit": "GTEPS",
+                "h2d_bytes_per_step": int(sum(4 * (g.n + 1) + 4 * g.m for g in graphs)),
+                "d2h_bytes_per_step": int(sum(8 * g.n for g in graphs))},
+        "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "clocks": clk,
+        "counters": {k: stats[k] for k in ("frontier_entries", "scanned_in_edges",
+                                           "scanned_out_edges", "dag_pairs", "reached_pairs",
+                                           "heavy_chunks", "max_levels", "batches")},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# ---- serving ----------------------------------------------------------------------
+
+def run_serving(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import torch
+    import paper_1409_7764_gb300 as bc
+    from paper_1409_7764_gb300.serving import (Request, poisson_arrivals, run_open_loop,
+                                                solo_service_times, summarize)
+    scales = list(range(8, 21))
+    seeds = [1, 2, 3, 4]
+    ctx = bc.Context(0)
+    pool = {}
+    for s in scales:
+        for sd in seeds:
+            g = bcgen.rmat(s, 16, seed=sd)
+            pool[(s, sd)] = ctx.create_graph(g.row_ptr, g.col_idx)
+    rs = np.random.default_rng(args.serve_seed)
+
+    def make_requests(count, fp64):
+        reqs = []
+        for i in range(count):
+            s = int(rs.integers(8, 21))
+            G = pool[(s, seeds[int(rs.integers(0, 4))])]
+            srcs = None if s <= 14 else bcgen.sample_sources(G.n, 1024, seed=1000 + i)
+            reqs.append(Request(G, srcs, dict(delta_fp64=fp64)))
+        return reqs
+
+    out = {}
+    for fp64 in (False, True):
+        key = "fp64" if fp64 else "fp32"
+        # capacity from solo service times of one request per pool graph
+        probe = []
+        for s in scales:
+            G = pool[(s, 1)]
+            probe.append(Request(G, None if s <= 14 else bcgen.sample_sources(G.n, 1024, seed=7),
+                                 dict(delta_fp64=fp64)))
+        solo_service_times(ctx, probe[:3])  # warm-up
+        tau = float(np.mean(solo_service_times(ctx, probe)))
+        res = {"mean_solo_ms": tau * 1e3, "capacity_rps": 1.0 / tau}
+        for rho in (0.5, 0.8):
+            reqs = make_requests(args.serve_requests, fp64)
+            arr = poisson_arrivals(len(reqs), rho / tau, seed=args.serve_seed + int(rho * 10))
+            recs = run_open_loop(ctx, reqs, arr)
+            res[f"rho{rho}"] = summarize(recs)
+        out[key] = res
+    main = out["fp32"]["rho0.8"]
+    line = {
+        "metric": "BC GTEPS (sources*m/s)", "value": main["gteps"], "unit": "GTEPS", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
+        "config": {"workload": "serving", "pool": "R-MAT scales 8..20 x 4 seeds, edge factor 16",
+                   "requests": args.serve_requests,
+                   "request_mix": "scale uniform 8..20; exact for scale <= 14, "
+                                  "1024 seeded sources above",
+                   "arrivals": "Poisson at rho x capacity (capacity from solo service times)"},
+        "serving": out,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat16-exact", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat16-exact",
+                    choices=sorted(WORKLOADS) + ["rmat-many10k", "serving"])
     ap.add_argument("--fp64", action="store_true", help="FP64 dependencies")
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -444,7 +624,18 @@ def main():
                     help="override the workload's schedule")
     ap.add_argument("--max-sources", type=int, default=0,
                     help="use only the first N sources of the workload (profiling runs)")
+    ap.add_argument("--many-count", type=int, default=10000)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-seed", type=int, default=1)
     args = ap.parse_args()
+    if args.workload == "rmat-many10k" and args.impl == "ours":
+        return run_many(args)
+    if args.workload == "serving" and args.impl == "ours":
+        return run_serving(args)
+    if args.workload in ("rmat-many10k", "serving"):
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the reference arm covers the single-graph workloads"}))
+        return
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w, args.workload)
