@@ -418,7 +418,7 @@ def run_ours(args, w, name):
             "counters": {k: st[k] for k in ("frontier_entries", "scanned_in_edges",
                                             "scanned_out_edges", "dag_pairs", "reached_pairs",
                                             "heavy_chunks", "max_levels", "levels_sum",
-                                            "batches", "kernel_kind")},
+                                            "batches", "kernel_kind", "chunk_edges", "grab")},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

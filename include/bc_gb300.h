@@ -101,6 +101,8 @@ typedef struct {
   int32_t kernel_kind;       /* kernel of the last launch: 1 plain, 2 batch (frontier queue),
                                 3 batch (per-level dense masks) */
   int32_t levels_sum;        /* BFS level counts summed over all batches */
+  int32_t chunk_edges;       /* edges per chunk of a high-degree vertex in the last launch */
+  int32_t grab;              /* work items a warp fetched at a time in the last launch */
 } bc_stats;
 
 /* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t

@@ -73,7 +73,22 @@ struct GraphRec {
   size_t bytes = 0;
   int active_jobs = 0;
   std::atomic<bool> deep{false}; // more BFS levels than the dense kernel's masks hold
+  // chunk counts of the high-degree vertices for each candidate chunk size
+  const int32_t *nch_variant[kChunkVariants] = {};
+  int64_t heavy_v[kChunkVariants] = {}, heavy_c[kChunkVariants] = {};
+  // per-graph tuning of the batched kernel: chunk variant and grab size
+  // (-1: not tuned yet)
+  std::atomic<int> tuned{-1};
 };
+
+// Launch configurations the tuner compares: (chunk variant, items per fetch).
+struct TuneCandidate {
+  int variant;
+  int grab;
+};
+constexpr TuneCandidate kTuneCandidates[] = {{0, 2}, {1, 2}, {2, 2}, {0, 1}};
+constexpr int kNumTune = 4;
+constexpr int kTuneRounds = 2; // trial batches per candidate
 
 enum WsKind { WS_PLAIN = 0, WS_QUEUE = 1, WS_DENSE = 2 };
 
@@ -248,6 +263,7 @@ struct JobRec {
   int64_t launches = 0;
   int64_t batches = 0;
   int kind = 0;              // workspace / kernel kind of the last launch
+  int cand = 0;              // tuning candidate of the last launch
   size_t footprint = 0;
   bc_status status = BC_PENDING;
   bc_stats stats{};
@@ -359,15 +375,24 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
     for (int32_t v = 0; v < n; ++v)
       for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) ii[(size_t)fill[ci[e]]++] = v;
   }
-  std::vector<int32_t> nch((size_t)std::max<int32_t>(n, 1), 0);
-  int64_t hv = 0, hc = 0;
-  for (int32_t v = 0; v < n; ++v) {
-    const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (ip[(size_t)v + 1] - ip[v]);
-    if (cost > kChunk) {
-      nch[v] = (int32_t)((cost + kChunk - 1) / kChunk);
-      ++hv;
-      hc += nch[v];
+  std::vector<std::vector<int32_t>> nchv(kChunkVariants,
+                                         std::vector<int32_t>((size_t)std::max<int32_t>(n, 1), 0));
+  int64_t hvv[kChunkVariants] = {}, hcv[kChunkVariants] = {};
+  for (int c = 0; c < kChunkVariants; ++c) {
+    const int64_t ch = kChunkCandidates[c];
+    for (int32_t v = 0; v < n; ++v) {
+      const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (ip[(size_t)v + 1] - ip[v]);
+      if (cost > ch) {
+        nchv[(size_t)c][(size_t)v] = (int32_t)((cost + ch - 1) / ch);
+        ++hvv[c];
+        hcv[c] += nchv[(size_t)c][(size_t)v];
+      }
     }
+  }
+  int64_t hv = 0, hc = 0; // maxima over the variants (workspace sizing)
+  for (int c = 0; c < kChunkVariants; ++c) {
+    hv = std::max(hv, hvv[c]);
+    hc = std::max(hc, hcv[c]);
   }
 
   auto g = std::make_unique<GraphRec>();
@@ -376,7 +401,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   int32_t *d_ci = c.take<int32_t>((size_t)me);
   int32_t *d_ip = c.take<int32_t>((size_t)n + 1);
   int32_t *d_ii = c.take<int32_t>((size_t)me);
-  int32_t *d_nc = c.take<int32_t>((size_t)n);
+  int32_t *d_nc = c.take<int32_t>((size_t)n * kChunkVariants);
   (void)d_rp; (void)d_ci; (void)d_ip; (void)d_ii; (void)d_nc;
   const size_t bytes = align_up(c.off, 256);
   if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
@@ -388,14 +413,16 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   d_ci = c2.take<int32_t>((size_t)me);
   d_ip = c2.take<int32_t>((size_t)n + 1);
   d_ii = c2.take<int32_t>((size_t)me);
-  d_nc = c2.take<int32_t>((size_t)n);
+  d_nc = c2.take<int32_t>((size_t)n * kChunkVariants);
   cudaStream_t st = ctx->stream;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && me) e = cudaMemcpyAsync(d_ci, ci.data(), sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && me) e = cudaMemcpyAsync(d_ii, ii.data(), sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_nc, nch.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+  for (int c = 0; c < kChunkVariants && e == cudaSuccess && n; ++c)
+    e = cudaMemcpyAsync(d_nc + (size_t)c * n, nchv[(size_t)c].data(), sizeof(int32_t) * (size_t)n,
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFree(mem);
@@ -409,9 +436,14 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   g->dev.col_idx = d_ci;
   g->dev.in_ptr = d_ip;
   g->dev.in_idx = d_ii;
-  g->dev.nchunks = d_nc;
+  g->dev.nchunks = d_nc; // variant 0 until tuned
   g->dev.heavy_vertices = hv;
   g->dev.heavy_chunks = hc;
+  for (int c = 0; c < kChunkVariants; ++c) {
+    g->nch_variant[c] = d_nc + (size_t)c * n;
+    g->heavy_v[c] = hvv[c];
+    g->heavy_c[c] = hcv[c];
+  }
   ctx->used += bytes;
   if (m_eff) *m_eff = me;
   out = std::move(g);
@@ -602,7 +634,24 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   BC_TRY(cudaEventRecord(j->ev0, st));
   j->batches = 0;
   j->launches = 0;
-  for (int64_t b0 = 0; b0 < k; b0 += kb) {
+  // Per-graph tuning of the queue kernel: the first job on a graph with
+  // enough batches runs kTuneRounds trial batches with each candidate
+  // (chunk size, items per fetch), times them with events, and keeps the
+  // fastest for the rest of the job and for later jobs on the graph.  Every
+  // candidate computes the same result; only the work split differs.
+  const int64_t nbatch = (k + kb - 1) / kb;
+  const int tuned = j->g->tuned.load();
+  const bool tune = kind == WS_QUEUE && tuned < 0 && !dbg && !std::getenv("BC_NO_TUNE") &&
+                    nbatch >= kNumTune * kTuneRounds + 8;
+  auto apply = [&](int cand) {
+    p.g.nchunks = j->g->nch_variant[kTuneCandidates[cand].variant];
+    p.grab = kTuneCandidates[cand].grab;
+    j->cand = cand;
+  };
+  apply(kind == WS_QUEUE && tuned >= 0 ? tuned : 0);
+  cudaEvent_t tev[kNumTune * kTuneRounds + 1] = {};
+  int64_t bi = 0;
+  for (int64_t b0 = 0; b0 < k; b0 += kb, ++bi) {
     p.src = j->d_src + b0;
     p.k = (int32_t)std::min<int64_t>(kb, k - b0);
     p.src_base = b0;
@@ -613,12 +662,39 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
       p.dbg_sigma = dbg->sigma + b0 * n;
       p.dbg_delta = dbg->delta + b0 * n;
     }
+    if (tune && bi <= kNumTune * kTuneRounds) {
+      if (!tev[bi]) BC_TRY(cudaEventCreate(&tev[bi]));
+      BC_TRY(cudaEventRecord(tev[bi], st));
+      if (bi < kNumTune * kTuneRounds) {
+        apply((int)(bi % kNumTune));
+      } else {
+        // all trial batches are enqueued: pick the fastest candidate
+        BC_TRY(cudaEventSynchronize(tev[bi]));
+        float sum[kNumTune] = {};
+        for (int64_t t = 0; t < kNumTune * kTuneRounds; ++t) {
+          float ms = 0.f;
+          BC_TRY(cudaEventElapsedTime(&ms, tev[t], tev[t + 1]));
+          sum[t % kNumTune] += ms;
+        }
+        int best = 0;
+        for (int c = 1; c < kNumTune; ++c)
+          if (sum[c] < sum[best]) best = c;
+        j->g->tuned = best;
+        apply(best);
+        for (auto &ev : tev) {
+          cudaEventDestroy(ev);
+          ev = nullptr;
+        }
+      }
+    }
     BC_TRY(kind == WS_DENSE   ? launch_dense(p, fp64, grid, st)
            : kind == WS_QUEUE ? launch_batch(p, fp64, grid, st)
                               : launch_plain(p, fp64, grid, st));
     ++j->batches;
     ++j->launches;
   }
+  for (auto &ev : tev)
+    if (ev) cudaEventDestroy(ev);
   BC_TRY(cudaEventRecord(j->ev1, st));
   double factor = 1.0;
   if (j->opts.normalize && n > 2) factor /= (double)(n - 1) * (double)(n - 2);
@@ -662,8 +738,15 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.max_levels = (int32_t)j->h_cnt[CNT_MAXLEV];
   s.kernel_kind = j->kind == WS_DENSE ? 3 : j->kind == WS_QUEUE ? 2 : 1;
   s.levels_sum = (int32_t)j->h_cnt[CNT_LEVELS];
+  s.chunk_edges = kChunkCandidates[kTuneCandidates[j->cand].variant];
+  s.grab = kTuneCandidates[j->cand].grab;
   int32_t novf = 0;
   for (int64_t i = 0; i < j->k; ++i) novf += j->h_ovf[i] ? 1 : 0;
+  if (j->h_trace && (j->h_cnt[CNT_BUSY] || j->h_cnt[CNT_IDLE])) {
+    const double b = (double)j->h_cnt[CNT_BUSY], i = (double)j->h_cnt[CNT_IDLE];
+    std::fprintf(stderr, "# phase clocks: items %.1f%%, waiting for the step end %.1f%%\n",
+                 100.0 * b / (b + i), 100.0 * i / (b + i));
+  }
   if (j->h_trace) {
     std::fprintf(stderr, "# trace batch %lld: step level items heavy_chunks us\n",
                  (long long)j->trace_batch);

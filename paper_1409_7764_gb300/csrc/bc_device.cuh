@@ -101,7 +101,19 @@ __device__ __forceinline__ unsigned chunk_ticket(unsigned *arrive, int lane) {
 
 struct Counters {
   unsigned long long entries = 0, out_e = 0, in_e = 0, dag = 0, reached = 0, heavy = 0;
+  unsigned long long busy = 0, idle = 0; // phase clocks (BC_PHASE_CLOCKS builds)
 };
+
+#ifndef BC_PHASE_CLOCKS
+#define BC_PHASE_CLOCKS 0
+#endif
+__device__ __forceinline__ long long phase_clock() {
+#if BC_PHASE_CLOCKS
+  return clock64();
+#else
+  return 0;
+#endif
+}
 
 // Up to four set lanes of a ballot, in lane order; missing ones are -1.
 struct Lanes4 {

@@ -12,8 +12,15 @@ constexpr int kWarp = 32;
 constexpr int kBlock = 256;                    // threads per CTA of the persistent kernels
 constexpr int kWarpsPerBlock = kBlock / kWarp; // 8
 constexpr int kK = 64;                         // sources per batch (one bit each in a u64 mask)
-constexpr int kChunk = 64;                     // edges per work chunk of a high-degree vertex
-constexpr int kGrab = 4;                       // work items a warp takes per counter fetch
+// Edges per work chunk of a high-degree vertex: candidates the per-graph
+// tuner picks from (the first is the default before tuning).
+constexpr int kChunkCandidates[3] = {256, 128, 512};
+constexpr int kChunkVariants = 3;
+constexpr int kChunk = kChunkCandidates[0];    // chunk size of the plain and no-alloc paths
+#ifndef BC_PREFETCH_GROUPS
+#define BC_PREFETCH_GROUPS 0 // 1: fetch the next item group before processing the current one
+#endif
+constexpr int kGrabDefault = 2;                // work items a warp takes per counter fetch
 #ifndef BC_BATCH_MIN_BLOCKS
 #define BC_BATCH_MIN_BLOCKS 4                  // resident CTAs per SM the batch kernel is built for
 #endif
@@ -39,7 +46,9 @@ enum : int {
   CNT_HEAVY = 5,     // heavy chunks processed (forward + backward)
   CNT_MAXLEV = 6,    // max level count (atomicMax)
   CNT_LEVELS = 7,    // level counts summed over batches
-  CNT_N = 8
+  CNT_BUSY = 8,      // phase-clock builds: warp cycles spent on step items
+  CNT_IDLE = 9,      // phase-clock builds: warp cycles from a warp's last item to the step's end
+  CNT_N = 10
 };
 
 constexpr int kGroup = 8;      // dense kernel: vertices per light work group
@@ -115,6 +124,7 @@ struct KParams {
   int32_t skip_block = -1;      // failure-injection hook (-1: none)
   unsigned long long *trace = nullptr; // optional [trace_cap][4] per-step records
   int32_t trace_cap = 0;
+  int32_t grab = kGrabDefault;  // work items per counter fetch
 };
 
 // Parameters of the many-small-graphs launch: one thread block per graph at a

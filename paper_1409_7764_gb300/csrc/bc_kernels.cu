@@ -88,18 +88,18 @@ __device__ __forceinline__ void enqueue_new(const KParams &p, const LevelView &l
 //
 // The work of one step is a list of items: the chunks of the level's heavy
 // entries first (largest units first), then its light entries.  Warps take
-// kGrab consecutive items per fetch from the step's counter and fetch the
+// `grab` consecutive items (KParams::grab) per fetch from the step's counter and fetch the
 // next group before processing the current one, so the counter round trip
 // overlaps useful work.
 
-// The first group of every warp is static (items gwarp*kGrab ..), so a step
+// The first group of every warp is static (items gwarp*grab ..), so a step
 // whose items all fit in one group per warp touches no counter; later groups
 // come from the step's counter.
 __device__ __forceinline__ int64_t next_items(unsigned long long *ctr, int64_t total,
-                                              int64_t stat, int lane) {
+                                              int64_t stat, int grab, int lane) {
   if (total <= stat) return total;
   unsigned long long v = 0;
-  if (lane == 0) v = atomicAdd(ctr, (unsigned long long)kGrab);
+  if (lane == 0) v = atomicAdd(ctr, (unsigned long long)grab);
   return stat + (int64_t)__shfl_sync(kFull, v, 0);
 }
 
@@ -123,42 +123,125 @@ __device__ __forceinline__ void zero_ring_ahead(Ctl *ctl, int step, int64_t gtid
   if (gtid == 0) ctl->work[(step + 2) & 3] = 0;
 }
 
-// Batch: discovery push over out-edges [eb, ee) of a frontier vertex with mask F.
-__device__ __forceinline__ void batch_discover(const KParams &p, const LevelView &lv, uint64_t F,
-                                               int64_t eb, int64_t ee, uint64_t *Bn, int lane) {
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    bool isnew = false;
-    int x = 0;
-    if (e < ee) {
-      x = __ldg(p.g.col_idx + e);
-      const uint64_t m = F & ~ldcg(p.w.vis + x);
-      if (m) {
-        const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(p.w.vis + x), m);
-        const uint64_t nb = m & ~old;
-        if (nb) {
-          const uint64_t oldB = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb);
-          isnew = (oldB == 0);
-        }
+constexpr int kStage = 64; // per-warp staging of newly discovered vertices
+
+// Appends a warp's staged vertices to the next level's queue with one tail
+// atomic; high-degree ones also get their chunk range in the level's list.
+__device__ __forceinline__ void stage_flush(const KParams &p, const LevelView &lv, const int *buf,
+                                            int nst, int lane) {
+  if (nst == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&p.w.ctl->tail, (unsigned long long)nst);
+  base = __shfl_sync(kFull, base, 0);
+  for (int i = lane; i < nst; i += kWarp) {
+    const long long pos = (long long)base + i;
+    if (pos >= p.w.cap) {
+      set_err(p.w.ctl, KERR_QUEUE);
+      continue;
+    }
+    const int x = buf[i];
+    p.w.qv[pos] = x;
+    const int nch = __ldg(p.g.nchunks + x);
+    if (nch > 0) {
+      const unsigned long long h =
+          atomicAdd(&p.w.hpack[lv.lvl + 1], (1ull << 32) | (unsigned long long)nch);
+      const int64_t hidx = lv.hoff_next + (int64_t)(h >> 32);
+      const int64_t cpre = (int64_t)(h & 0xffffffffull);
+      if (hidx >= p.w.hcap) {
+        set_err(p.w.ctl, KERR_HEAVY);
+        continue;
+      }
+      if (cpre + nch > p.w.chunk_cap) {
+        set_err(p.w.ctl, KERR_CHUNKS);
+        continue;
+      }
+      p.w.hq_e[hidx] = pos;
+      p.w.hq_c[hidx] = cpre;
+    }
+  }
+}
+
+// Stages the vertices this round discovered first (isnew lanes) in the
+// warp's shared buffer; the buffer is flushed to the queue when full and at
+// the end of the step.
+__device__ __forceinline__ void stage_new(const KParams &p, const LevelView &lv, bool isnew, int x,
+                                          int *buf, int &nst, int lane) {
+  const unsigned bal = __ballot_sync(kFull, isnew);
+  if (!bal) return;
+  const int c = __popc(bal);
+  if (nst + c > kStage) {
+    __syncwarp();
+    stage_flush(p, lv, buf, nst, lane);
+    __syncwarp();
+    nst = 0;
+  }
+  if (isnew) buf[nst + __popc(bal & lanemask_lt())] = x;
+  nst += c;
+}
+
+// Forward work of one frontier entry (mask F) at level l: the path-count
+// pull over in-edges [ib, ie) and the discovery push over out-edges
+// [ob, oe), advanced together 32 edges of each per round so that their
+// loads overlap.  A vertex x gets the bits F & ~(visited before level l |
+// level l | already marked for level l+1); the OR's old value tells the first
+// toucher, and is only read after the round's path-count gathers.
+__device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, uint64_t F,
+                                         int64_t ib, int64_t ie, int64_t ob, int64_t oe,
+                                         const uint64_t *A, const uint64_t *Pm, uint64_t *Bn,
+                                         int *stage, int &nst, int lane, uint64_t &s0,
+                                         uint64_t &s1, bool &o0, bool &o1,
+                                         unsigned long long &dag) {
+  constexpr int U = BC_GATHER_UNROLL;
+  const int64_t din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
+  const int64_t span = din > dout ? din : dout;
+  for (int64_t r = 0; r < span; r += kWarp) {
+    const int64_t t = r + lane;
+    const bool vi = t < din, vo = t < dout;
+    int u = 0, x = 0;
+    if (vi) u = __ldg(p.g.in_idx + ib + t);
+    if (vo) x = __ldg(p.g.col_idx + ob + t);
+    uint64_t P = 0, nb = 0;
+    if (vi) P = ldcg(Pm + u) & F;
+    if (vo) nb = F & ~(ldcg(p.w.vis + x) | ldcg(A + x) | ldcg(Bn + x));
+    uint64_t oldB = 1;
+    if (nb) oldB = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb);
+    unsigned bal = __ballot_sync(kFull, P != 0);
+    while (bal) {
+      const LanesU<U> q(bal);
+      uint64_t x0[U], x1[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int uu = shfl_or_zero(u, q.l[i]);
+        const uint64_t PP = shfl_or_zero(P, q.l[i]);
+        const uint64_t *row = p.w.sigma + (size_t)uu * kK;
+        x0[i] = ((PP >> lane) & 1ull) ? ldcg(row + lane) : 0ull;
+        x1[i] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : 0ull;
+        if (lane == 0) dag += __popcll(PP);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        sat_add(s0, x0[i], o0);
+        sat_add(s1, x1[i], o1);
       }
     }
-    enqueue_new(p, lv, isnew, x, lane);
+    stage_new(p, lv, nb != 0 && oldB == 0, x, stage, nst, lane);
   }
 }
 
 // Batch: closes entry v (mask F) at level l of the backward sweep given the
-// lane's successor sums a0/a1: dependencies, coefficients, BC, resets.
+// lane's successor sums a0/a1, its path counts sg0/sg1 and (lane 0) the
+// current BC value bcv, all loaded by the caller ahead of the successor scan:
+// dependencies, coefficients, BC, resets.
 template <typename DT>
 __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, uint64_t F, DT a0,
-                                             DT a1, uint64_t *Wn, int s_lo, int s_hi,
-                                             int lane) {
+                                             DT a1, uint64_t sg0, uint64_t sg1, double bcv,
+                                             uint64_t *Wn, int s_lo, int s_hi, int lane) {
   uint64_t *srow = p.w.sigma + (size_t)v * kK;
   DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * kK;
   double contrib = 0.0;
   const int n = p.g.n;
   if ((F >> lane) & 1ull) {
-    const uint64_t sg = ldcg(srow + lane);
-    const DT sf = u64_to<DT>(sg);
+    const DT sf = u64_to<DT>(sg0);
     const DT dl = sf * a0;
     crow[lane] = (DT(1) + dl) / sf;
     srow[lane] = 0;
@@ -166,13 +249,12 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, u
     if (p.dbg_d) {
       const size_t o = (size_t)lane * n + v;
       p.dbg_d[o] = lvl;
-      p.dbg_sigma[o] = sg;
+      p.dbg_sigma[o] = sg0;
       p.dbg_delta[o] = (double)dl;
     }
   }
   if ((F >> (lane + 32)) & 1ull) {
-    const uint64_t sg = ldcg(srow + 32 + lane);
-    const DT sf = u64_to<DT>(sg);
+    const DT sf = u64_to<DT>(sg1);
     const DT dl = sf * a1;
     crow[32 + lane] = (DT(1) + dl) / sf;
     srow[32 + lane] = 0;
@@ -180,18 +262,31 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, u
     if (p.dbg_d) {
       const size_t o = (size_t)(lane + 32) * n + v;
       p.dbg_d[o] = lvl;
-      p.dbg_sigma[o] = sg;
+      p.dbg_sigma[o] = sg1;
       p.dbg_delta[o] = (double)dl;
     }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(kFull, contrib, off);
   if (lane == 0) {
-    if (contrib != 0.0) p.bc[v] = ldcg(p.bc + v) + contrib;
+    if (contrib != 0.0) p.bc[v] = bcv + contrib;
     p.w.vis[v] = 0;
     if (Wn) Wn[v] = F;
   }
 }
+
+// Loads of an entry's own path counts and BC value, issued before its
+// successor scan so they overlap it.
+struct EntryOwn {
+  uint64_t sg0, sg1;
+  double bcv;
+  __device__ __forceinline__ EntryOwn(const KParams &p, int v, uint64_t F, int lane) {
+    const uint64_t *srow = p.w.sigma + (size_t)v * kK;
+    sg0 = ((F >> lane) & 1ull) ? ldcg(srow + lane) : 0ull;
+    sg1 = ((F >> (lane + 32)) & 1ull) ? ldcg(srow + 32 + lane) : 0ull;
+    bcv = lane == 0 ? ldcg(p.bc + v) : 0.0;
+  }
+};
 
 // Header of up to four consecutive queue entries, loaded with one round of
 // lane-parallel loads: lane 4f+i holds field f of entry i.
@@ -296,6 +391,10 @@ __device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, cons
     atomicAdd(job_cnt + CNT_DAG, cnt.dag);
     atomicAdd(job_cnt + CNT_REACHED, cnt.reached);
     atomicAdd(job_cnt + CNT_HEAVY, cnt.heavy);
+    if (BC_PHASE_CLOCKS) {
+      atomicAdd(job_cnt + CNT_BUSY, cnt.busy);
+      atomicAdd(job_cnt + CNT_IDLE, cnt.idle);
+    }
   }
 }
 
@@ -304,7 +403,7 @@ __device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, cons
 // state.  Warp counters accumulate into cnt.
 template <typename DT, typename Scope>
 __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
-                                           unsigned long long *wacc, Counters &cnt) {
+                                           unsigned long long *wacc, int *stage, Counters &cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)sc.size() * kWarpsPerBlock;
@@ -385,11 +484,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
     const int64_t total = lv.nhc + (lv.hi - lv.lo);
     trace_step(p, step, l, total, lv.nhc, gtid);
     HeavyCursor hc;
-    const int64_t stat = nwarps * kGrab;
-    int64_t base = gwarp * kGrab;
+    int nst = 0; // staged new vertices of this warp
+    const int grab = p.grab;
+    const int64_t stat = nwarps * grab;
+    int64_t base = gwarp * grab;
+    const long long t_step = phase_clock();
     while (base < total) {
-      const int64_t next = next_items(ctr, total, stat, lane);
-      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
+      const int64_t end = base + grab < total ? base + grab : total;
       for (int64_t item = base; item < end && item < lv.nhc; ++item) {
         // one chunk of a heavy entry
         hc.seek(p, lv, item, lane);
@@ -405,11 +507,11 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
         const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
         uint64_t s0 = 0, s1 = 0;
         bool o0 = false, o1 = false;
-        if (l > 0 && a < indeg)
-          batch_pull_sigma(p, F, is + a, is + (b < indeg ? b : indeg), Pm, lane, wacc, s0, s1,
-                           o0, o1, cnt.dag);
-        if (b > indeg)
-          batch_discover(p, lv, F, rs + (a > indeg ? a - indeg : 0), rs + (b - indeg), Bn, lane);
+        const int64_t ib = is + (a < indeg ? a : indeg), ie2 = is + (b < indeg ? b : indeg);
+        const int64_t obg = rs + (a > indeg ? a - indeg : 0);
+        const int64_t oen = rs + (b > indeg ? b - indeg : 0);
+        fwd_scan(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage, nst, lane,
+                 s0, s1, o0, o1, cnt.dag);
         if (lane == 0) {
           cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
           cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
@@ -444,6 +546,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
           if (lane == 0) {
             p.w.harrive[h] = 0;
             p.w.qm[e] = F;
+            p.w.vis[w] = ldcg(p.w.vis + w) | F;
             cnt.entries++;
             cnt.reached += __popcll(F);
           }
@@ -461,15 +564,15 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
           const int w = (int)hd.field(6, i);
           uint64_t s0 = 0, s1 = 0;
           bool o0 = false, o1 = false;
+          fwd_scan(p, lv, F, l > 0 ? is : 0, l > 0 ? ie : 0, rs, re, A, Pm, Bn, stage, nst, lane,
+                   s0, s1, o0, o1, cnt.dag);
           if (l == 0) {
             s0 = 1;
             s1 = 1;
-          } else {
-            batch_pull_sigma(p, F, is, ie, Pm, lane, wacc, s0, s1, o0, o1, cnt.dag);
           }
           batch_store_sigma(p, w, F, s0, s1, o0, o1, lane);
-          batch_discover(p, lv, F, rs, re, Bn, lane);
           if (lane == 0) {
+            p.w.vis[w] = ldcg(p.w.vis + w) | F;
             p.w.qm[e0 + i] = F;
             cnt.entries++;
             cnt.reached += __popcll(F);
@@ -478,9 +581,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
           }
         }
       }
-      base = next;
+      base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
+    __syncwarp();
+    stage_flush(p, lv, stage, nst, lane);
+    const long long t_done = phase_clock();
     if (!sc.sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    cnt.busy += (unsigned long long)(t_done - t_step);
+    cnt.idle += (unsigned long long)(phase_clock() - t_done);
     ++step;
     const int64_t nh = ldcg(p.w.qoff + l + 2);
     if (nh == lv.hi) {
@@ -528,11 +636,13 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
     const int64_t total = bl.nhc + (bl.hi - bl.lo);
     trace_step(p, step, -1 - l, total, bl.nhc, gtid);
     HeavyCursor hc;
-    const int64_t stat = nwarps * kGrab;
-    int64_t base = gwarp * kGrab;
+    const int grab = p.grab;
+    const int64_t stat = nwarps * grab;
+    int64_t base = gwarp * grab;
+    const long long t_step = phase_clock();
     while (base < total) {
-      const int64_t next = next_items(ctr, total, stat, lane);
-      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
+      const int64_t end = base + grab < total ? base + grab : total;
       for (int64_t item = base; item < end && item < bl.nhc; ++item) {
         hc.seek(p, bl, item, lane);
         const int64_t h = hc.h;
@@ -565,7 +675,8 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
             t0 += ldcg(pp + (size_t)cc * kK + lane);
             t1 += ldcg(pp + (size_t)cc * kK + 32 + lane);
           }
-          batch_finish<DT>(p, l, v, F, t0, t1, Wn, s_lo, s_hi, lane);
+          const EntryOwn own(p, v, F, lane);
+          batch_finish<DT>(p, l, v, F, t0, t1, own.sg0, own.sg1, own.bcv, Wn, s_lo, s_hi, lane);
           if (lane == 0) p.w.harrive[h] = 0;
         }
       }
@@ -578,17 +689,21 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
           const uint64_t F = hd.field(0, i);
           const int64_t rs = (int64_t)hd.field(1, i), re = (int64_t)hd.field(2, i);
           const int v = (int)hd.field(4, i);
+          const EntryOwn own(p, v, F, lane);
           DT a0 = 0, a1 = 0;
           if (!deepest) {
             batch_pull_delta<DT>(p, F, rs, re, Dn, lane, reinterpret_cast<DT *>(wacc), a0, a1);
             if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
           }
-          batch_finish<DT>(p, l, v, F, a0, a1, Wn, s_lo, s_hi, lane);
+          batch_finish<DT>(p, l, v, F, a0, a1, own.sg0, own.sg1, own.bcv, Wn, s_lo, s_hi, lane);
         }
       }
-      base = next;
+      base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
+    const long long t_done = phase_clock();
     if (!sc.sync(ctl, p.timeout_ns)) return;
+    cnt.busy += (unsigned long long)(t_done - t_step);
+    cnt.idle += (unsigned long long)(phase_clock() - t_done);
     ++step;
   }
 
@@ -606,8 +721,9 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
 template <typename DT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
   __shared__ unsigned long long s_acc[kWarpsPerBlock][kK]; // warp-private gather rows
+  __shared__ int s_stage[kWarpsPerBlock][kStage];           // warp-private new-vertex stage
   Counters cnt;
-  batch_body<DT>(p, GridScope(), s_acc[threadIdx.x >> 5], cnt);
+  batch_body<DT>(p, GridScope(), s_acc[threadIdx.x >> 5], s_stage[threadIdx.x >> 5], cnt);
   flush_counters(p.job_cnt, cnt, threadIdx.x & 31);
 }
 
@@ -618,6 +734,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
 template <typename DT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const ManyParams mp) {
   __shared__ unsigned long long s_acc[kWarpsPerBlock][kK];
+  __shared__ int s_stage[kWarpsPerBlock][kStage];
   __shared__ int s_item;
   Counters cnt;
   KParams p = mp.base;
@@ -636,7 +753,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
       p.src = mp.iota + b0;
       p.k = p.g.n - b0 < mp.kb ? p.g.n - b0 : mp.kb;
       p.src_base = off + b0;
-      batch_body<DT>(p, CtaScope(), s_acc[threadIdx.x >> 5], cnt);
+      batch_body<DT>(p, CtaScope(), s_acc[threadIdx.x >> 5], s_stage[threadIdx.x >> 5], cnt);
       __syncthreads();
       if (read_err(p.w.ctl)) break;
     }
@@ -769,11 +886,12 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
     const int64_t total = lv.nhc + (lv.hi - lv.lo);
     trace_step(p, step, l, total, lv.nhc, gtid);
     HeavyCursor hc;
-    const int64_t stat = nwarps * kGrab;
-    int64_t base = gwarp * kGrab;
+    const int grab = p.grab;
+    const int64_t stat = nwarps * grab;
+    int64_t base = gwarp * grab;
     while (base < total) {
-      const int64_t next = next_items(ctr, total, stat, lane);
-      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
+      const int64_t end = base + grab < total ? base + grab : total;
       for (int64_t item = base; item < end; ++item) {
         if (item < lv.nhc) {
           hc.seek(p, lv, item, lane);
@@ -842,7 +960,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
           plain_discover(p, lv, rs, re, lane);
         }
       }
-      base = next;
+      base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
     if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
     ++step;
@@ -883,11 +1001,12 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
     const int64_t total = bl.nhc + (bl.hi - bl.lo);
     trace_step(p, step, -1 - l, total, bl.nhc, gtid);
     HeavyCursor hc;
-    const int64_t stat = nwarps * kGrab;
-    int64_t base = gwarp * kGrab;
+    const int grab = p.grab;
+    const int64_t stat = nwarps * grab;
+    int64_t base = gwarp * grab;
     while (base < total) {
-      const int64_t next = next_items(ctr, total, stat, lane);
-      const int64_t end = base + kGrab < total ? base + kGrab : total;
+      const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
+      const int64_t end = base + grab < total ? base + grab : total;
       for (int64_t item = base; item < end; ++item) {
         if (item < bl.nhc) {
           hc.seek(p, bl, item, lane);
@@ -931,7 +1050,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
           if (lane == 0) plain_finish<DT>(p, l, v, acc, s);
         }
       }
-      base = next;
+      base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
     if (!grid_sync(ctl, p.timeout_ns)) return;
     ++step;
