@@ -225,6 +225,64 @@ template <int U> struct LanesU {
   }
 };
 
+// Full-width gathers: per step up to U of the round's shortest-path edges
+// (lanes with a non-empty mask, in lane order), lane j loading sources j and
+// 32+j of each edge's row when the mask has them; loads of the U edges are in
+// flight together and are added in edge order.
+
+// Path counts, 64-bit sums with the carry recorded (a carry means the true
+// count reached 2^64).
+template <int U>
+__device__ __forceinline__ void gather_counts_full(const uint64_t *base, int u, uint64_t P,
+                                                   int lane, uint64_t &s0, uint64_t &s1,
+                                                   bool &c0, bool &c1) {
+  unsigned bal = __ballot_sync(kFull, P != 0);
+  while (bal) {
+    const LanesU<U> q(bal);
+    uint64_t x0[U], x1[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int uu = shfl_or_zero(u, q.l[i]);
+      const uint64_t PP = shfl_or_zero(P, q.l[i]);
+      const uint64_t *row = base + (size_t)uu * kK;
+      x0[i] = ((PP >> lane) & 1ull) ? ldcg(row + lane) : 0ull;
+      x1[i] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      s0 += x0[i];
+      c0 |= s0 < x0[i];
+      s1 += x1[i];
+      c1 |= s1 < x1[i];
+    }
+  }
+}
+
+// Dependency coefficients, added in edge order.
+template <int U, typename DT>
+__device__ __forceinline__ void gather_coeffs_full(const DT *base, int x, uint64_t S, int lane,
+                                                   DT &a0, DT &a1) {
+  unsigned bal = __ballot_sync(kFull, S != 0);
+  while (bal) {
+    const LanesU<U> q(bal);
+    DT y0[U], y1[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int xx = shfl_or_zero(x, q.l[i]);
+      const uint64_t SS = shfl_or_zero(S, q.l[i]);
+      const DT *row = base + (size_t)xx * kK;
+      y0[i] = ((SS >> lane) & 1ull) ? ldcg(row + lane) : DT(0);
+      y1[i] = ((SS >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : DT(0);
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i)
+      if (q.l[i] >= 0) {
+        a0 += y0[i];
+        a1 += y1[i];
+      }
+  }
+}
+
 // Batch: path-count pull over in-edges [eb, ee) of entry w (mask F) from the
 // level l-1 dense mask Pm.  Returns the counts of sources lane and lane+32,
 // saturated at 2^64-1 on carry.
@@ -267,6 +325,7 @@ __device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, i
 #else
   (void)wacc;
   constexpr int U = BC_GATHER_UNROLL;
+  unsigned long long nd = 0;
   for (int64_t base = eb; base < ee; base += kWarp) {
     const int64_t e = base + lane;
     int u = 0;
@@ -275,26 +334,11 @@ __device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, i
       u = __ldg(p.g.in_idx + e);
       P = ldcg(Pm + u) & F;
     }
-    unsigned bal = __ballot_sync(kFull, P != 0);
-    while (bal) {
-      const LanesU<U> q(bal);
-      uint64_t x0[U], x1[U];
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        const int uu = shfl_or_zero(u, q.l[i]);
-        const uint64_t PP = shfl_or_zero(P, q.l[i]);
-        const uint64_t *row = p.w.sigma + (size_t)uu * kK;
-        x0[i] = ((PP >> lane) & 1ull) ? ldcg(row + lane) : 0ull;
-        x1[i] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : 0ull;
-        if (lane == 0) dag += __popcll(PP);
-      }
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        sat_add(s0, x0[i], o0);
-        sat_add(s1, x1[i], o1);
-      }
-    }
+    nd += __popcll(P);
+    gather_counts_full<U>(p.w.sigma, u, P, lane, s0, s1, o0, o1);
   }
+  nd = warp_sum_u64(nd);
+  if (lane == 0) dag += nd;
 #endif
 }
 
@@ -334,26 +378,7 @@ __device__ __forceinline__ void batch_pull_delta(const KParams &p, uint64_t F, i
       x = __ldg(p.g.col_idx + e);
       S = ldcg(Dn + x) & F;
     }
-    unsigned bal = __ballot_sync(kFull, S != 0);
-    while (bal) {
-      const LanesU<U> q(bal);
-      DT y0[U], y1[U];
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        const int xx = shfl_or_zero(x, q.l[i]);
-        const uint64_t SS = shfl_or_zero(S, q.l[i]);
-        const DT *row = cdep + (size_t)xx * kK;
-        y0[i] = ((SS >> lane) & 1ull) ? ldcg(row + lane) : DT(0);
-        y1[i] = ((SS >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : DT(0);
-      }
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        if (q.l[i] >= 0) {
-          a0 += y0[i];
-          a1 += y1[i];
-        }
-      }
-    }
+    gather_coeffs_full<U, DT>(cdep, x, S, lane, a0, a1);
   }
 #endif
 }
@@ -363,8 +388,8 @@ __device__ __forceinline__ void batch_store_sigma(const KParams &p, int w, uint6
                                                   uint64_t s0, uint64_t s1, bool o0, bool o1,
                                                   int lane) {
   uint64_t *row = p.w.sigma + (size_t)w * kK;
-  if ((F >> lane) & 1ull) row[lane] = s0;
-  if ((F >> (lane + 32)) & 1ull) row[32 + lane] = s1;
+  if ((F >> lane) & 1ull) row[lane] = o0 ? ~0ull : s0;
+  if ((F >> (lane + 32)) & 1ull) row[32 + lane] = o1 ? ~0ull : s1;
   const uint64_t ob =
       ((uint64_t)__ballot_sync(kFull, o0) | ((uint64_t)__ballot_sync(kFull, o1) << 32)) & F;
   if (ob && lane == 0) atomicOr(&p.w.ctl->ovf, (unsigned long long)ob);

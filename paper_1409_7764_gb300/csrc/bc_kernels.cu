@@ -205,25 +205,8 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
     if (vo) nb = F & ~(ldcg(p.w.vis + x) | ldcg(A + x) | ldcg(Bn + x));
     uint64_t oldB = 1;
     if (nb) oldB = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb);
-    unsigned bal = __ballot_sync(kFull, P != 0);
-    while (bal) {
-      const LanesU<U> q(bal);
-      uint64_t x0[U], x1[U];
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        const int uu = shfl_or_zero(u, q.l[i]);
-        const uint64_t PP = shfl_or_zero(P, q.l[i]);
-        const uint64_t *row = p.w.sigma + (size_t)uu * kK;
-        x0[i] = ((PP >> lane) & 1ull) ? ldcg(row + lane) : 0ull;
-        x1[i] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : 0ull;
-        if (lane == 0) dag += __popcll(PP);
-      }
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        sat_add(s0, x0[i], o0);
-        sat_add(s1, x1[i], o1);
-      }
-    }
+    dag += __popcll(P); // per lane; the warp's counters are summed at the flush
+    gather_counts_full<U>(p.w.sigma, u, P, lane, s0, s1, o0, o1);
     stage_new(p, lv, nb != 0 && oldB == 0, x, stage, nst, lane);
   }
 }
@@ -381,9 +364,15 @@ struct CtaScope {
   }
 };
 
-// Flushes a warp's counters into the job counters (lane 0 holds them).
-__device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, const Counters &cnt,
+// Sums a warp's per-lane counters and adds them to the job counters.
+__device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, Counters cnt,
                                                int lane) {
+  cnt.entries = warp_sum_u64(cnt.entries);
+  cnt.out_e = warp_sum_u64(cnt.out_e);
+  cnt.in_e = warp_sum_u64(cnt.in_e);
+  cnt.dag = warp_sum_u64(cnt.dag);
+  cnt.reached = warp_sum_u64(cnt.reached);
+  cnt.heavy = warp_sum_u64(cnt.heavy);
   if (lane == 0) {
     atomicAdd(job_cnt + CNT_ENTRIES, cnt.entries);
     atomicAdd(job_cnt + CNT_OUT_EDGES, cnt.out_e);
@@ -1060,14 +1049,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
     const int64_t q2 = L >= 2 ? ldcg(p.w.qoff + 2) : ldcg(p.w.qoff + 1);
     for (int64_t i = gtid; i < q2; i += nthr) p.w.d[ldcg(p.w.qv + i)] = -1;
   }
-  if (lane == 0) {
-    atomicAdd(p.job_cnt + CNT_ENTRIES, cnt.entries);
-    atomicAdd(p.job_cnt + CNT_OUT_EDGES, cnt.out_e);
-    atomicAdd(p.job_cnt + CNT_IN_EDGES, cnt.in_e);
-    atomicAdd(p.job_cnt + CNT_DAG, cnt.dag);
-    atomicAdd(p.job_cnt + CNT_REACHED, cnt.reached);
-    atomicAdd(p.job_cnt + CNT_HEAVY, cnt.heavy);
-  }
+  flush_counters(p.job_cnt, cnt, lane);
 }
 
 __global__ void scale_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t n,
