@@ -291,7 +291,8 @@ def run_ours(args, w, name):
     stream = torch.cuda.current_stream()
     ctx = bc.Context(local, stream=stream)
     fp64 = bool(w.get("fp64", False)) or args.fp64
-    opts = dict(schedule=args.schedule or w["schedule"], batch_k=w["batch_k"], delta_fp64=fp64)
+    opts = dict(schedule=args.schedule or w["schedule"], batch_k=w["batch_k"], delta_fp64=fp64,
+                keep_source_order=args.keep_source_order)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
     out = torch.zeros(g.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -403,7 +404,9 @@ def run_ours(args, w, name):
             "data": "synthetic",
             "config": dict(describe(name, w, g, len(srcs)),
                            l2="flushed between timed steps (512 MiB write)",
-                           parallelism=f"source shards x{world}"),
+                           parallelism=f"source shards x{world}",
+                           source_order="given" if args.keep_source_order
+                           else "grouped (library batch composition)"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
@@ -463,7 +466,7 @@ def run_many(args):
     hs = [ctx.create_graph(g.row_ptr, g.col_idx) for g in graphs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        ctx.exact_many(hs, delta_fp64=fp64)
+        ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -473,7 +476,7 @@ def run_many(args):
         flush.fill_(1)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        ctx.exact_many(hs, delta_fp64=fp64)
+        ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order)
         e.record(stream)
         torch.cuda.synchronize()
         ms.append(s.elapsed_time(e))
@@ -624,6 +627,8 @@ def main():
                     help="override the workload's schedule")
     ap.add_argument("--max-sources", type=int, default=0,
                     help="use only the first N sources of the workload (profiling runs)")
+    ap.add_argument("--keep-source-order", action="store_true",
+                    help="batches take the sources in the given order instead of the library's grouping")
     ap.add_argument("--many-count", type=int, default=10000)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-seed", type=int, default=1)

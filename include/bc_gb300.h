@@ -80,6 +80,13 @@ typedef struct {
   int32_t normalize;     /* 0: raw sums; 1: divide by (n-1)(n-2) when n > 2 */
   int32_t scale_sampled; /* 0: raw sum over the given sources; 1: multiply by n/k */
   int32_t out_device;    /* 0: bc_out is host memory; 1: device memory */
+  int32_t source_order;  /* batched schedules: 0 (default) = the library composes the batches,
+                            grouping sources whose traversals line up (sources without
+                            out-edges last, the others by the number of two-hop walks,
+                            descending), so fewer (vertex, level) frontier entries and
+                            edge scans are shared by more sources; 1 = batches take the
+                            sources in the given order.  The result is the same sum over
+                            the sources, up to floating-point summation order. */
 } bc_opts;
 
 /* Per-call statistics.  Counters feed the bytes model of the roofline. */

@@ -54,7 +54,7 @@ def _check(rc: int, what: str):
 
 def make_opts(delta_fp64: bool = False, batch_k: int = 0, schedule="auto",
               normalize: bool = False, scale_sampled: bool = False,
-              out_device: bool = False) -> bc_opts:
+              out_device: bool = False, keep_source_order: bool = False) -> bc_opts:
     o = bc_opts()
     o.delta_fp64 = int(bool(delta_fp64))
     o.batch_k = int(batch_k)
@@ -62,6 +62,7 @@ def make_opts(delta_fp64: bool = False, batch_k: int = 0, schedule="auto",
     o.normalize = int(bool(normalize))
     o.scale_sampled = int(bool(scale_sampled))
     o.out_device = int(bool(out_device))
+    o.source_order = int(bool(keep_source_order))
     return o
 
 

@@ -79,6 +79,8 @@ struct GraphRec {
   // per-graph tuning of the batched kernel: chunk variant and grab size
   // (-1: not tuned yet)
   std::atomic<int> tuned{-1};
+  // batch composition: every vertex in grouping order, and its position there
+  std::vector<int32_t> order, pos;
 };
 
 // Launch configurations the tuner compares: (chunk variant, items per fetch).
@@ -296,7 +298,8 @@ bool opts_valid(const bc_opts &o) {
          o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_DENSE &&
          (o.normalize == 0 || o.normalize == 1) &&
          (o.scale_sampled == 0 || o.scale_sampled == 1) &&
-         (o.out_device == 0 || o.out_device == 1);
+         (o.out_device == 0 || o.out_device == 1) &&
+         (o.source_order == 0 || o.source_order == 1);
 }
 
 int resolve_schedule(const bc_opts &o, const GraphDev &) {
@@ -389,6 +392,33 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
       }
     }
   }
+  // Batch composition order of the vertices as sources.  A batch advances
+  // the union of its sources' frontiers, so its cost grows with the (vertex,
+  // level) entries and edge scans of that union; sources whose traversals
+  // reach the same vertices at the same depths share them.  The key: sources
+  // without out-edges (a traversal of one vertex) last, the others by the
+  // number of two-hop walks leaving them (a proxy for how fast the traversal
+  // fans out into the graph's core), descending; ties by out-degree, then
+  // vertex id.
+  std::vector<int32_t> order((size_t)n), pos((size_t)n);
+  {
+    std::vector<int64_t> two((size_t)n, 0);
+    for (int32_t v = 0; v < n; ++v) {
+      int64_t t = 0;
+      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e)
+        t += rp[(size_t)ci[(size_t)e] + 1] - rp[ci[(size_t)e]];
+      two[(size_t)v] = t;
+    }
+    for (int32_t v = 0; v < n; ++v) order[(size_t)v] = v;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      const int32_t da = rp[(size_t)a + 1] - rp[a], db = rp[(size_t)b + 1] - rp[b];
+      if ((da == 0) != (db == 0)) return db == 0;
+      if (two[(size_t)a] != two[(size_t)b]) return two[(size_t)a] > two[(size_t)b];
+      if (da != db) return da > db;
+      return a < b;
+    });
+    for (int32_t i = 0; i < n; ++i) pos[(size_t)order[(size_t)i]] = i;
+  }
   int64_t hv = 0, hc = 0; // maxima over the variants (workspace sizing)
   for (int c = 0; c < kChunkVariants; ++c) {
     hv = std::max(hv, hvv[c]);
@@ -402,7 +432,8 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   int32_t *d_ip = c.take<int32_t>((size_t)n + 1);
   int32_t *d_ii = c.take<int32_t>((size_t)me);
   int32_t *d_nc = c.take<int32_t>((size_t)n * kChunkVariants);
-  (void)d_rp; (void)d_ci; (void)d_ip; (void)d_ii; (void)d_nc;
+  int32_t *d_ord = c.take<int32_t>((size_t)n);
+  (void)d_rp; (void)d_ci; (void)d_ip; (void)d_ii; (void)d_nc; (void)d_ord;
   const size_t bytes = align_up(c.off, 256);
   if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
   void *mem = nullptr;
@@ -414,6 +445,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   d_ip = c2.take<int32_t>((size_t)n + 1);
   d_ii = c2.take<int32_t>((size_t)me);
   d_nc = c2.take<int32_t>((size_t)n * kChunkVariants);
+  d_ord = c2.take<int32_t>((size_t)n);
   cudaStream_t st = ctx->stream;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
@@ -423,6 +455,8 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   for (int c = 0; c < kChunkVariants && e == cudaSuccess && n; ++c)
     e = cudaMemcpyAsync(d_nc + (size_t)c * n, nchv[(size_t)c].data(), sizeof(int32_t) * (size_t)n,
                         cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && n)
+    e = cudaMemcpyAsync(d_ord, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFree(mem);
@@ -439,6 +473,9 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   g->dev.nchunks = d_nc; // variant 0 until tuned
   g->dev.heavy_vertices = hv;
   g->dev.heavy_chunks = hc;
+  g->dev.order = d_ord;
+  g->order = std::move(order);
+  g->pos = std::move(pos);
   for (int c = 0; c < kChunkVariants; ++c) {
     g->nch_variant[c] = d_nc + (size_t)c * n;
     g->heavy_v[c] = hvv[c];
@@ -592,10 +629,22 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   BC_TRY(cudaMallocHost(&j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
   BC_TRY(cudaMallocHost(&j->h_ovf, (size_t)std::max<int64_t>(k, 1)));
   j->h_err = reinterpret_cast<int *>(j->h_cnt + CNT_N);
-  if (j->all_sources)
-    for (int64_t i = 0; i < k; ++i) j->h_src[i] = (int32_t)i;
-  else if (k)
+  // batch composition (bc_opts.source_order); debug exports keep the given
+  // order, since their rows follow it
+  const bool grouped = batch && !dbg && j->opts.source_order == 0 && k > kb;
+  if (j->all_sources) {
+    if (grouped)
+      std::memcpy(j->h_src, j->g->order.data(), sizeof(int32_t) * (size_t)k);
+    else
+      for (int64_t i = 0; i < k; ++i) j->h_src[i] = (int32_t)i;
+  } else if (k) {
     std::memcpy(j->h_src, j->src.data(), sizeof(int32_t) * (size_t)k);
+    if (grouped) {
+      const int32_t *pos = j->g->pos.data();
+      std::stable_sort(j->h_src, j->h_src + k,
+                       [pos](int32_t a, int32_t b) { return pos[a] < pos[b]; });
+    }
+  }
   BC_TRY(cudaMallocAsync(&j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));
   BC_TRY(cudaMallocAsync(&j->d_bc, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
   BC_TRY(cudaMallocAsync(&j->d_ovf, (size_t)std::max<int64_t>(k, 1), st));
@@ -666,7 +715,11 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
       if (!tev[bi]) BC_TRY(cudaEventCreate(&tev[bi]));
       BC_TRY(cudaEventRecord(tev[bi], st));
       if (bi < kNumTune * kTuneRounds) {
-        apply((int)(bi % kNumTune));
+        // rounds alternate direction (c0 c1 c2 c3 c3 c2 c1 c0 ...), so a
+        // trend in batch cost along the source order weighs every candidate
+        // alike
+        const int64_t r = bi / kNumTune, c = bi % kNumTune;
+        apply((int)(r % 2 == 0 ? c : kNumTune - 1 - c));
       } else {
         // all trial batches are enqueued: pick the fastest candidate
         BC_TRY(cudaEventSynchronize(tev[bi]));
@@ -674,7 +727,8 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
         for (int64_t t = 0; t < kNumTune * kTuneRounds; ++t) {
           float ms = 0.f;
           BC_TRY(cudaEventElapsedTime(&ms, tev[t], tev[t + 1]));
-          sum[t % kNumTune] += ms;
+          const int64_t r = t / kNumTune, c = t % kNumTune;
+          sum[r % 2 == 0 ? c : kNumTune - 1 - c] += ms;
         }
         int best = 0;
         for (int c = 1; c < kNumTune; ++c)
@@ -1300,6 +1354,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     mp.out = d_out;
     mp.next = d_next;
     mp.kb = kb;
+    mp.grouped = o.source_order == 0 ? 1 : 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);

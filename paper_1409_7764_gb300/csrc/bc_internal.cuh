@@ -77,6 +77,7 @@ struct GraphDev {
   const int32_t *nchunks = nullptr;
   int64_t heavy_vertices = 0; // vertices with nchunks > 0
   int64_t heavy_chunks = 0;   // sum of nchunks
+  const int32_t *order = nullptr; // all vertices in batch-composition order (exact BC)
 };
 
 // Device workspace of one in-flight batch (or one plain source).
@@ -136,7 +137,8 @@ struct ManyParams {
   const int64_t *out_off = nullptr; // [count] offset of each graph's BC (and source flags)
   int32_t count = 0;
   const Work *works = nullptr;    // [grid] one workspace per thread block
-  const int32_t *iota = nullptr;  // [max n] 0, 1, 2, ...: the sources of exact BC
+  const int32_t *iota = nullptr;  // [max n] 0, 1, 2, ...: the sources of exact BC in given order
+  int32_t grouped = 1;            // 1: batches take the sources in GraphDev::order
   double *out = nullptr;          // [sum of n]
   unsigned *next = nullptr;       // graph counter
   int32_t kb = kK;                // sources per batch

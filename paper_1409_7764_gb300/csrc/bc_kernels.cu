@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
     const int64_t off = __ldg(mp.out_off + gi);
     p.bc = mp.out + off;
     for (int b0 = 0; b0 < p.g.n; b0 += mp.kb) {
-      p.src = mp.iota + b0;
+      p.src = (mp.grouped && p.g.order ? p.g.order : mp.iota) + b0;
       p.k = p.g.n - b0 < mp.kb ? p.g.n - b0 : mp.kb;
       p.src_base = off + b0;
       batch_body<DT>(p, CtaScope(), s_acc[threadIdx.x >> 5], s_stage[threadIdx.x >> 5], cnt);

@@ -261,3 +261,27 @@ def test_batched_schedules_pick_their_kernel(ctx, schedule, kind):
         assert_bc_close(ctx.exact(G, schedule=schedule, delta_fp64=fp64), ref, fp64)
         assert ctx.last_stats()["kernel_kind"] == kind
     ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_batch_composition(ctx, fp64):
+    """The library's grouping of sources into batches (default) and the given
+    order compute the same BC within the parity tolerance, both against the
+    oracle, for exact and sampled jobs (duplicates included); grouping shares
+    frontier entries among more sources, so it needs fewer of them."""
+    g = bcgen.rmat(12, 16, seed=5)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    grouped = ctx.exact(G, delta_fp64=fp64).copy()
+    e_grouped = ctx.last_stats()["frontier_entries"]
+    given = ctx.exact(G, delta_fp64=fp64, keep_source_order=True).copy()
+    e_given = ctx.last_stats()["frontier_entries"]
+    assert_bc_close(grouped, ref, fp64)
+    assert_bc_close(given, ref, fp64)
+    assert e_grouped < e_given
+    srcs = np.concatenate([bcgen.sample_sources(g.n, 700, seed=2), [9, 9, 17]]).astype(np.int32)
+    sref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    assert_bc_close(ctx.sources(G, srcs, delta_fp64=fp64), sref, fp64)
+    assert_bc_close(ctx.sources(G, srcs, delta_fp64=fp64, keep_source_order=True), sref, fp64)
+    assert_bc_close(ctx.sources(G, srcs[::-1].copy(), delta_fp64=fp64), sref, fp64)
+    ctx.destroy_graph(G)
