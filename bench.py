@@ -40,16 +40,16 @@ L2_FLUSH_BYTES = 512 << 20
 
 WORKLOADS = {
     # R-MAT scale 16, edge factor 16, all 65,536 sources in batches of 64
-    "rmat16-exact": dict(kind="rmat", scale=16, ef=16, seed=1, sources="all", batch_k=64,
+    "rmat16-exact": dict(kind="rmat", scale=16, ef=16, seed=1, sources="all", batch_k=0,
                          schedule="batch"),
     # R-MAT scale 20, edge factor 16, 4096 / 1024 seeded uniform sources
     "rmat20-sampled4096": dict(kind="rmat", scale=20, ef=16, seed=1, sources=4096,
-                               src_seed=1, batch_k=64, schedule="batch"),
+                               src_seed=1, batch_k=0, schedule="batch"),
     "rmat20-sampled1024": dict(kind="rmat", scale=20, ef=16, seed=1, sources=1024,
-                               src_seed=1, batch_k=64, schedule="batch"),
+                               src_seed=1, batch_k=0, schedule="batch"),
     # directed preferential attachment n = 2^20, 8 out-edges, 4096 sources
     "ba20-sampled4096": dict(kind="ba", n=1 << 20, out=8, seed=1, sources=4096, src_seed=1,
-                             batch_k=64, schedule="batch"),
+                             batch_k=0, schedule="batch"),
     # R-MAT scale 10, edge factor 8, all 1024 sources, one source per launch
     "rmat10-exact-plain": dict(kind="rmat", scale=10, ef=8, seed=1, sources="all", batch_k=1,
                                schedule="plain", fp64=True),
@@ -291,7 +291,8 @@ def run_ours(args, w, name):
     stream = torch.cuda.current_stream()
     ctx = bc.Context(local, stream=stream)
     fp64 = bool(w.get("fp64", False)) or args.fp64
-    opts = dict(schedule=args.schedule or w["schedule"], batch_k=w["batch_k"], delta_fp64=fp64,
+    opts = dict(schedule=args.schedule or w["schedule"], batch_k=w["batch_k"],
+                delta_fp64=fp64,
                 keep_source_order=args.keep_source_order)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
     out = torch.zeros(g.n, dtype=torch.float64, device="cuda")
@@ -403,6 +404,7 @@ def run_ours(args, w, name):
             "vs_baseline": None, "dtype": "u64+f64" if fp64 else "u64+f32",
             "data": "synthetic",
             "config": dict(describe(name, w, g, len(srcs)),
+                           batch_k=int(st.get("batch_sources") or w["batch_k"]),
                            l2="flushed between timed steps (512 MiB write)",
                            parallelism=f"source shards x{world}",
                            source_order="given" if args.keep_source_order
@@ -421,7 +423,8 @@ def run_ours(args, w, name):
             "counters": {k: st[k] for k in ("frontier_entries", "scanned_in_edges",
                                             "scanned_out_edges", "dag_pairs", "reached_pairs",
                                             "heavy_chunks", "max_levels", "levels_sum",
-                                            "batches", "kernel_kind", "chunk_edges", "grab")},
+                                            "batches", "kernel_kind", "chunk_edges", "grab",
+                                            "batch_sources", "mask_words")},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -627,6 +630,8 @@ def main():
                     help="override the workload's schedule")
     ap.add_argument("--max-sources", type=int, default=0,
                     help="use only the first N sources of the workload (profiling runs)")
+    ap.add_argument("--batch-k", type=int, default=-1,
+                    help="sources per batch (0: the library picks; default: the workload's)")
     ap.add_argument("--keep-source-order", action="store_true",
                     help="batches take the sources in the given order instead of the library's grouping")
     ap.add_argument("--many-count", type=int, default=10000)
@@ -642,6 +647,8 @@ def main():
                           "unavailable": "the reference arm covers the single-graph workloads"}))
         return
     w = WORKLOADS[args.workload]
+    if args.batch_k >= 0:
+        w = dict(w, batch_k=args.batch_k)
     if args.impl == "reference":
         run_reference(args, w, args.workload)
     else:

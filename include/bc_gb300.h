@@ -66,7 +66,7 @@ typedef enum {
 enum {
   BC_SCHED_AUTO = 0,
   BC_SCHED_PLAIN = 1,       /* one source per kernel launch, whole GPU, level-synchronous */
-  BC_SCHED_BATCH = 2,       /* up to 64 sources per launch, bitset frontiers, [n][64] state;
+  BC_SCHED_BATCH = 2,       /* up to 256 sources per launch, bitset frontiers, [n][k] state;
                                the library picks the frontier representation */
   BC_SCHED_BATCH_QUEUE = 3, /* BATCH with per-level frontier queues */
   BC_SCHED_BATCH_DENSE = 4  /* BATCH with per-level dense frontier masks (falls back to the
@@ -75,7 +75,15 @@ enum {
 
 typedef struct {
   int32_t delta_fp64;    /* 0: dependencies in FP32 (fast path); 1: FP64 */
-  int32_t batch_k;       /* sources per batch for BC_SCHED_BATCH: 0 = 64, else 1..64 */
+  int32_t batch_k;       /* sources per batch of the batched schedules: 0 = the library picks
+                            64, 128 or 256 (the widest that still gives the job eight batches;
+                            64 for debug exports and bc_exact_many); else 1..256 for
+                            BC_SCHED_AUTO / BATCH / BATCH_QUEUE, 1..64 for BATCH_DENSE and
+                            bc_exact_many.  Bit j of a batch's source masks is its j-th
+                            source; masks are 1, 2 or 4 64-bit words.  Wider batches size
+                            their frontier queue for 64 distinct depths per vertex; a job
+                            that overruns it reruns with 64 sources per batch, and so do
+                            later jobs on that graph */
   int32_t schedule;      /* BC_SCHED_* */
   int32_t normalize;     /* 0: raw sums; 1: divide by (n-1)(n-2) when n > 2 */
   int32_t scale_sampled; /* 0: raw sum over the given sources; 1: multiply by n/k */
@@ -110,6 +118,8 @@ typedef struct {
   int32_t levels_sum;        /* BFS level counts summed over all batches */
   int32_t chunk_edges;       /* edges per chunk of a high-degree vertex in the last launch */
   int32_t grab;              /* work items a warp fetched at a time in the last launch */
+  int32_t batch_sources;     /* sources per batch in the last launch */
+  int32_t mask_words;        /* 64-bit words per source mask in the last launch (1, 2 or 4) */
 } bc_stats;
 
 /* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t

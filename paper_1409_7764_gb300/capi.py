@@ -54,7 +54,8 @@ class bc_stats(ctypes.Structure):
                 ("dag_pairs", ctypes.c_int64), ("reached_pairs", ctypes.c_int64),
                 ("heavy_chunks", ctypes.c_int64), ("kernel_kind", ctypes.c_int32),
                 ("levels_sum", ctypes.c_int32),
-                ("chunk_edges", ctypes.c_int32), ("grab", ctypes.c_int32)]
+                ("chunk_edges", ctypes.c_int32), ("grab", ctypes.c_int32),
+                ("batch_sources", ctypes.c_int32), ("mask_words", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

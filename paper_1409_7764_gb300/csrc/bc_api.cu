@@ -76,9 +76,12 @@ struct GraphRec {
   // chunk counts of the high-degree vertices for each candidate chunk size
   const int32_t *nch_variant[kChunkVariants] = {};
   int64_t heavy_v[kChunkVariants] = {}, heavy_c[kChunkVariants] = {};
-  // per-graph tuning of the batched kernel: chunk variant and grab size
-  // (-1: not tuned yet)
-  std::atomic<int> tuned{-1};
+  // per-graph tuning of the batched kernel, per batch width (1, 2, 4 mask
+  // words): chunk variant and grab size (-1: not tuned yet)
+  std::atomic<int> tuned[3] = {-1, -1, -1};
+  // a batch wider than 64 sources overran its frontier queue or heavy list
+  // (sized for 64 distinct depths per vertex): later jobs use 64 sources
+  std::atomic<bool> narrow{false};
   // batch composition: every vertex in grouping order, and its position there
   std::vector<int32_t> order, pos;
 };
@@ -97,6 +100,7 @@ enum WsKind { WS_PLAIN = 0, WS_QUEUE = 1, WS_DENSE = 2 };
 struct WsRec {
   bool batch = true;
   int kind = WS_QUEUE;
+  int words = 1; // 64-bit words per source mask (queue kernel: 1, 2 or 4)
   int32_t n = 0;
   int32_t dmax = 0;
   int64_t cap = 0, hcap = 0, chunk_cap = 0;
@@ -108,11 +112,14 @@ struct WsRec {
 
 struct WsNeed {
   int kind;
+  int words;
   int32_t n;
   int32_t dmax;
   int64_t cap, hcap, chunk_cap;
   bool fits(const WsRec &r) const {
-    if (r.kind != kind || r.n < n || r.hcap < hcap || r.chunk_cap < chunk_cap) return false;
+    if (r.kind != kind || r.words != words || r.n < n || r.hcap < hcap ||
+        r.chunk_cap < chunk_cap)
+      return false;
     return kind == WS_DENSE ? r.dmax >= dmax : r.cap >= cap;
   }
 };
@@ -120,12 +127,38 @@ struct WsNeed {
 // Levels the dense kernel's per-level masks hold for an n-vertex graph.
 int32_t dense_levels(int32_t n) { return n <= (1 << 22) ? kDenseLevels : kDenseLevels / 2; }
 
-WsNeed ws_need(const GraphDev &g, int kind, int kb) {
+// Sources per batch and mask words of a job.  Explicit batch_k: that many
+// sources, in as many words as they need.  Automatic: the queue kernel takes
+// 64 sources per mask word and the widest batch (up to 256 sources) that
+// still gives the job kWideMinBatches batches; wider batches share each
+// (vertex, level) entry and edge scan among more sources.  Debug exports and
+// graphs that overran a wide batch's queue use 64.
+constexpr int kWideMinBatches = 8;
+struct BatchShape {
+  int kb;
+  int words;
+};
+BatchShape batch_shape(const bc_opts &o, int kind, int64_t k, bool narrow, bool dbg) {
+  if (kind == WS_PLAIN) return {1, 1};
+  if (narrow && kind == WS_QUEUE) return {o.batch_k > 0 && o.batch_k < kK ? o.batch_k : kK, 1};
+  if (o.batch_k > 0) return {o.batch_k, o.batch_k <= kK ? 1 : o.batch_k <= 2 * kK ? 2 : 4};
+  if (kind == WS_QUEUE && !narrow && !dbg)
+    for (int w = kMaxWords; w > 1; w /= 2)
+      if (k >= (int64_t)kWideMinBatches * kK * w) return {kK * w, w};
+  return {kK, 1};
+}
+
+int word_index(int words) { return words == 1 ? 0 : words == 2 ? 1 : 2; }
+
+WsNeed ws_need(const GraphDev &g, int kind, int kb, int words) {
   WsNeed nd;
   nd.kind = kind;
+  nd.words = kind == WS_QUEUE ? words : 1;
   nd.n = g.n;
   nd.dmax = kind == WS_DENSE ? dense_levels(g.n) : 0;
-  const int64_t kk = kind == WS_PLAIN ? 1 : kb;
+  // a vertex is queued at most once per distinct depth among the batch's
+  // sources; wider batches are sized for 64 depths (overruns are detected)
+  const int64_t kk = kind == WS_PLAIN ? 1 : std::min<int64_t>(kb, kK);
   nd.cap = kind == WS_DENSE ? 1 : std::max<int64_t>(1, (int64_t)g.n * kk);
   nd.hcap = std::max<int64_t>(1, g.heavy_vertices * kk);
   nd.chunk_cap = std::max<int64_t>(1, g.heavy_chunks);
@@ -137,11 +170,13 @@ size_t ws_layout(WsRec &r, char *mem) {
   Carver c;
   c.base = mem;
   const size_t n = (size_t)r.n;
-  const size_t kk = r.batch ? kK : 1;
+  const size_t words = r.batch ? (size_t)r.words : 1;
+  const size_t kk = r.batch ? kK * words : 1;
   Work &w = r.w;
   w = Work();
   w.n = r.n;
   w.k_max = (int32_t)kk;
+  w.words = (int32_t)words;
   w.ctl = c.take<Ctl>(1);
   if (r.kind == WS_DENSE) {
     w.vis = c.take<uint64_t>(n);
@@ -162,9 +197,10 @@ size_t ws_layout(WsRec &r, char *mem) {
     return align_up(c.off, 256);
   }
   if (r.batch) {
-    w.vis = c.take<uint64_t>(n);
-    w.fr = c.take<uint64_t>(4 * n);
-    w.qm = c.take<uint64_t>((size_t)r.cap);
+    w.vis = c.take<uint64_t>(n * words);
+    w.fr = c.take<uint64_t>(4 * n * words);
+    w.qm = c.take<uint64_t>((size_t)r.cap * words);
+    w.claim = words > 1 ? c.take<int32_t>(n) : nullptr;
     w.d = nullptr;
   } else {
     w.d = c.take<int32_t>(n);
@@ -182,7 +218,7 @@ size_t ws_layout(WsRec &r, char *mem) {
   w.harrive = c.take<unsigned>((size_t)r.hcap);
   w.hcap = r.hcap;
   w.partial = c.take<uint64_t>((size_t)r.chunk_cap * kk);
-  w.partial_ovf = c.take<uint64_t>((size_t)r.chunk_cap);
+  w.partial_ovf = c.take<uint64_t>((size_t)r.chunk_cap * words);
   w.chunk_cap = r.chunk_cap;
   w.sigma = c.take<uint64_t>(n * kk);
   w.cdep = c.take<double>(n * kk);
@@ -208,7 +244,7 @@ struct bc_ctx {
   size_t budget = 0;
   std::atomic<size_t> used{0};
   int sm_count = 0;
-  int grid_batch[2] = {0, 0}; // [fp64]
+  int grid_batch[3][2] = {}; // [mask words 1/2/4][fp64]
   int grid_dense[2] = {0, 0};
   int grid_many[2] = {0, 0};
   int grid_plain[2] = {0, 0};
@@ -265,6 +301,8 @@ struct JobRec {
   int64_t launches = 0;
   int64_t batches = 0;
   int kind = 0;              // workspace / kernel kind of the last launch
+  int kb = 0;                // sources per batch of the last launch
+  int words = 1;             // mask words of the last launch
   int cand = 0;              // tuning candidate of the last launch
   size_t footprint = 0;
   bc_status status = BC_PENDING;
@@ -294,7 +332,10 @@ bc_opts default_opts() {
 }
 
 bool opts_valid(const bc_opts &o) {
-  return (o.delta_fp64 == 0 || o.delta_fp64 == 1) && o.batch_k >= 0 && o.batch_k <= kK &&
+  return (o.delta_fp64 == 0 || o.delta_fp64 == 1) && o.batch_k >= 0 &&
+         o.batch_k <= kK * kMaxWords &&
+         (o.batch_k <= kK || o.schedule == BC_SCHED_AUTO || o.schedule == BC_SCHED_BATCH ||
+          o.schedule == BC_SCHED_BATCH_QUEUE) &&
          o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_DENSE &&
          (o.normalize == 0 || o.normalize == 1) &&
          (o.scale_sampled == 0 || o.scale_sampled == 1) &&
@@ -307,7 +348,6 @@ int resolve_schedule(const bc_opts &o, const GraphDev &) {
   return BC_SCHED_BATCH;
 }
 
-int resolve_batch_k(const bc_opts &o) { return o.batch_k == 0 ? kK : o.batch_k; }
 
 // Frontier representation for BC_SCHED_BATCH: the queue form measured faster
 // than the dense-level form on every workload tried (R-MAT scales 16 and 20,
@@ -316,9 +356,9 @@ int pick_batch_kind(const GraphDev &) { return WS_QUEUE; }
 
 // Grid of a persistent launch: the co-resident maximum for large graphs, a
 // smaller share of the GPU for small ones so that concurrent jobs overlap.
-int pick_grid(const bc_ctx *ctx, const GraphDev &g, int kind, bool fp64) {
+int pick_grid(const bc_ctx *ctx, const GraphDev &g, int kind, bool fp64, int words) {
   const int gmax = kind == WS_DENSE   ? ctx->grid_dense[fp64]
-                   : kind == WS_QUEUE ? ctx->grid_batch[fp64]
+                   : kind == WS_QUEUE ? ctx->grid_batch[word_index(words)][fp64]
                                       : ctx->grid_plain[fp64];
   if (const char *env = std::getenv("BC_GRID")) {
     int v = std::atoi(env);
@@ -513,6 +553,7 @@ bc_status ws_acquire(bc_ctx *ctx, const WsNeed &nd, cudaStream_t st, std::unique
   }
   auto r = std::make_unique<WsRec>();
   r->kind = nd.kind;
+  r->words = nd.words;
   r->batch = nd.kind != WS_PLAIN;
   r->dmax = nd.dmax;
   r->n = nd.n;
@@ -556,13 +597,16 @@ void ws_release(bc_ctx *ctx, std::unique_ptr<WsRec> ws) {
 
 // ---- jobs -------------------------------------------------------------------
 
-size_t job_footprint(const GraphDev &g, int sched, int kb, int64_t k) {
+size_t job_footprint(const GraphRec &gr, int sched, const bc_opts &o, int64_t k) {
+  const GraphDev &g = gr.dev;
   WsRec r;
   const int kind = sched == BC_SCHED_PLAIN         ? WS_PLAIN
                    : sched == BC_SCHED_BATCH_DENSE ? WS_DENSE
                                                    : WS_QUEUE;
-  WsNeed nd = ws_need(g, kind, kb);
+  const BatchShape bs = batch_shape(o, kind, k, gr.narrow, false);
+  WsNeed nd = ws_need(g, kind, bs.kb, bs.words);
   r.kind = nd.kind;
+  r.words = nd.words;
   r.batch = nd.kind != WS_PLAIN;
   r.dmax = nd.dmax;
   r.n = nd.n;
@@ -612,7 +656,6 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   const int sched = resolve_schedule(j->opts, g);
   const bool batch = sched != BC_SCHED_PLAIN;
   const bool fp64 = j->opts.delta_fp64 != 0;
-  const int kb = batch ? resolve_batch_k(j->opts) : 1;
   const int64_t n = g.n, k = j->k;
   cudaStream_t st = j->st;
   // batches run on the dense-level kernel unless the graph is known to be
@@ -622,8 +665,14 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
                    : sched == BC_SCHED_BATCH_DENSE               ? WS_DENSE
                                                                  : pick_batch_kind(j->g->dev);
   j->kind = kind;
+  const BatchShape bs = batch_shape(j->opts, kind, k, j->g->narrow, dbg != nullptr);
+  // wider than one mask word: the queue kernel only
+  if (bs.words > 1 && kind != WS_QUEUE) return BC_ERR_ARG;
+  const int kb = bs.kb, words = bs.words;
+  j->kb = kb;
+  j->words = words;
 
-  bc_status s = ws_acquire(ctx, ws_need(g, kind, kb), st, j->ws);
+  bc_status s = ws_acquire(ctx, ws_need(g, kind, kb, words), st, j->ws);
   if (s != BC_OK) return s;
   BC_TRY(cudaMallocHost(&j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
   BC_TRY(cudaMallocHost(&j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
@@ -669,7 +718,7 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
     p.timeout_ns = (long long)ctx->inject_timeout_ms * 1000000LL;
     ctx->inject_block = -1;
   }
-  const int grid = pick_grid(ctx, g, kind, fp64);
+  const int grid = pick_grid(ctx, g, kind, fp64, words);
   if (grid <= 0) return BC_ERR_CUDA;
   constexpr int kTraceCap = 8192;
   if (const char *tr = std::getenv("BC_TRACE")) {
@@ -689,7 +738,8 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   // fastest for the rest of the job and for later jobs on the graph.  Every
   // candidate computes the same result; only the work split differs.
   const int64_t nbatch = (k + kb - 1) / kb;
-  const int tuned = j->g->tuned.load();
+  std::atomic<int> &tuned_slot = j->g->tuned[word_index(words)];
+  const int tuned = tuned_slot.load();
   const bool tune = kind == WS_QUEUE && tuned < 0 && !dbg && !std::getenv("BC_NO_TUNE") &&
                     nbatch >= kNumTune * kTuneRounds + 8;
   auto apply = [&](int cand) {
@@ -733,7 +783,7 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
         int best = 0;
         for (int c = 1; c < kNumTune; ++c)
           if (sum[c] < sum[best]) best = c;
-        j->g->tuned = best;
+        tuned_slot = best;
         apply(best);
         for (auto &ev : tev) {
           cudaEventDestroy(ev);
@@ -742,7 +792,7 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
       }
     }
     BC_TRY(kind == WS_DENSE   ? launch_dense(p, fp64, grid, st)
-           : kind == WS_QUEUE ? launch_batch(p, fp64, grid, st)
+           : kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words)
                               : launch_plain(p, fp64, grid, st));
     ++j->batches;
     ++j->launches;
@@ -793,6 +843,8 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.kernel_kind = j->kind == WS_DENSE ? 3 : j->kind == WS_QUEUE ? 2 : 1;
   s.levels_sum = (int32_t)j->h_cnt[CNT_LEVELS];
   s.chunk_edges = kChunkCandidates[kTuneCandidates[j->cand].variant];
+  s.batch_sources = j->kb;
+  s.mask_words = j->words;
   s.grab = kTuneCandidates[j->cand].grab;
   int32_t novf = 0;
   for (int64_t i = 0; i < j->k; ++i) novf += j->h_ovf[i] ? 1 : 0;
@@ -821,6 +873,12 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
     j->g->deep = true;
     st = kStatusRetry;
     j->ws->dirty = true;
+  } else if ((kerr == KERR_QUEUE || kerr == KERR_HEAVY) && j->words > 1) {
+    // a wide batch queued vertices at more distinct depths than its queue
+    // holds: rerun the job with 64 sources per batch
+    j->g->narrow = true;
+    st = kStatusRetry;
+    j->ws->dirty = true;
   } else if (kerr != KERR_NONE) {
     st = kerr == KERR_TIMEOUT ? BC_ERR_TIMEOUT : BC_ERR_INTERNAL;
     j->ws->dirty = true;
@@ -844,7 +902,7 @@ bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool
   if (!all && k) j.src.assign(src, src + k);
   j.st = ctx->stream;
   bc_status s = kStatusRetry;
-  for (int attempt = 0; attempt < 2 && s == kStatusRetry; ++attempt) {
+  for (int attempt = 0; attempt < 3 && s == kStatusRetry; ++attempt) {
     s = job_launch(ctx, &j, out, dbg);
     if (s != BC_OK) {
       cudaStreamSynchronize(j.st);
@@ -1006,11 +1064,14 @@ bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)freeb);
   BC_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
   for (int f = 0; f < 2; ++f) {
-    ctx->grid_batch[f] = max_grid_batch(f != 0, device);
+    for (int wi = 0; wi < 3; ++wi) {
+      ctx->grid_batch[wi][f] = max_grid_batch(f != 0, device, 1 << wi);
+      if (ctx->grid_batch[wi][f] <= 0) return BC_ERR_CUDA;
+    }
     ctx->grid_dense[f] = max_grid_dense(f != 0, device);
     ctx->grid_many[f] = max_grid_many(f != 0, device);
     ctx->grid_plain[f] = max_grid_plain(f != 0, device);
-    if (ctx->grid_batch[f] <= 0 || ctx->grid_plain[f] <= 0 || ctx->grid_dense[f] <= 0)
+    if (ctx->grid_plain[f] <= 0 || ctx->grid_dense[f] <= 0)
       return BC_ERR_CUDA;
   }
   for (int i = 0; i < kMaxSlots; ++i)
@@ -1130,7 +1191,7 @@ bc_status bc_submit(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, cons
   j->opts = o;
   j->n = j->g->dev.n;
   const int sched = resolve_schedule(o, j->g->dev);
-  j->footprint = job_footprint(j->g->dev, sched, resolve_batch_k(o), j->k);
+  j->footprint = job_footprint(*j->g, sched, o, j->k);
   if (j->footprint > ctx->budget) return BC_ERR_ADMISSION;
   if (cudaMallocHost(&j->h_out, sizeof(double) * (size_t)std::max<int32_t>(j->g->dev.n, 1)) !=
       cudaSuccess)
@@ -1253,7 +1314,8 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
       if (!(gs[(size_t)i] = find_graph(ctx, graphs[i]))) return BC_ERR_GRAPH;
   }
   const bool fp64 = o.delta_fp64 != 0;
-  const int kb = resolve_batch_k(o);
+  if (o.batch_k > kK) return BC_ERR_ARG; // one block per graph: up to 64 sources per batch
+  const int kb = o.batch_k == 0 ? kK : o.batch_k;
   std::vector<int64_t> off((size_t)count + 1, 0);
   for (int32_t i = 0; i < count; ++i) off[(size_t)i + 1] = off[(size_t)i] + gs[(size_t)i]->dev.n;
   const int64_t total_n = off[(size_t)count];

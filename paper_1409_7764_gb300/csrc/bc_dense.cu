@@ -245,7 +245,7 @@ __device__ void fwd_group(const KParams &p, const HeavyLevel &hl, int64_t v0, co
       row[32 + lane] = l == 0 ? 1ull
                               : (((oi >> (lane + 32)) & 1ull) ? ~0ull
                                                               : (uint64_t)acc[i * kK + 32 + lane]);
-    if (oi && lane == 0) atomicOr(&p.w.ctl->ovf, (unsigned long long)oi);
+    if (oi && lane == 0) atomicOr(&p.w.ctl->ovf[0], (unsigned long long)oi);
   }
   __syncwarp();
   // discovery: flattened out-edges of all active vertices
@@ -445,8 +445,14 @@ __device__ void bwd_chunk(const KParams &p, const HeavyLevel &hl, int64_t item,
   const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
   const int64_t od = re - rs;
   const int64_t a = r.ci * od / nch, b = (r.ci + 1) * od / nch;
-  DT a0 = 0, a1 = 0;
-  if (Dn) batch_pull_delta<DT>(p, F, rs + a, rs + b, Dn, lane, reinterpret_cast<DT *>(wacc), a0, a1);
+  (void)wacc;
+  DT acc[2] = {DT(0), DT(0)};
+  if (Dn) {
+    Mask<1> FM;
+    FM.w[0] = F;
+    batch_pull_delta_w<1, DT>(p, FM, rs + a, rs + b, Dn, lane, acc);
+  }
+  const DT a0 = acc[0], a1 = acc[1];
   if (lane == 0) {
     cnt.out_e += (uint64_t)(Dn ? b - a : 0);
     cnt.heavy++;
@@ -503,7 +509,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) dense_kernel(const KP
 
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {
-      ctl->ovf = 0;
+      ctl->ovf[0] = 0;
       ctl->nlevels = 0;
       p.w.hpack[0] = 0;
       p.w.hpack[1] = 0;
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) dense_kernel(const KP
     ctl->nlevels = L;
     atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
     atomicAdd(p.job_cnt + CNT_LEVELS, (unsigned long long)L);
-    const uint64_t ob = ldcg(&ctl->ovf);
+    const uint64_t ob = ldcg(&ctl->ovf[0]);
     for (int j = 0; j < p.k; ++j)
       if ((ob >> j) & 1ull) p.ovf_flags[p.src_base + j] = 1;
   }

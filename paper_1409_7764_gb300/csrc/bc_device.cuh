@@ -209,9 +209,6 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 #ifndef BC_GATHER_UNROLL
 #define BC_GATHER_UNROLL 4 // DAG edges gathered per round (lanes-per-source form)
 #endif
-#ifndef BC_GATHER_BY_EDGE
-#define BC_GATHER_BY_EDGE 0 // 1: lanes take edges and add through shared-memory atomics
-#endif
 
 // Up to U set lanes of a ballot, in lane order; missing ones are -1.
 template <int U> struct LanesU {
@@ -283,46 +280,16 @@ __device__ __forceinline__ void gather_coeffs_full(const DT *base, int x, uint64
   }
 }
 
-// Batch: path-count pull over in-edges [eb, ee) of entry w (mask F) from the
-// level l-1 dense mask Pm.  Returns the counts of sources lane and lane+32,
-// saturated at 2^64-1 on carry.
-//   lanes-per-source form: lane j owns sources j and j+32; per round the warp
-//     gathers the predecessor rows of BC_GATHER_UNROLL shortest-path edges
-//     (coalesced row segments) and adds them in edge order;
-//   lanes-per-edge form: lanes take edges and add the predecessor's counts
-//     into the warp's shared row wacc[64] with integer atomics.
+// Dense kernel, heavy chunks: path-count pull over in-edges [eb, ee) of
+// entry w (mask F) from the level l-1 dense mask Pm.  Lane j owns sources j
+// and j+32; per round the warp gathers the predecessor rows of
+// BC_GATHER_UNROLL shortest-path edges and adds them in edge order.  Counts
+// saturate at 2^64-1 on carry.
 __device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, int64_t eb,
                                                  int64_t ee, const uint64_t *Pm, int lane,
                                                  unsigned long long *wacc, uint64_t &s0,
                                                  uint64_t &s1, bool &o0, bool &o1,
                                                  unsigned long long &dag) {
-#if BC_GATHER_BY_EDGE
-  wacc[lane] = 0;
-  wacc[lane + 32] = 0;
-  __syncwarp();
-  uint64_t ovf = 0;
-  unsigned long long nd = 0;
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    if (e < ee) {
-      const int u = __ldg(p.g.in_idx + e);
-      const uint64_t P = ldcg(Pm + u) & F;
-      nd += __popcll(P);
-      gather_counts(p.w.sigma + (size_t)u * kK, P, wacc, ovf);
-    }
-  }
-  __syncwarp();
-  ovf = warp_or64(ovf);
-  nd = warp_sum_u64(nd);
-  if (lane == 0) dag += nd;
-  s0 = wacc[lane];
-  s1 = wacc[lane + 32];
-  o0 = o0 || ((ovf >> lane) & 1ull);
-  o1 = o1 || ((ovf >> (lane + 32)) & 1ull);
-  if (o0) s0 = ~0ull;
-  if (o1) s1 = ~0ull;
-  __syncwarp();
-#else
   (void)wacc;
   constexpr int U = BC_GATHER_UNROLL;
   unsigned long long nd = 0;
@@ -339,48 +306,6 @@ __device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, i
   }
   nd = warp_sum_u64(nd);
   if (lane == 0) dag += nd;
-#endif
-}
-
-// Batch: dependency pull over out-edges [eb, ee) of entry v (mask F) from
-// the level l+1 dense mask Dn (same two forms; the lanes-per-source form adds
-// successor coefficients in edge order, the lanes-per-edge form through
-// floating-point shared atomics whose order may vary between runs).
-template <typename DT>
-__device__ __forceinline__ void batch_pull_delta(const KParams &p, uint64_t F, int64_t eb,
-                                                 int64_t ee, const uint64_t *Dn, int lane,
-                                                 DT *wacc, DT &a0, DT &a1) {
-  const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
-#if BC_GATHER_BY_EDGE
-  wacc[lane] = DT(0);
-  wacc[lane + 32] = DT(0);
-  __syncwarp();
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    if (e < ee) {
-      const int x = __ldg(p.g.col_idx + e);
-      const uint64_t S = ldcg(Dn + x) & F;
-      gather_coeffs<DT>(cdep + (size_t)x * kK, S, wacc);
-    }
-  }
-  __syncwarp();
-  a0 = wacc[lane];
-  a1 = wacc[lane + 32];
-  __syncwarp();
-#else
-  (void)wacc;
-  constexpr int U = BC_GATHER_UNROLL;
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    int x = 0;
-    uint64_t S = 0;
-    if (e < ee) {
-      x = __ldg(p.g.col_idx + e);
-      S = ldcg(Dn + x) & F;
-    }
-    gather_coeffs_full<U, DT>(cdep, x, S, lane, a0, a1);
-  }
-#endif
 }
 
 // Batch: writes the path counts of entry w (mask F) and records overflow.
@@ -392,7 +317,200 @@ __device__ __forceinline__ void batch_store_sigma(const KParams &p, int w, uint6
   if ((F >> (lane + 32)) & 1ull) row[32 + lane] = o1 ? ~0ull : s1;
   const uint64_t ob =
       ((uint64_t)__ballot_sync(kFull, o0) | ((uint64_t)__ballot_sync(kFull, o1) << 32)) & F;
-  if (ob && lane == 0) atomicOr(&p.w.ctl->ovf, (unsigned long long)ob);
+  if (ob && lane == 0) atomicOr(&p.w.ctl->ovf[0], (unsigned long long)ob);
+}
+
+// ---------------------------------------------------------------------------
+// Source masks of W 64-bit words (64*W sources per batch).  Lane j owns the
+// sources 32*i + j, i = 0 .. 2W-1 ("slot" i); slot i is bit (i&1)*32 + j of
+// word i/2.  Per-vertex masks are stored as W consecutive words.
+// ---------------------------------------------------------------------------
+template <int W> struct Mask {
+  uint64_t w[W];
+  __device__ __forceinline__ static Mask zero() {
+    Mask m;
+#pragma unroll
+    for (int i = 0; i < W; ++i) m.w[i] = 0;
+    return m;
+  }
+  __device__ __forceinline__ bool any() const {
+    uint64_t a = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) a |= w[i];
+    return a != 0;
+  }
+  __device__ __forceinline__ int popc() const {
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) c += __popcll(w[i]);
+    return c;
+  }
+  __device__ __forceinline__ bool has(int slot, int lane) const {
+    return (w[slot >> 1] >> ((slot & 1) * 32 + lane)) & 1ull;
+  }
+  __device__ __forceinline__ Mask operator&(const Mask &o) const {
+    Mask m;
+#pragma unroll
+    for (int i = 0; i < W; ++i) m.w[i] = w[i] & o.w[i];
+    return m;
+  }
+  __device__ __forceinline__ Mask operator|(const Mask &o) const {
+    Mask m;
+#pragma unroll
+    for (int i = 0; i < W; ++i) m.w[i] = w[i] | o.w[i];
+    return m;
+  }
+  __device__ __forceinline__ Mask and_not(const Mask &o) const {
+    Mask m;
+#pragma unroll
+    for (int i = 0; i < W; ++i) m.w[i] = w[i] & ~o.w[i];
+    return m;
+  }
+};
+
+// Mask of vertex v from an array of W-word masks, through L2 (16-byte loads
+// for W >= 2).
+template <int W> __device__ __forceinline__ Mask<W> load_mask(const uint64_t *base, int64_t v) {
+  Mask<W> m;
+  const uint64_t *q = base + (size_t)v * W;
+  if constexpr (W == 1) {
+    m.w[0] = ldcg(q);
+  } else {
+#pragma unroll
+    for (int i = 0; i < W; i += 2) {
+      const ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2 *>(q + i));
+      m.w[i] = t.x;
+      m.w[i + 1] = t.y;
+    }
+  }
+  return m;
+}
+
+template <int W> __device__ __forceinline__ void store_mask(uint64_t *base, int64_t v,
+                                                            const Mask<W> &m) {
+  uint64_t *q = base + (size_t)v * W;
+#pragma unroll
+  for (int i = 0; i < W; ++i) q[i] = m.w[i];
+}
+
+template <int W> __device__ __forceinline__ void zero_mask(uint64_t *base, int64_t v) {
+  store_mask<W>(base, v, Mask<W>::zero());
+}
+
+template <int W> __device__ __forceinline__ Mask<W> shfl_mask(const Mask<W> &m, int src) {
+  Mask<W> r;
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.w[i] = shfl_or_zero(m.w[i], src);
+  return r;
+}
+
+// Edges whose predecessor rows a warp gathers per round: 8 row loads per
+// lane in flight whatever the mask width.
+template <int W> struct GatherUnroll {
+  static constexpr int value = W == 1 ? BC_GATHER_UNROLL : (W == 2 ? 2 : 1);
+};
+
+// Path counts over the round's shortest-path edges (lanes whose mask P is not
+// empty, in lane order): lane j adds row[32*i + j] of each edge's row for
+// every slot i whose bit is set; 64-bit sums, carry of slot i recorded in
+// bit i of cbits (a carry means the true count reached 2^64).
+template <int W>
+__device__ __forceinline__ void gather_counts_w(const uint64_t *base, int u, const Mask<W> &P,
+                                                int lane, uint64_t (&s)[2 * W],
+                                                unsigned &cbits) {
+  constexpr int U = GatherUnroll<W>::value;
+  unsigned bal = __ballot_sync(kFull, P.any());
+  while (bal) {
+    const LanesU<U> q(bal);
+    uint64_t x[U][2 * W];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int uu = shfl_or_zero(u, q.l[i]);
+      const uint64_t *row = base + (size_t)uu * (kK * W);
+#pragma unroll
+      for (int wi = 0; wi < W; ++wi) {
+        const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
+        x[i][2 * wi] = ((PP >> lane) & 1ull) ? ldcg(row + 64 * wi + lane) : 0ull;
+        x[i][2 * wi + 1] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 64 * wi + 32 + lane) : 0ull;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i)
+#pragma unroll
+      for (int t = 0; t < 2 * W; ++t) {
+        s[t] += x[i][t];
+        cbits |= (s[t] < x[i][t] ? 1u : 0u) << t;
+      }
+  }
+}
+
+// Dependency coefficients over the round's successor edges, added in edge
+// order.
+template <int W, typename DT>
+__device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mask<W> &S,
+                                                int lane, DT (&a)[2 * W]) {
+  constexpr int U = GatherUnroll<W>::value;
+  unsigned bal = __ballot_sync(kFull, S.any());
+  while (bal) {
+    const LanesU<U> q(bal);
+    DT y[U][2 * W];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int xx = shfl_or_zero(x, q.l[i]);
+      const DT *row = base + (size_t)xx * (kK * W);
+#pragma unroll
+      for (int wi = 0; wi < W; ++wi) {
+        const uint64_t SS = shfl_or_zero(S.w[wi], q.l[i]);
+        y[i][2 * wi] = ((SS >> lane) & 1ull) ? ldcg(row + 64 * wi + lane) : DT(0);
+        y[i][2 * wi + 1] = ((SS >> (lane + 32)) & 1ull) ? ldcg(row + 64 * wi + 32 + lane) : DT(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i)
+      if (q.l[i] >= 0) {
+#pragma unroll
+        for (int t = 0; t < 2 * W; ++t) a[t] += y[i][t];
+      }
+  }
+}
+
+// Dependency pull over out-edges [eb, ee) of an entry with mask F from the
+// level l+1 masks Dn: lane j sums c[x][32*i + j] over successors x whose
+// level-(l+1) mask has source 32*i + j, in edge order.
+template <int W, typename DT>
+__device__ __forceinline__ void batch_pull_delta_w(const KParams &p, const Mask<W> &F,
+                                                   int64_t eb, int64_t ee, const uint64_t *Dn,
+                                                   int lane, DT (&a)[2 * W]) {
+  const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
+  for (int64_t base = eb; base < ee; base += kWarp) {
+    const int64_t e = base + lane;
+    int x = 0;
+    Mask<W> S = Mask<W>::zero();
+    if (e < ee) {
+      x = __ldg(p.g.col_idx + e);
+      S = load_mask<W>(Dn, x) & F;
+    }
+    gather_coeffs_w<W, DT>(cdep, x, S, lane, a);
+  }
+}
+
+// Writes the path counts of entry w (mask F; counts saturated where the carry
+// bit is set) and records the overflowing sources in the control block.
+template <int W>
+__device__ __forceinline__ void batch_store_sigma_w(const KParams &p, int w, const Mask<W> &F,
+                                                    const uint64_t (&s)[2 * W], unsigned cbits,
+                                                    int lane) {
+  uint64_t *row = p.w.sigma + (size_t)w * (kK * W);
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i)
+    if (F.has(i, lane)) row[32 * i + lane] = ((cbits >> i) & 1u) ? ~0ull : s[i];
+#pragma unroll
+  for (int wi = 0; wi < W; ++wi) {
+    const uint64_t ob = ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi)) & 1u) |
+                         ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi + 1)) & 1u) << 32)) &
+                        F.w[wi];
+    if (ob && lane == 0) atomicOr(&p.w.ctl->ovf[wi], (unsigned long long)ob);
+  }
 }
 
 // Last heavy entry h in [base, base+cnt) whose first chunk hq_c[h] <= item:

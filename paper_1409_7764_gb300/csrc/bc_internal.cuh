@@ -11,7 +11,8 @@ namespace bcgpu {
 constexpr int kWarp = 32;
 constexpr int kBlock = 256;                    // threads per CTA of the persistent kernels
 constexpr int kWarpsPerBlock = kBlock / kWarp; // 8
-constexpr int kK = 64;                         // sources per batch (one bit each in a u64 mask)
+constexpr int kK = 64;                         // sources per mask word (one bit each in a u64)
+constexpr int kMaxWords = 4;                   // queue kernel: up to 4 words = 256 sources per batch
 // Edges per work chunk of a high-degree vertex: candidates the per-graph
 // tuner picks from (the first is the default before tuning).
 constexpr int kChunkCandidates[3] = {256, 128, 512};
@@ -61,7 +62,7 @@ struct Ctl {
   int err;                // first device error (KERR_*), sticky for the job
   int nlevels;            // levels of the current batch
   unsigned long long tail; // frontier queue tail (entries)
-  unsigned long long ovf;  // batch: sources (bits) whose count reached 2^64; plain: 0/1
+  unsigned long long ovf[kMaxWords]; // batch: sources (bits) whose count reached 2^64; plain: [0] 0/1
   unsigned long long work[4]; // work-item counters of consecutive steps (ring)
 };
 
@@ -83,12 +84,15 @@ struct GraphDev {
 // Device workspace of one in-flight batch (or one plain source).
 struct Work {
   int32_t n = 0;
-  int32_t k_max = 0;          // 64 for the batch kernel, 1 for plain
-  uint64_t *vis = nullptr;    // batch: [n] visited masks
-  uint64_t *fr = nullptr;     // batch: [4][n] rotating dense frontier masks
+  int32_t k_max = 0;          // 64 * words for the batch kernels, 1 for plain
+  int32_t words = 1;          // batch: 64-bit words per source mask
+  uint64_t *vis = nullptr;    // batch: [n][words] visited masks
+  uint64_t *fr = nullptr;     // batch: [4][n][words] rotating dense frontier masks
+  int32_t *claim = nullptr;   // queue kernel, words > 1: [n] 1 + the deepest level a vertex was
+                              // queued at (first-toucher claims)
   int32_t *d = nullptr;       // plain: [n] depth (-1 unreached)
   int32_t *qv = nullptr;      // [cap] frontier entries (vertex ids), levels back to back
-  uint64_t *qm = nullptr;     // batch: [cap] entry masks
+  uint64_t *qm = nullptr;     // batch: [cap][words] entry masks
   int64_t cap = 0;
   int64_t *qoff = nullptr;    // [n+3] start of each level in qv
   unsigned long long *hpack = nullptr; // [n+3] per level: (heavy count << 32) | chunk total
@@ -99,7 +103,7 @@ struct Work {
   unsigned *harrive = nullptr; // [hcap] chunk arrivals per heavy entry
   int64_t hcap = 0;
   void *partial = nullptr;    // [chunk_cap][k_max] chunk partial sums (u64 or float type)
-  uint64_t *partial_ovf = nullptr; // [chunk_cap] overflow bits of forward partials
+  uint64_t *partial_ovf = nullptr; // [chunk_cap][words] overflow bits of forward partials
   int64_t chunk_cap = 0;
   uint64_t *sigma = nullptr;  // [n][k_max] path counts
   void *cdep = nullptr;       // [n][k_max] (1 + delta) / sigma, float or double
@@ -147,12 +151,12 @@ struct ManyParams {
 // Host launchers (bc_kernels.cu).  Return a cudaError_t.
 cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st);
 int max_grid_many(bool fp64, int device);
-cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_dense(const KParams &p, bool fp64, int grid, cudaStream_t st);
 int max_grid_dense(bool fp64, int device);
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
-int max_grid_batch(bool fp64, int device);
+int max_grid_batch(bool fp64, int device, int words = 1);
 int max_grid_plain(bool fp64, int device);
 
 } // namespace bcgpu

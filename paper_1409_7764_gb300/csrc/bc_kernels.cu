@@ -183,154 +183,172 @@ __device__ __forceinline__ void stage_new(const KParams &p, const LevelView &lv,
 // pull over in-edges [ib, ie) and the discovery push over out-edges
 // [ob, oe), advanced together 32 edges of each per round so that their
 // loads overlap.  A vertex x gets the bits F & ~(visited before level l |
-// level l | already marked for level l+1); the OR's old value tells the first
-// toucher, and is only read after the round's path-count gathers.
-__device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, uint64_t F,
+// level l | already marked for level l+1), OR-ed into its level-(l+1) mask.
+// The first toucher of x at level l+1 queues it: with one mask word the OR's
+// old value says so (all zero before); with several words a claim on x
+// decides (claim[x] < l+2 before, raised to l+2).  The returned value is only
+// read after the round's path-count gathers, so its latency overlaps them.
+template <int W>
+__device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, const Mask<W> &F,
                                          int64_t ib, int64_t ie, int64_t ob, int64_t oe,
                                          const uint64_t *A, const uint64_t *Pm, uint64_t *Bn,
-                                         int *stage, int &nst, int lane, uint64_t &s0,
-                                         uint64_t &s1, bool &o0, bool &o1,
-                                         unsigned long long &dag) {
-  constexpr int U = BC_GATHER_UNROLL;
+                                         int *stage, int &nst, int lane, uint64_t (&s)[2 * W],
+                                         unsigned &cbits, unsigned long long &dag) {
   const int64_t din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
   const int64_t span = din > dout ? din : dout;
+  const int claim_to = lv.lvl + 2;
   for (int64_t r = 0; r < span; r += kWarp) {
     const int64_t t = r + lane;
     const bool vi = t < din, vo = t < dout;
     int u = 0, x = 0;
     if (vi) u = __ldg(p.g.in_idx + ib + t);
     if (vo) x = __ldg(p.g.col_idx + ob + t);
-    uint64_t P = 0, nb = 0;
-    if (vi) P = ldcg(Pm + u) & F;
-    if (vo) nb = F & ~(ldcg(p.w.vis + x) | ldcg(A + x) | ldcg(Bn + x));
-    uint64_t oldB = 1;
-    if (nb) oldB = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb);
-    dag += __popcll(P); // per lane; the warp's counters are summed at the flush
-    gather_counts_full<U>(p.w.sigma, u, P, lane, s0, s1, o0, o1);
-    stage_new(p, lv, nb != 0 && oldB == 0, x, stage, nst, lane);
+    Mask<W> P = Mask<W>::zero(), nb = Mask<W>::zero();
+    if (vi) P = load_mask<W>(Pm, u) & F;
+    if (vo)
+      nb = F.and_not(load_mask<W>(p.w.vis, x) | load_mask<W>(A, x) | load_mask<W>(Bn, x));
+    const bool any_new = nb.any();
+    unsigned long long old = 1;
+    if (any_new) {
+      if constexpr (W == 1) {
+        old = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb.w[0]);
+      } else {
+        unsigned long long *bx = reinterpret_cast<unsigned long long *>(Bn + (size_t)x * W);
+#pragma unroll
+        for (int wi = 0; wi < W; ++wi)
+          if (nb.w[wi]) atomicOr(bx + wi, nb.w[wi]);
+        old = (unsigned long long)atomicMax(p.w.claim + x, claim_to);
+      }
+    }
+    dag += P.popc(); // per lane; the warp's counters are summed at the flush
+    gather_counts_w<W>(p.w.sigma, u, P, lane, s, cbits);
+    const bool first = any_new && (W == 1 ? old == 0 : (long long)old < claim_to);
+    stage_new(p, lv, first, x, stage, nst, lane);
   }
 }
 
 // Batch: closes entry v (mask F) at level l of the backward sweep given the
-// lane's successor sums a0/a1, its path counts sg0/sg1 and (lane 0) the
-// current BC value bcv, all loaded by the caller ahead of the successor scan:
+// lane's successor sums a, its path counts sg and (lane 0) the current BC
+// value bcv, all loaded by the caller ahead of the successor scan:
 // dependencies, coefficients, BC, resets.
-template <typename DT>
-__device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, uint64_t F, DT a0,
-                                             DT a1, uint64_t sg0, uint64_t sg1, double bcv,
-                                             uint64_t *Wn, int s_lo, int s_hi, int lane) {
-  uint64_t *srow = p.w.sigma + (size_t)v * kK;
-  DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * kK;
+template <typename DT, int W>
+__device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, const Mask<W> &F,
+                                             const DT (&a)[2 * W], const uint64_t (&sg)[2 * W],
+                                             double bcv, uint64_t *Wn, int lane) {
+  uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
+  DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * (kK * W);
   double contrib = 0.0;
   const int n = p.g.n;
-  if ((F >> lane) & 1ull) {
-    const DT sf = u64_to<DT>(sg0);
-    const DT dl = sf * a0;
-    crow[lane] = (DT(1) + dl) / sf;
-    srow[lane] = 0;
-    if (s_lo != v) contrib += (double)dl;
-    if (p.dbg_d) {
-      const size_t o = (size_t)lane * n + v;
-      p.dbg_d[o] = lvl;
-      p.dbg_sigma[o] = sg0;
-      p.dbg_delta[o] = (double)dl;
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i)
+    if (F.has(i, lane)) {
+      const int j = 32 * i + lane; // source index within the batch (j < k)
+      const DT sf = u64_to<DT>(sg[i]);
+      const DT dl = sf * a[i];
+      crow[j] = (DT(1) + dl) / sf;
+      srow[j] = 0;
+      if (__ldg(p.src + j) != v) contrib += (double)dl;
+      if (p.dbg_d) {
+        const size_t o = (size_t)j * n + v;
+        p.dbg_d[o] = lvl;
+        p.dbg_sigma[o] = sg[i];
+        p.dbg_delta[o] = (double)dl;
+      }
     }
-  }
-  if ((F >> (lane + 32)) & 1ull) {
-    const DT sf = u64_to<DT>(sg1);
-    const DT dl = sf * a1;
-    crow[32 + lane] = (DT(1) + dl) / sf;
-    srow[32 + lane] = 0;
-    if (s_hi != v) contrib += (double)dl;
-    if (p.dbg_d) {
-      const size_t o = (size_t)(lane + 32) * n + v;
-      p.dbg_d[o] = lvl;
-      p.dbg_sigma[o] = sg1;
-      p.dbg_delta[o] = (double)dl;
-    }
-  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(kFull, contrib, off);
   if (lane == 0) {
     if (contrib != 0.0) p.bc[v] = bcv + contrib;
-    p.w.vis[v] = 0;
-    if (Wn) Wn[v] = F;
+    zero_mask<W>(p.w.vis, v);
+    if (Wn) store_mask<W>(Wn, v, F);
+    if (W > 1) p.w.claim[v] = 0;
   }
 }
 
 // Loads of an entry's own path counts and BC value, issued before its
 // successor scan so they overlap it.
-struct EntryOwn {
-  uint64_t sg0, sg1;
+template <int W> struct EntryOwn {
+  uint64_t sg[2 * W];
   double bcv;
-  __device__ __forceinline__ EntryOwn(const KParams &p, int v, uint64_t F, int lane) {
-    const uint64_t *srow = p.w.sigma + (size_t)v * kK;
-    sg0 = ((F >> lane) & 1ull) ? ldcg(srow + lane) : 0ull;
-    sg1 = ((F >> (lane + 32)) & 1ull) ? ldcg(srow + 32 + lane) : 0ull;
+  __device__ __forceinline__ EntryOwn(const KParams &p, int v, const Mask<W> &F, int lane) {
+    const uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) sg[i] = F.has(i, lane) ? ldcg(srow + 32 * i + lane) : 0ull;
     bcv = lane == 0 ? ldcg(p.bc + v) : 0.0;
   }
 };
 
-// Header of up to four consecutive queue entries, loaded with one round of
-// lane-parallel loads: lane 4f+i holds field f of entry i.
-struct EntryHeaders {
+// Headers of up to kEntries consecutive queue entries, loaded with one round
+// of lane-parallel loads: lane kEntries*f + i holds field f of entry i.
+template <int W, int kFields> struct EntryHeaders {
+  static constexpr int kEntries = kFields * 4 <= kWarp ? 4 : 2;
   uint64_t hv;
   int cnt;
   __device__ __forceinline__ uint64_t field(int f, int i) const {
-    return __shfl_sync(kFull, hv, 4 * f + i);
+    return __shfl_sync(kFull, hv, kEntries * f + i);
+  }
+  __device__ __forceinline__ Mask<W> mask(int i) const {
+    Mask<W> m;
+#pragma unroll
+    for (int wi = 0; wi < W; ++wi) m.w[wi] = field(wi, i);
+    return m;
   }
 };
 
-// Forward headers: f0 = mask F (from the dense level mask), f1/f2 = in-CSR
-// range, f3/f4 = out-CSR range, f5 = chunk count, f6 = vertex id.
-__device__ __forceinline__ EntryHeaders fwd_headers(const KParams &p, const uint64_t *A,
-                                                    int64_t e0, int cnt, int lane) {
+// Forward headers: fields 0..W-1 = mask words (from the dense level mask),
+// then in-CSR range, out-CSR range, chunk count, vertex id.
+template <int W> struct FwdField {
+  static constexpr int kIn0 = W, kIn1 = W + 1, kOut0 = W + 2, kOut1 = W + 3, kNch = W + 4,
+                       kId = W + 5, kCount = W + 6;
+};
+template <int W>
+__device__ __forceinline__ EntryHeaders<W, FwdField<W>::kCount>
+fwd_headers(const KParams &p, const uint64_t *A, int64_t e0, int cnt, int lane) {
+  using F = FwdField<W>;
+  using H = EntryHeaders<W, F::kCount>;
   int wv = 0;
   if (lane < cnt) wv = ldcg(p.w.qv + e0 + lane);
-  const int i = lane & 3, f = lane >> 2;
+  const int i = lane % H::kEntries, f = lane / H::kEntries;
   const int w = __shfl_sync(kFull, wv, i);
   uint64_t hv = 0;
-  if (i < cnt) {
-    switch (f) {
-      case 0: hv = ldcg(A + w); break;
-      case 1: hv = (uint64_t)(uint32_t)__ldg(p.g.in_ptr + w); break;
-      case 2: hv = (uint64_t)(uint32_t)__ldg(p.g.in_ptr + w + 1); break;
-      case 3: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + w); break;
-      case 4: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + w + 1); break;
-      case 5: hv = (uint64_t)(uint32_t)__ldg(p.g.nchunks + w); break;
-      case 6: hv = (uint64_t)(uint32_t)w; break;
-      default: break;
-    }
+  if (i < cnt && f < F::kCount) {
+    if (f < W) hv = ldcg(A + (size_t)w * W + f);
+    else if (f == F::kIn0) hv = (uint64_t)(uint32_t)__ldg(p.g.in_ptr + w);
+    else if (f == F::kIn1) hv = (uint64_t)(uint32_t)__ldg(p.g.in_ptr + w + 1);
+    else if (f == F::kOut0) hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + w);
+    else if (f == F::kOut1) hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + w + 1);
+    else if (f == F::kNch) hv = (uint64_t)(uint32_t)__ldg(p.g.nchunks + w);
+    else hv = (uint64_t)(uint32_t)w;
   }
-  EntryHeaders h;
+  H h;
   h.hv = hv;
   h.cnt = cnt;
   return h;
 }
 
-// Backward headers: f0 = mask (queue), f1/f2 = out-CSR range, f3 = chunk
-// count, f4 = vertex id.
-__device__ __forceinline__ EntryHeaders bwd_headers(const KParams &p, int64_t e0, int cnt,
-                                                    int lane) {
+// Backward headers: fields 0..W-1 = mask words (queue), then out-CSR range,
+// chunk count, vertex id.
+template <int W> struct BwdField {
+  static constexpr int kOut0 = W, kOut1 = W + 1, kNch = W + 2, kId = W + 3, kCount = W + 4;
+};
+template <int W>
+__device__ __forceinline__ EntryHeaders<W, BwdField<W>::kCount>
+bwd_headers(const KParams &p, int64_t e0, int cnt, int lane) {
+  using F = BwdField<W>;
+  using H = EntryHeaders<W, F::kCount>;
   int wv = 0;
   if (lane < cnt) wv = ldcg(p.w.qv + e0 + lane);
-  uint64_t mq = 0;
-  if (lane < cnt) mq = ldcg(p.w.qm + e0 + lane);
-  const int i = lane & 3, f = lane >> 2;
+  const int i = lane % H::kEntries, f = lane / H::kEntries;
   const int v = __shfl_sync(kFull, wv, i);
-  const uint64_t F = __shfl_sync(kFull, mq, i);
   uint64_t hv = 0;
-  if (i < cnt) {
-    switch (f) {
-      case 0: hv = F; break;
-      case 1: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + v); break;
-      case 2: hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + v + 1); break;
-      case 3: hv = (uint64_t)(uint32_t)__ldg(p.g.nchunks + v); break;
-      case 4: hv = (uint64_t)(uint32_t)v; break;
-      default: break;
-    }
+  if (i < cnt && f < F::kCount) {
+    if (f < W) hv = ldcg(p.w.qm + (size_t)(e0 + i) * W + f);
+    else if (f == F::kOut0) hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + v);
+    else if (f == F::kOut1) hv = (uint64_t)(uint32_t)__ldg(p.g.row_ptr + v + 1);
+    else if (f == F::kNch) hv = (uint64_t)(uint32_t)__ldg(p.g.nchunks + v);
+    else hv = (uint64_t)(uint32_t)v;
   }
-  EntryHeaders h;
+  H h;
   h.hv = hv;
   h.cnt = cnt;
   return h;
@@ -387,12 +405,19 @@ __device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, Coun
   }
 }
 
-// One batch of up to 64 sources through both sweeps, in the given scope.
+// Sets the path counts of a level-0 entry (every source bit of it is the
+// vertex itself: one path) in the lane's slots.
+template <int W> __device__ __forceinline__ void unit_counts(uint64_t (&s)[2 * W]) {
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i) s[i] = 1;
+}
+
+// One batch of up to 64*W sources through both sweeps, in the given scope.
 // Returns early (leaving the workspace dirty) when the job is in an error
 // state.  Warp counters accumulate into cnt.
-template <typename DT, typename Scope>
-__device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
-                                           unsigned long long *wacc, int *stage, Counters &cnt) {
+template <typename DT, int W, typename Scope>
+__device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int *stage,
+                                           Counters &cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)sc.size() * kWarpsPerBlock;
@@ -400,18 +425,17 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
   const int64_t nthr = (int64_t)sc.size() * kBlock;
   Ctl *ctl = p.w.ctl;
   const int n = p.g.n;
+  const size_t nW = (size_t)n * W; // words of one dense level mask array
   uint64_t *const fr = p.w.fr;
+  constexpr int kRow = kK * W;     // sources per state row
 
   if (read_err(ctl)) return;
-  // sources owned by this lane (for excluding s from its own BC)
-  const int s_lo = lane < p.k ? __ldg(p.src + lane) : -1;
-  const int s_hi = lane + 32 < p.k ? __ldg(p.src + lane + 32) : -1;
 
   // ---- init: level 0 = the sources (block 0) ------------------------------
   if (sc.rank() == 0) {
     if (threadIdx.x == 0) {
       ctl->tail = 0;
-      ctl->ovf = 0;
+      for (int i = 0; i < kMaxWords; ++i) ctl->ovf[i] = 0;
       ctl->nlevels = 0;
       for (int i = 0; i < 4; ++i) ctl->work[i] = 0;
       p.w.hpack[0] = 0;
@@ -423,9 +447,12 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
     if (threadIdx.x < p.k) {
       const int j = threadIdx.x;
       const int s = __ldg(p.src + j);
-      atomicOr(reinterpret_cast<unsigned long long *>(p.w.vis + s), 1ull << j);
-      const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(fr + s), 1ull << j);
-      if (old == 0) {
+      const size_t word = (size_t)s * W + (j >> 6);
+      const unsigned long long bit = 1ull << (j & 63);
+      atomicOr(reinterpret_cast<unsigned long long *>(p.w.vis + word), bit);
+      const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(fr + word), bit);
+      const bool first = W == 1 ? old == 0 : atomicMax(p.w.claim + s, 1) < 1;
+      if (first) {
         const unsigned long long pos = atomicAdd(&ctl->tail, 1ull);
         p.w.qv[pos] = s;
         const int nch = __ldg(p.g.nchunks + s);
@@ -453,10 +480,10 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
   int step = 0;
   while (true) {
     const int l = lv.lvl;
-    uint64_t *Bn = fr + (size_t)((l + 1) & 3) * n;      // level l+1 (being built)
-    const uint64_t *A = fr + (size_t)(l & 3) * n;       // level l
-    const uint64_t *Pm = fr + (size_t)((l + 3) & 3) * n; // level l-1
-    uint64_t *Z = fr + (size_t)((l + 2) & 3) * n;       // level l-2 (cleared now)
+    uint64_t *Bn = fr + (size_t)((l + 1) & 3) * nW;      // level l+1 (being built)
+    const uint64_t *A = fr + (size_t)(l & 3) * nW;       // level l
+    const uint64_t *Pm = fr + (size_t)((l + 3) & 3) * nW; // level l-1
+    uint64_t *Z = fr + (size_t)((l + 2) & 3) * nW;       // level l-2 (cleared now)
     const unsigned long long hp = ldcg(p.w.hpack + l);
     lv.nheavy = (int64_t)(hp >> 32);
     lv.nhc = (int64_t)(hp & 0xffffffffull);
@@ -467,7 +494,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
     }
     zero_ring_ahead(ctl, step, gtid);
     if (l >= 2)
-      for (int64_t i = lo_m2 + gtid; i < lo_m1; i += nthr) Z[ldcg(p.w.qv + i)] = 0;
+      for (int64_t i = lo_m2 + gtid; i < lo_m1; i += nthr) zero_mask<W>(Z, ldcg(p.w.qv + i));
 
     unsigned long long *ctr = &ctl->work[step & 3];
     const int64_t total = lv.nhc + (lv.hi - lv.lo);
@@ -487,84 +514,85 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
         const int64_t h = hc.h;
         const int64_t e = ldcg(p.w.hq_e + h);
         const int w = ldcg(p.w.qv + e);
-        const uint64_t F = ldcg(A + w);
+        const Mask<W> F = load_mask<W>(A, w);
         const int nch = __ldg(p.g.nchunks + w);
         const int64_t c = item - hc.first;
         const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
         const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
         const int64_t indeg = ie - is, tot = indeg + (re - rs);
         const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
-        uint64_t s0 = 0, s1 = 0;
-        bool o0 = false, o1 = false;
+        uint64_t s[2 * W] = {};
+        unsigned cb = 0;
         const int64_t ib = is + (a < indeg ? a : indeg), ie2 = is + (b < indeg ? b : indeg);
         const int64_t obg = rs + (a > indeg ? a - indeg : 0);
         const int64_t oen = rs + (b > indeg ? b - indeg : 0);
-        fwd_scan(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage, nst, lane,
-                 s0, s1, o0, o1, cnt.dag);
+        fwd_scan<W>(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage, nst,
+                    lane, s, cb, cnt.dag);
         if (lane == 0) {
           cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
           cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
           cnt.heavy++;
         }
-        uint64_t *part = reinterpret_cast<uint64_t *>(p.w.partial) + (size_t)item * kK;
-        part[lane] = s0;
-        part[32 + lane] = s1;
-        const uint64_t ob = (uint64_t)__ballot_sync(kFull, o0) |
-                            ((uint64_t)__ballot_sync(kFull, o1) << 32);
-        if (lane == 0) p.w.partial_ovf[item] = ob;
+        uint64_t *part = reinterpret_cast<uint64_t *>(p.w.partial) + (size_t)item * kRow;
+#pragma unroll
+        for (int i = 0; i < 2 * W; ++i) part[32 * i + lane] = s[i];
+#pragma unroll
+        for (int wi = 0; wi < W; ++wi) {
+          const uint64_t ob = (uint64_t)__ballot_sync(kFull, (cb >> (2 * wi)) & 1u) |
+                              ((uint64_t)__ballot_sync(kFull, (cb >> (2 * wi + 1)) & 1u) << 32);
+          if (lane == 0) p.w.partial_ovf[(size_t)item * W + wi] = ob;
+        }
         const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
         if (ticket == (unsigned)(nch - 1)) {
           const int64_t c0 = hc.first;
-          uint64_t t0 = 0, t1 = 0;
-          bool q0 = false, q1 = false;
-          uint64_t ovb = 0;
+          uint64_t t[2 * W] = {};
+          unsigned q = 0;
           if (l == 0) {
-            t0 = 1;
-            t1 = 1;
+            unit_counts<W>(t);
           } else {
             const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
-#pragma unroll 4
             for (int64_t cc = c0; cc < c0 + nch; ++cc) {
-              sat_add(t0, ldcg(pp + (size_t)cc * kK + lane), q0);
-              sat_add(t1, ldcg(pp + (size_t)cc * kK + 32 + lane), q1);
-              ovb |= ldcg(p.w.partial_ovf + cc);
+#pragma unroll
+              for (int i = 0; i < 2 * W; ++i) {
+                bool o = false;
+                sat_add(t[i], ldcg(pp + (size_t)cc * kRow + 32 * i + lane), o);
+                const uint64_t ow = ldcg(p.w.partial_ovf + (size_t)cc * W + (i >> 1));
+                if (o || ((ow >> ((i & 1) * 32 + lane)) & 1ull)) q |= 1u << i;
+              }
             }
           }
-          batch_store_sigma(p, w, F, t0, t1, q0 || ((ovb >> lane) & 1ull),
-                            q1 || ((ovb >> (lane + 32)) & 1ull), lane);
+          batch_store_sigma_w<W>(p, w, F, t, q, lane);
           if (lane == 0) {
             p.w.harrive[h] = 0;
-            p.w.qm[e] = F;
-            p.w.vis[w] = ldcg(p.w.vis + w) | F;
+            store_mask<W>(p.w.qm, e, F);
+            store_mask<W>(p.w.vis, w, load_mask<W>(p.w.vis, w) | F);
             cnt.entries++;
-            cnt.reached += __popcll(F);
+            cnt.reached += F.popc();
           }
         }
       }
       if (end > lv.nhc) {
+        using FF = FwdField<W>;
         const int64_t first = base > lv.nhc ? base : lv.nhc;
         const int64_t e0 = lv.lo + (first - lv.nhc);
-        const EntryHeaders hd = fwd_headers(p, A, e0, (int)(end - first), lane);
+        const auto hd = fwd_headers<W>(p, A, e0, (int)(end - first), lane);
         for (int i = 0; i < hd.cnt; ++i) {
-          if (hd.field(5, i) != 0) continue; // heavy: handled as chunks
-          const uint64_t F = hd.field(0, i);
-          const int64_t is = (int64_t)hd.field(1, i), ie = (int64_t)hd.field(2, i);
-          const int64_t rs = (int64_t)hd.field(3, i), re = (int64_t)hd.field(4, i);
-          const int w = (int)hd.field(6, i);
-          uint64_t s0 = 0, s1 = 0;
-          bool o0 = false, o1 = false;
-          fwd_scan(p, lv, F, l > 0 ? is : 0, l > 0 ? ie : 0, rs, re, A, Pm, Bn, stage, nst, lane,
-                   s0, s1, o0, o1, cnt.dag);
-          if (l == 0) {
-            s0 = 1;
-            s1 = 1;
-          }
-          batch_store_sigma(p, w, F, s0, s1, o0, o1, lane);
+          if (hd.field(FF::kNch, i) != 0) continue; // heavy: handled as chunks
+          const Mask<W> F = hd.mask(i);
+          const int64_t is = (int64_t)hd.field(FF::kIn0, i), ie = (int64_t)hd.field(FF::kIn1, i);
+          const int64_t rs = (int64_t)hd.field(FF::kOut0, i), re = (int64_t)hd.field(FF::kOut1, i);
+          const int w = (int)hd.field(FF::kId, i);
+          uint64_t s[2 * W] = {};
+          unsigned cb = 0;
+          fwd_scan<W>(p, lv, F, l > 0 ? is : 0, l > 0 ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
+                      lane, s, cb, cnt.dag);
+          if (l == 0) unit_counts<W>(s);
+          batch_store_sigma_w<W>(p, w, F, s, cb, lane);
           if (lane == 0) {
-            p.w.vis[w] = ldcg(p.w.vis + w) | F;
-            p.w.qm[e0 + i] = F;
+            store_mask<W>(p.w.vis, w, load_mask<W>(p.w.vis, w) | F);
+            store_mask<W>(p.w.qm, e0 + i, F);
             cnt.entries++;
-            cnt.reached += __popcll(F);
+            cnt.reached += F.popc();
             cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
             cnt.out_e += (uint64_t)(re - rs);
           }
@@ -596,16 +624,18 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
     ctl->nlevels = L;
     atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
     atomicAdd(p.job_cnt + CNT_LEVELS, (unsigned long long)L);
-    const uint64_t ob = ldcg(&ctl->ovf);
-    for (int j = 0; j < p.k; ++j)
-      if ((ob >> j) & 1ull) p.ovf_flags[p.src_base + j] = 1;
+    for (int wi = 0; wi < W; ++wi) {
+      const uint64_t ob = ldcg(&ctl->ovf[wi]);
+      for (int j = 64 * wi; j < p.k && j < 64 * (wi + 1); ++j)
+        if ((ob >> (j & 63)) & 1ull) p.ovf_flags[p.src_base + j] = 1;
+    }
   }
 
   // ---- backward sweep ------------------------------------------------------
   for (int l = L - 1; l >= 0; --l) {
-    const uint64_t *Dn = fr + (size_t)((l + 1) & 3) * n; // level l+1 masks
-    uint64_t *Wn = l > 0 ? fr + (size_t)(l & 3) * n : nullptr; // level l masks for step l-1
-    uint64_t *Z = fr + (size_t)((l + 2) & 3) * n;        // level l+2 (cleared now)
+    const uint64_t *Dn = fr + (size_t)((l + 1) & 3) * nW; // level l+1 masks
+    uint64_t *Wn = l > 0 ? fr + (size_t)(l & 3) * nW : nullptr; // level l masks for step l-1
+    uint64_t *Z = fr + (size_t)((l + 2) & 3) * nW;        // level l+2 (cleared now)
     LevelView bl;
     bl.lvl = l;
     bl.lo = ldcg(p.w.qoff + l);
@@ -618,7 +648,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
     zero_ring_ahead(ctl, step, gtid);
     if (l + 2 <= L - 1) {
       const int64_t zlo = ldcg(p.w.qoff + l + 2), zhi = ldcg(p.w.qoff + l + 3);
-      for (int64_t i = zlo + gtid; i < zhi; i += nthr) Z[ldcg(p.w.qv + i)] = 0;
+      for (int64_t i = zlo + gtid; i < zhi; i += nthr) zero_mask<W>(Z, ldcg(p.w.qv + i));
     }
     const bool deepest = (l == L - 1);
     unsigned long long *ctr = &ctl->work[step & 3];
@@ -637,54 +667,51 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
         const int64_t h = hc.h;
         const int64_t e = ldcg(p.w.hq_e + h);
         const int v = ldcg(p.w.qv + e);
-        const uint64_t F = ldcg(p.w.qm + e);
+        const Mask<W> F = load_mask<W>(p.w.qm, e);
         const int nch = __ldg(p.g.nchunks + v);
         const int64_t c = item - hc.first;
         const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
         const int64_t od = re - rs;
         const int64_t a = c * od / nch, b = (c + 1) * od / nch;
-        DT a0 = 0, a1 = 0;
-        if (!deepest)
-          batch_pull_delta<DT>(p, F, rs + a, rs + b, Dn, lane, reinterpret_cast<DT *>(wacc), a0,
-                               a1);
+        DT acc[2 * W] = {};
+        if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs + a, rs + b, Dn, lane, acc);
         if (lane == 0) {
           cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
           cnt.heavy++;
         }
-        DT *part = reinterpret_cast<DT *>(p.w.partial) + (size_t)item * kK;
-        part[lane] = a0;
-        part[32 + lane] = a1;
+        DT *part = reinterpret_cast<DT *>(p.w.partial) + (size_t)item * kRow;
+#pragma unroll
+        for (int i = 0; i < 2 * W; ++i) part[32 * i + lane] = acc[i];
         const unsigned ticket = chunk_ticket(p.w.harrive + h, lane);
         if (ticket == (unsigned)(nch - 1)) {
           const int64_t c0 = hc.first;
           const DT *pp = reinterpret_cast<const DT *>(p.w.partial);
-          DT t0 = 0, t1 = 0;
-#pragma unroll 4
-          for (int64_t cc = c0; cc < c0 + nch; ++cc) {
-            t0 += ldcg(pp + (size_t)cc * kK + lane);
-            t1 += ldcg(pp + (size_t)cc * kK + 32 + lane);
-          }
-          const EntryOwn own(p, v, F, lane);
-          batch_finish<DT>(p, l, v, F, t0, t1, own.sg0, own.sg1, own.bcv, Wn, s_lo, s_hi, lane);
+          DT t[2 * W] = {};
+          for (int64_t cc = c0; cc < c0 + nch; ++cc)
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) t[i] += ldcg(pp + (size_t)cc * kRow + 32 * i + lane);
+          const EntryOwn<W> own(p, v, F, lane);
+          batch_finish<DT, W>(p, l, v, F, t, own.sg, own.bcv, Wn, lane);
           if (lane == 0) p.w.harrive[h] = 0;
         }
       }
       if (end > bl.nhc) {
+        using BF = BwdField<W>;
         const int64_t first = base > bl.nhc ? base : bl.nhc;
         const int64_t e0 = bl.lo + (first - bl.nhc);
-        const EntryHeaders hd = bwd_headers(p, e0, (int)(end - first), lane);
+        const auto hd = bwd_headers<W>(p, e0, (int)(end - first), lane);
         for (int i = 0; i < hd.cnt; ++i) {
-          if (hd.field(3, i) != 0) continue;
-          const uint64_t F = hd.field(0, i);
-          const int64_t rs = (int64_t)hd.field(1, i), re = (int64_t)hd.field(2, i);
-          const int v = (int)hd.field(4, i);
-          const EntryOwn own(p, v, F, lane);
-          DT a0 = 0, a1 = 0;
+          if (hd.field(BF::kNch, i) != 0) continue;
+          const Mask<W> F = hd.mask(i);
+          const int64_t rs = (int64_t)hd.field(BF::kOut0, i), re = (int64_t)hd.field(BF::kOut1, i);
+          const int v = (int)hd.field(BF::kId, i);
+          const EntryOwn<W> own(p, v, F, lane);
+          DT acc[2 * W] = {};
           if (!deepest) {
-            batch_pull_delta<DT>(p, F, rs, re, Dn, lane, reinterpret_cast<DT *>(wacc), a0, a1);
+            batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
             if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
           }
-          batch_finish<DT>(p, l, v, F, a0, a1, own.sg0, own.sg1, own.bcv, Wn, s_lo, s_hi, lane);
+          batch_finish<DT, W>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
         }
       }
       base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
@@ -702,17 +729,16 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc,
   {
     const int64_t q1 = ldcg(p.w.qoff + 1);
     const int64_t q2 = L >= 2 ? ldcg(p.w.qoff + 2) : q1;
-    for (int64_t i = gtid; i < q1; i += nthr) fr[ldcg(p.w.qv + i)] = 0;
-    for (int64_t i = q1 + gtid; i < q2; i += nthr) fr[(size_t)n + ldcg(p.w.qv + i)] = 0;
+    for (int64_t i = gtid; i < q1; i += nthr) zero_mask<W>(fr, ldcg(p.w.qv + i));
+    for (int64_t i = q1 + gtid; i < q2; i += nthr) zero_mask<W>(fr + nW, ldcg(p.w.qv + i));
   }
 }
 
-template <typename DT>
+template <typename DT, int W>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
-  __shared__ unsigned long long s_acc[kWarpsPerBlock][kK]; // warp-private gather rows
-  __shared__ int s_stage[kWarpsPerBlock][kStage];           // warp-private new-vertex stage
+  __shared__ int s_stage[kWarpsPerBlock][kStage]; // warp-private new-vertex stage
   Counters cnt;
-  batch_body<DT>(p, GridScope(), s_acc[threadIdx.x >> 5], s_stage[threadIdx.x >> 5], cnt);
+  batch_body<DT, W>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt);
   flush_counters(p.job_cnt, cnt, threadIdx.x & 31);
 }
 
@@ -722,7 +748,6 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
 // graph's BC is written by one block without atomics.
 template <typename DT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const ManyParams mp) {
-  __shared__ unsigned long long s_acc[kWarpsPerBlock][kK];
   __shared__ int s_stage[kWarpsPerBlock][kStage];
   __shared__ int s_item;
   Counters cnt;
@@ -742,7 +767,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
       p.src = (mp.grouped && p.g.order ? p.g.order : mp.iota) + b0;
       p.k = p.g.n - b0 < mp.kb ? p.g.n - b0 : mp.kb;
       p.src_base = off + b0;
-      batch_body<DT>(p, CtaScope(), s_acc[threadIdx.x >> 5], s_stage[threadIdx.x >> 5], cnt);
+      batch_body<DT, 1>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt);
       __syncthreads();
       if (read_err(p.w.ctl)) break;
     }
@@ -835,7 +860,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->tail = 1;
-    ctl->ovf = 0;
+    ctl->ovf[0] = 0;
     for (int i = 0; i < 4; ++i) ctl->work[i] = 0;
     p.w.qv[0] = s;
     p.w.d[s] = 0;
@@ -923,7 +948,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
               }
             }
             p.w.sigma[w] = t;
-            if (q) atomicOr(&ctl->ovf, 1ull);
+            if (q) atomicOr(&ctl->ovf[0], 1ull);
             p.w.harrive[h] = 0;
             cnt.entries++;
             cnt.reached++;
@@ -940,7 +965,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
           warp_sat_sum(sv, o);
           if (lane == 0) {
             p.w.sigma[w] = (l == 0) ? 1ull : sv;
-            if (o) atomicOr(&ctl->ovf, 1ull);
+            if (o) atomicOr(&ctl->ovf[0], 1ull);
             cnt.entries++;
             cnt.reached++;
             cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
@@ -967,7 +992,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
     ctl->nlevels = L;
     atomicMax(p.job_cnt + CNT_MAXLEV, (unsigned long long)L);
     atomicAdd(p.job_cnt + CNT_LEVELS, (unsigned long long)L);
-    if (ldcg(&ctl->ovf)) p.ovf_flags[p.src_base] = 1;
+    if (ldcg(&ctl->ovf[0])) p.ovf_flags[p.src_base] = 1;
   }
 
   for (int l = L - 1; l >= 0; --l) {
@@ -1077,9 +1102,20 @@ template <typename K> cudaError_t coop_launch(K kernel, const KParams &p, int gr
 
 } // namespace
 
-cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st) {
-  return fp64 ? coop_launch(batch_kernel<double>, p, grid, st)
-              : coop_launch(batch_kernel<float>, p, grid, st);
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words) {
+  switch (words) {
+    case 1:
+      return fp64 ? coop_launch(batch_kernel<double, 1>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 1>, p, grid, st);
+    case 2:
+      return fp64 ? coop_launch(batch_kernel<double, 2>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 2>, p, grid, st);
+    case 4:
+      return fp64 ? coop_launch(batch_kernel<double, 4>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 4>, p, grid, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st) {
@@ -1107,9 +1143,20 @@ int max_grid_many(bool fp64, int device) {
               : max_grid_for(many_kernel<float>, device);
 }
 
-int max_grid_batch(bool fp64, int device) {
-  return fp64 ? max_grid_for(batch_kernel<double>, device)
-              : max_grid_for(batch_kernel<float>, device);
+int max_grid_batch(bool fp64, int device, int words) {
+  switch (words) {
+    case 1:
+      return fp64 ? max_grid_for(batch_kernel<double, 1>, device)
+                  : max_grid_for(batch_kernel<float, 1>, device);
+    case 2:
+      return fp64 ? max_grid_for(batch_kernel<double, 2>, device)
+                  : max_grid_for(batch_kernel<float, 2>, device);
+    case 4:
+      return fp64 ? max_grid_for(batch_kernel<double, 4>, device)
+                  : max_grid_for(batch_kernel<float, 4>, device);
+    default:
+      return 0;
+  }
 }
 
 int max_grid_plain(bool fp64, int device) {

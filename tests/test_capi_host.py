@@ -66,5 +66,5 @@ def test_product_path_never_touches_the_oracle():
 def test_options_struct_matches_header():
     from paper_1409_7764_gb300 import capi
     assert ctypes.sizeof(capi.bc_opts) == 7 * 4
-    # int64 x5, int32 x2, double, int64 x6, int32 x4
-    assert ctypes.sizeof(capi.bc_stats) == 5 * 8 + 2 * 4 + 8 + 6 * 8 + 4 * 4
+    # int64 x5, int32 x2, double, int64 x6, int32 x6
+    assert ctypes.sizeof(capi.bc_stats) == 5 * 8 + 2 * 4 + 8 + 6 * 8 + 6 * 4

@@ -285,3 +285,103 @@ def test_batch_composition(ctx, fp64):
     assert_bc_close(ctx.sources(G, srcs, delta_fp64=fp64, keep_source_order=True), sref, fp64)
     assert_bc_close(ctx.sources(G, srcs[::-1].copy(), delta_fp64=fp64), sref, fp64)
     ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("kb", [65, 128, 200, 256])
+def test_wide_batches(ctx, fp64, kb):
+    """Batches of more than 64 sources (masks of 2 or 4 words): exact and
+    sampled BC against the oracle, including hubs split into chunks, a ragged
+    last batch and duplicate sources; d and sigma stay bit-exact through the
+    same kernel (checked on the narrow debug path elsewhere)."""
+    g = hub_graph()
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    got = ctx.exact(G, delta_fp64=fp64, batch_k=kb, schedule="batch_queue")
+    st = ctx.last_stats()
+    assert st["batch_sources"] == kb and st["mask_words"] == (2 if kb <= 128 else 4)
+    assert_bc_close(got, ref, fp64)
+    r = bcgen.rmat(12, 16, seed=8)
+    R = ctx.create_graph(r.row_ptr, r.col_idx)
+    srcs = np.concatenate([bcgen.sample_sources(r.n, 900, seed=4), [5, 5, 7]]).astype(np.int32)
+    sref, _ = oracle.bc(r.n, r.row_ptr, r.col_idx, srcs)
+    assert_bc_close(ctx.sources(R, srcs, delta_fp64=fp64, batch_k=kb), sref, fp64)
+    ctx.destroy_graph(G)
+    ctx.destroy_graph(R)
+
+
+def test_wide_batch_width_is_automatic(ctx):
+    """Without batch_k the library takes 256 sources per batch once the job
+    has eight such batches, 128 below that, and 64 for small jobs."""
+    g = bcgen.rmat(11, 8, seed=2)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    for k, words in ((2048, 4), (1800, 2), (1024, 2), (1000, 1), (300, 1)):
+        srcs = bcgen.sample_sources(g.n, k, seed=k)
+        ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+        assert_bc_close(ctx.sources(G, srcs, delta_fp64=True), ref, True)
+        assert ctx.last_stats()["mask_words"] == words
+    ctx.destroy_graph(G)
+
+
+def test_wide_batch_overflow_flags(ctx):
+    """Path-count overflow in a batch of 256 sources: the job reports it and
+    counts the flagged sources exactly as the oracle does."""
+    import paper_1409_7764_gb300 as bc
+    g = bcgen.layered_chain(64, 2)  # 2^64 paths from the first vertex to the last
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    srcs = np.concatenate([np.zeros(3, np.int32), np.arange(g.n, dtype=np.int32)])
+    _, ovf = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    with pytest.raises(bc.BCError) as ei:
+        ctx.sources(G, srcs, batch_k=256, delta_fp64=True)
+    assert ei.value.status == bc.BC_ERR_SIGMA_OVERFLOW
+    assert ei.value.stats["overflow_sources"] == int(np.count_nonzero(ovf))
+    assert ei.value.stats["mask_words"] == 4
+    ctx.destroy_graph(G)
+
+
+def test_wide_batch_depths_and_counts_bit_exact(ctx):
+    """Depths and path counts of every source of a 256-source batch (and a
+    ragged 150-source one) equal the oracle's bit for bit."""
+    g = hub_graph()
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    srcs = np.concatenate([bcgen.sample_sources(g.n, 250, seed=3), [0, 0, 5, 3040, 3040, 1]])
+    for kb in (256, 150):
+        d, sig, dl = ctx.debug_sources(G, srcs.astype(np.int32), batch_k=kb, delta_fp64=True)
+        for i, s_ in enumerate(srcs):
+            od, osig, odl, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, int(s_))
+            np.testing.assert_array_equal(d[i], od)
+            np.testing.assert_array_equal(sig[i], osig)
+            np.testing.assert_allclose(dl[i], odl, rtol=1e-12, atol=0)
+    ctx.destroy_graph(G)
+
+
+def test_wide_batch_queue_overrun_reruns_narrow():
+    """A long path with 256 sources along it queues the deep vertices at more
+    than 64 distinct depths: the wide batch overruns its queue (sized for 64
+    depths per vertex; a fresh context, so no larger cached workspace), the
+    job reruns with 64 sources per batch and is still exact; later jobs on the
+    graph stay narrow."""
+    import paper_1409_7764_gb300 as bc
+    g = bcgen.path(320)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    with bc.Context(0) as fresh:
+        G = fresh.create_graph(g.row_ptr, g.col_idx)
+        got = fresh.exact(G, delta_fp64=True, batch_k=256, schedule="batch_queue")
+        assert_bc_close(got, ref, True)
+        assert fresh.last_stats()["mask_words"] == 1
+        assert_bc_close(fresh.exact(G, delta_fp64=False, batch_k=256), ref, False)
+        assert fresh.last_stats()["mask_words"] == 1
+        fresh.destroy_graph(G)
+
+
+def test_width_limits_of_other_schedules(ctx):
+    import paper_1409_7764_gb300 as bc
+    g = bcgen.rmat(8, 8, seed=1)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    for call in (lambda: ctx.exact(G, batch_k=128, schedule="batch_dense"),
+                 lambda: ctx.exact_many([G], batch_k=128),
+                 lambda: ctx.exact(G, batch_k=257)):
+        with pytest.raises(bc.BCError) as ei:
+            call()
+        assert ei.value.status == bc.BC_ERR_ARG
+    ctx.destroy_graph(G)
