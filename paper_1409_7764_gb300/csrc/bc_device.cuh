@@ -478,12 +478,12 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
 // level l+1 masks Dn: lane j sums c[x][32*i + j] over successors x whose
 // level-(l+1) mask has source 32*i + j, in edge order.
 template <int W, typename DT>
-__device__ __forceinline__ void batch_pull_delta_w(const KParams &p, const Mask<W> &F,
-                                                   int64_t eb, int64_t ee, const uint64_t *Dn,
-                                                   int lane, DT (&a)[2 * W]) {
+__device__ __forceinline__ void batch_pull_delta_w(const KParams &p, const Mask<W> &F, int eb,
+                                                   int ee, const uint64_t *Dn, int lane,
+                                                   DT (&a)[2 * W]) {
   const DT *cdep = reinterpret_cast<const DT *>(p.w.cdep);
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
+  for (int base = eb; base < ee; base += kWarp) {
+    const int e = base + lane;
     int x = 0;
     Mask<W> S = Mask<W>::zero();
     if (e < ee) {

@@ -181,49 +181,81 @@ __device__ __forceinline__ void stage_new(const KParams &p, const LevelView &lv,
 
 // Forward work of one frontier entry (mask F) at level l: the path-count
 // pull over in-edges [ib, ie) and the discovery push over out-edges
-// [ob, oe), advanced together 32 edges of each per round so that their
-// loads overlap.  A vertex x gets the bits F & ~(visited before level l |
-// level l | already marked for level l+1), OR-ed into its level-(l+1) mask.
-// The first toucher of x at level l+1 queues it: with one mask word the OR's
-// old value says so (all zero before); with several words a claim on x
-// decides (claim[x] < l+2 before, raised to l+2).  The returned value is only
-// read after the round's path-count gathers, so its latency overlaps them.
+// [ob, oe).  A vertex x gets the bits F & ~visited[x], OR-ed into its
+// level-(l+1) mask and into visited[x] (so visited holds every source that
+// reached x at levels up to l+1, and one load tests it), and the first
+// toucher of x at level l+1 queues it.  With one mask word the two
+// scans advance together, 32 edges of each per round so that their loads
+// overlap, and the OR's returned old value (all zero before) tells the first
+// toucher; it is read only after the round's path-count gathers.  With
+// several words no single atomic covers the mask: a claim on x decides
+// (claim[x] < l+2 before, raised to l+2).
 template <int W>
 __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, const Mask<W> &F,
-                                         int64_t ib, int64_t ie, int64_t ob, int64_t oe,
+                                         int ib, int ie, int ob, int oe,
                                          const uint64_t *A, const uint64_t *Pm, uint64_t *Bn,
                                          int *stage, int &nst, int lane, uint64_t (&s)[2 * W],
                                          unsigned &cbits, unsigned long long &dag) {
-  const int64_t din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
-  const int64_t span = din > dout ? din : dout;
+  const int din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
   const int claim_to = lv.lvl + 2;
-  for (int64_t r = 0; r < span; r += kWarp) {
-    const int64_t t = r + lane;
-    const bool vi = t < din, vo = t < dout;
-    int u = 0, x = 0;
-    if (vi) u = __ldg(p.g.in_idx + ib + t);
-    if (vo) x = __ldg(p.g.col_idx + ob + t);
-    Mask<W> P = Mask<W>::zero(), nb = Mask<W>::zero();
-    if (vi) P = load_mask<W>(Pm, u) & F;
-    if (vo)
-      nb = F.and_not(load_mask<W>(p.w.vis, x) | load_mask<W>(A, x) | load_mask<W>(Bn, x));
-    const bool any_new = nb.any();
-    unsigned long long old = 1;
-    if (any_new) {
-      if constexpr (W == 1) {
-        old = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb.w[0]);
-      } else {
-        unsigned long long *bx = reinterpret_cast<unsigned long long *>(Bn + (size_t)x * W);
-#pragma unroll
-        for (int wi = 0; wi < W; ++wi)
-          if (nb.w[wi]) atomicOr(bx + wi, nb.w[wi]);
-        old = (unsigned long long)atomicMax(p.w.claim + x, claim_to);
+  if constexpr (W >= 2) {
+    // wide masks: the pull and the push run as two loops, so the registers
+    // of the path-count gathers and of the discovery masks are not live
+    // together
+    for (int r = 0; r < din; r += kWarp) {
+      const int t = r + lane;
+      int u = 0;
+      Mask<W> P = Mask<W>::zero();
+      if (t < din) {
+        u = __ldg(p.g.in_idx + ib + t);
+        P = load_mask<W>(Pm, u) & F;
       }
+      dag += P.popc(); // per lane; the warp's counters are summed at the flush
+      gather_counts_w<W>(p.w.sigma, u, P, lane, s, cbits);
     }
-    dag += P.popc(); // per lane; the warp's counters are summed at the flush
-    gather_counts_w<W>(p.w.sigma, u, P, lane, s, cbits);
-    const bool first = any_new && (W == 1 ? old == 0 : (long long)old < claim_to);
-    stage_new(p, lv, first, x, stage, nst, lane);
+    for (int r = 0; r < dout; r += kWarp) {
+      const int t = r + lane;
+      int x = 0;
+      bool first = false;
+      if (t < dout) {
+        x = __ldg(p.g.col_idx + ob + t);
+        const Mask<W> nb = F.and_not(load_mask<W>(p.w.vis, x));
+        if (nb.any()) {
+          unsigned long long *bx = reinterpret_cast<unsigned long long *>(Bn + (size_t)x * W);
+          unsigned long long *vx = reinterpret_cast<unsigned long long *>(p.w.vis + (size_t)x * W);
+#pragma unroll
+          for (int wi = 0; wi < W; ++wi)
+            if (nb.w[wi]) {
+              atomicOr(bx + wi, nb.w[wi]);
+              atomicOr(vx + wi, nb.w[wi]);
+            }
+          first = atomicMax(p.w.claim + x, claim_to) < claim_to;
+        }
+      }
+      stage_new(p, lv, first, x, stage, nst, lane);
+    }
+  } else {
+    const int span = din > dout ? din : dout;
+    for (int r = 0; r < span; r += kWarp) {
+      const int t = r + lane;
+      const bool vi = t < din, vo = t < dout;
+      int u = 0, x = 0;
+      if (vi) u = __ldg(p.g.in_idx + ib + t);
+      if (vo) x = __ldg(p.g.col_idx + ob + t);
+      uint64_t P = 0, nb = 0;
+      if (vi) P = ldcg(Pm + u) & F.w[0];
+      if (vo) nb = F.w[0] & ~ldcg(p.w.vis + x);
+      unsigned long long old = 1;
+      if (nb) {
+        old = atomicOr(reinterpret_cast<unsigned long long *>(Bn + x), nb);
+        atomicOr(reinterpret_cast<unsigned long long *>(p.w.vis + x), nb);
+      }
+      dag += __popcll(P); // per lane; the warp's counters are summed at the flush
+      Mask<1> PM;
+      PM.w[0] = P;
+      gather_counts_w<1>(p.w.sigma, u, PM, lane, s, cbits);
+      stage_new(p, lv, nb != 0 && old == 0, x, stage, nst, lane);
+    }
   }
 }
 
@@ -405,6 +437,38 @@ __device__ __forceinline__ void flush_counters(unsigned long long *job_cnt, Coun
   }
 }
 
+#ifndef BC_OWN_EARLY_MAX_W
+#define BC_OWN_EARLY_MAX_W 2 // widest mask whose entries preload their own counts
+#endif
+
+// Work counters of one warp of the batch kernels, kept in shared memory
+// (lane 0 updates them) so that they hold no registers; the per-lane DAG pair
+// count stays in a register.
+struct WarpCounters {
+  unsigned long long entries, out_e, in_e, reached, heavy, busy, idle;
+};
+
+__device__ __forceinline__ void zero_counters(WarpCounters &w, int lane) {
+  if (lane == 0) w = WarpCounters{0, 0, 0, 0, 0, 0, 0};
+  __syncwarp();
+}
+
+__device__ __forceinline__ Counters to_counters(const WarpCounters &w, unsigned long long dag,
+                                                int lane) {
+  Counters c;
+  c.dag = dag;
+  if (lane == 0) {
+    c.entries = w.entries;
+    c.out_e = w.out_e;
+    c.in_e = w.in_e;
+    c.reached = w.reached;
+    c.heavy = w.heavy;
+    c.busy = w.busy;
+    c.idle = w.idle;
+  }
+  return c;
+}
+
 // Sets the path counts of a level-0 entry (every source bit of it is the
 // vertex itself: one path) in the lane's slots.
 template <int W> __device__ __forceinline__ void unit_counts(uint64_t (&s)[2 * W]) {
@@ -414,10 +478,10 @@ template <int W> __device__ __forceinline__ void unit_counts(uint64_t (&s)[2 * W
 
 // One batch of up to 64*W sources through both sweeps, in the given scope.
 // Returns early (leaving the workspace dirty) when the job is in an error
-// state.  Warp counters accumulate into cnt.
+// state.  Warp counters accumulate into cnt (shared, lane 0) and dag (lane).
 template <typename DT, int W, typename Scope>
 __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int *stage,
-                                           Counters &cnt) {
+                                           WarpCounters &cnt, unsigned long long &dag) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)sc.size() * kWarpsPerBlock;
@@ -517,17 +581,17 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         const Mask<W> F = load_mask<W>(A, w);
         const int nch = __ldg(p.g.nchunks + w);
         const int64_t c = item - hc.first;
-        const int64_t is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
-        const int64_t rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
-        const int64_t indeg = ie - is, tot = indeg + (re - rs);
-        const int64_t a = c * tot / nch, b = (c + 1) * tot / nch;
+        const int is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
+        const int rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+        const int indeg = ie - is, tot = indeg + (re - rs);
+        const int a = (int)(c * tot / nch), b = (int)((c + 1) * tot / nch);
         uint64_t s[2 * W] = {};
         unsigned cb = 0;
-        const int64_t ib = is + (a < indeg ? a : indeg), ie2 = is + (b < indeg ? b : indeg);
-        const int64_t obg = rs + (a > indeg ? a - indeg : 0);
-        const int64_t oen = rs + (b > indeg ? b - indeg : 0);
+        const int ib = is + (a < indeg ? a : indeg), ie2 = is + (b < indeg ? b : indeg);
+        const int obg = rs + (a > indeg ? a - indeg : 0);
+        const int oen = rs + (b > indeg ? b - indeg : 0);
         fwd_scan<W>(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage, nst,
-                    lane, s, cb, cnt.dag);
+                    lane, s, cb, dag);
         if (lane == 0) {
           cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
           cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
@@ -565,7 +629,6 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           if (lane == 0) {
             p.w.harrive[h] = 0;
             store_mask<W>(p.w.qm, e, F);
-            store_mask<W>(p.w.vis, w, load_mask<W>(p.w.vis, w) | F);
             cnt.entries++;
             cnt.reached += F.popc();
           }
@@ -579,17 +642,16 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         for (int i = 0; i < hd.cnt; ++i) {
           if (hd.field(FF::kNch, i) != 0) continue; // heavy: handled as chunks
           const Mask<W> F = hd.mask(i);
-          const int64_t is = (int64_t)hd.field(FF::kIn0, i), ie = (int64_t)hd.field(FF::kIn1, i);
-          const int64_t rs = (int64_t)hd.field(FF::kOut0, i), re = (int64_t)hd.field(FF::kOut1, i);
+          const int is = (int)hd.field(FF::kIn0, i), ie = (int)hd.field(FF::kIn1, i);
+          const int rs = (int)hd.field(FF::kOut0, i), re = (int)hd.field(FF::kOut1, i);
           const int w = (int)hd.field(FF::kId, i);
           uint64_t s[2 * W] = {};
           unsigned cb = 0;
           fwd_scan<W>(p, lv, F, l > 0 ? is : 0, l > 0 ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
-                      lane, s, cb, cnt.dag);
+                      lane, s, cb, dag);
           if (l == 0) unit_counts<W>(s);
           batch_store_sigma_w<W>(p, w, F, s, cb, lane);
           if (lane == 0) {
-            store_mask<W>(p.w.vis, w, load_mask<W>(p.w.vis, w) | F);
             store_mask<W>(p.w.qm, e0 + i, F);
             cnt.entries++;
             cnt.reached += F.popc();
@@ -604,8 +666,10 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
     stage_flush(p, lv, stage, nst, lane);
     const long long t_done = phase_clock();
     if (!sc.sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
-    cnt.busy += (unsigned long long)(t_done - t_step);
-    cnt.idle += (unsigned long long)(phase_clock() - t_done);
+    if (lane == 0) {
+      cnt.busy += (unsigned long long)(t_done - t_step);
+      cnt.idle += (unsigned long long)(phase_clock() - t_done);
+    }
     ++step;
     const int64_t nh = ldcg(p.w.qoff + l + 2);
     if (nh == lv.hi) {
@@ -670,9 +734,9 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         const Mask<W> F = load_mask<W>(p.w.qm, e);
         const int nch = __ldg(p.g.nchunks + v);
         const int64_t c = item - hc.first;
-        const int64_t rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
-        const int64_t od = re - rs;
-        const int64_t a = c * od / nch, b = (c + 1) * od / nch;
+        const int rs = __ldg(p.g.row_ptr + v), re = __ldg(p.g.row_ptr + v + 1);
+        const int od = re - rs;
+        const int a = (int)(c * od / nch), b = (int)((c + 1) * od / nch);
         DT acc[2 * W] = {};
         if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs + a, rs + b, Dn, lane, acc);
         if (lane == 0) {
@@ -703,23 +767,31 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         for (int i = 0; i < hd.cnt; ++i) {
           if (hd.field(BF::kNch, i) != 0) continue;
           const Mask<W> F = hd.mask(i);
-          const int64_t rs = (int64_t)hd.field(BF::kOut0, i), re = (int64_t)hd.field(BF::kOut1, i);
+          const int rs = (int)hd.field(BF::kOut0, i), re = (int)hd.field(BF::kOut1, i);
           const int v = (int)hd.field(BF::kId, i);
-          const EntryOwn<W> own(p, v, F, lane);
           DT acc[2 * W] = {};
-          if (!deepest) {
-            batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
-            if (lane == 0) cnt.out_e += (uint64_t)(re - rs);
+          if constexpr (W <= BC_OWN_EARLY_MAX_W) {
+            // own counts loaded ahead of the successor scan (overlapping it)
+            const EntryOwn<W> own(p, v, F, lane);
+            if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
+            batch_finish<DT, W>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+          } else {
+            // widest masks: loaded after it, which keeps 4W registers free
+            if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
+            const EntryOwn<W> own(p, v, F, lane);
+            batch_finish<DT, W>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           }
-          batch_finish<DT, W>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+          if (!deepest && lane == 0) cnt.out_e += (uint64_t)(re - rs);
         }
       }
       base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
     const long long t_done = phase_clock();
     if (!sc.sync(ctl, p.timeout_ns)) return;
-    cnt.busy += (unsigned long long)(t_done - t_step);
-    cnt.idle += (unsigned long long)(phase_clock() - t_done);
+    if (lane == 0) {
+      cnt.busy += (unsigned long long)(t_done - t_step);
+      cnt.idle += (unsigned long long)(phase_clock() - t_done);
+    }
     ++step;
   }
 
@@ -737,9 +809,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
 template <typename DT, int W>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
   __shared__ int s_stage[kWarpsPerBlock][kStage]; // warp-private new-vertex stage
-  Counters cnt;
-  batch_body<DT, W>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt);
-  flush_counters(p.job_cnt, cnt, threadIdx.x & 31);
+  __shared__ WarpCounters s_cnt[kWarpsPerBlock];
+  const int lane = threadIdx.x & 31;
+  WarpCounters &cnt = s_cnt[threadIdx.x >> 5];
+  zero_counters(cnt, lane);
+  unsigned long long dag = 0;
+  batch_body<DT, W>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+  __syncwarp();
+  flush_counters(p.job_cnt, to_counters(cnt, dag, lane), lane);
 }
 
 // Exact BC of many small graphs in one launch: each thread block takes the
@@ -749,8 +826,12 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
 template <typename DT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const ManyParams mp) {
   __shared__ int s_stage[kWarpsPerBlock][kStage];
+  __shared__ WarpCounters s_cnt[kWarpsPerBlock];
   __shared__ int s_item;
-  Counters cnt;
+  const int lane = threadIdx.x & 31;
+  WarpCounters &cnt = s_cnt[threadIdx.x >> 5];
+  zero_counters(cnt, lane);
+  unsigned long long dag = 0;
   KParams p = mp.base;
   p.w = mp.works[blockIdx.x];
   while (true) {
@@ -767,12 +848,13 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
       p.src = (mp.grouped && p.g.order ? p.g.order : mp.iota) + b0;
       p.k = p.g.n - b0 < mp.kb ? p.g.n - b0 : mp.kb;
       p.src_base = off + b0;
-      batch_body<DT, 1>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt);
+      batch_body<DT, 1>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       __syncthreads();
       if (read_err(p.w.ctl)) break;
     }
   }
-  flush_counters(p.job_cnt, cnt, threadIdx.x & 31);
+  __syncwarp();
+  flush_counters(p.job_cnt, to_counters(cnt, dag, lane), lane);
 }
 
 // ---------------------------------------------------------------------------
