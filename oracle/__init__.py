@@ -121,6 +121,39 @@ def canonicalise(n: int, row_ptr, col_idx):
     return orp, oci[:m].copy()
 
 
+def source_terms(n: int, row_ptr, col_idx, sources) -> np.ndarray:
+    """Per-source BC terms x[i, v] = delta_{s_i}(v) for v != s_i and 0 for
+    v == s_i (the terms whose sum over sources is BC, paper Section I), one
+    row per given source, from the sequential single-source Brandes above."""
+    src = _i32(sources)
+    x = np.zeros((src.size, n), dtype=np.float64)
+    for i, s_ in enumerate(src):
+        _, _, dl, _ = single_source(n, row_ptr, col_idx, int(s_))
+        x[i] = dl
+        x[i, int(s_)] = 0.0
+    return x
+
+
+def sampled_estimate(n: int, row_ptr, col_idx, sources):
+    """Estimate of BC from k sources drawn uniformly without replacement from
+    the n vertices, with its standard error.  Sampling is cited in the paper
+    (Section I) without an estimator; this is the textbook one: with x_s(v)
+    the per-source terms above, the sample mean m(v) and the sample variance
+    S2(v) = sum_s (x_s(v) - m(v))^2 / (k - 1) (two-pass, from the definition),
+        estimate(v) = n * m(v),
+        stderr(v)   = n * sqrt((1 - k/n) * S2(v) / k)
+    (the finite-population correction (1 - k/n) makes stderr 0 when every
+    vertex is a source).  Returns (estimate, stderr); stderr is NaN for k < 2."""
+    x = source_terms(n, row_ptr, col_idx, sources)
+    k = x.shape[0]
+    m = x.mean(axis=0) if k else np.zeros(n)
+    est = n * m
+    if k < 2:
+        return est, np.full(n, np.nan)
+    s2 = ((x - m) ** 2).sum(axis=0) / (k - 1)
+    return est, n * np.sqrt((1.0 - k / n) * s2 / k)
+
+
 def normalise(bc_raw: np.ndarray, n: int) -> np.ndarray:
     """Directed normalisation 1/((n-1)(n-2)) for n > 2 (NetworkX's
     normalized=True convention for DiGraphs); identity otherwise."""
