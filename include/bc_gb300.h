@@ -160,6 +160,36 @@ bc_status bc_exact(bc_ctx *ctx, bc_graph g, const bc_opts *opts, double *bc_out)
 bc_status bc_sources(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t k,
                      const bc_opts *opts, double *bc_out);
 
+/* Estimate of BC from k sources taken as a uniform sample without
+ * replacement from the n vertices, with its standard error (paper, Section I
+ * cites approximate BC by source sampling without fixing an estimator).
+ * With x_s(v) = delta_s(v) for v != s and 0 for v == s, m(v) their mean over
+ * the k sources and S2(v) their sample variance (k - 1 denominator):
+ *   est_out[v]    = n * m(v)
+ *   stderr_out[v] = n * sqrt((1 - k/n) * S2(v) / k)
+ * (NaN for k < 2; the finite-population factor 1 - k/n is taken as 0 when
+ * k >= n, so all n distinct sources give the exact BC with zero error).  The
+ * kernels accumulate sums of x and x^2 per vertex in FP64; opts.normalize
+ * scales both outputs by 1/((n-1)(n-2)); opts.scale_sampled is ignored.
+ * est_out / stderr_out: float64[n] each, host or device per opts.out_device.
+ * Errors as bc_sources; BC_ERR_SIGMA_OVERFLOW still writes the outputs. */
+bc_status bc_sources_estimate(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t k,
+                              const bc_opts *opts, double *est_out, double *stderr_out);
+
+/* Adaptive source sampling: takes sources from `order` (host int32[max_k],
+ * each in [0, n), a sample order drawn by the caller, e.g. a seeded
+ * permutation) in rounds of `round`, and stops after the first round at
+ * which every vertex whose estimate (in output units) is at least min_est
+ * has stderr <= rel_err * estimate, or when max_k sources are used.  Writes
+ * the estimate and standard error over the sources used (as
+ * bc_sources_estimate over order[0 .. *k_used)) and their number to k_used.
+ * Errors: BC_ERR_ARG for max_k < 1, round < 1, rel_err <= 0, null outputs or
+ * a source out of range. */
+bc_status bc_sources_adaptive(bc_ctx *ctx, bc_graph g, const int32_t *order, int32_t max_k,
+                              int32_t round, double rel_err, double min_est,
+                              const bc_opts *opts, double *est_out, double *stderr_out,
+                              int32_t *k_used);
+
 /* Queues a BC job (src == NULL: all sources; else k host sources, copied)
  * for the context's scheduler thread and returns at once.  Jobs are admitted
  * when their device footprint fits the HBM budget next to the jobs already

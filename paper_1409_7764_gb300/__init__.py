@@ -168,6 +168,38 @@ class Context:
         res = holder if dev else holder[:g.n]
         return self._finish(rc, res, "bc_sources")
 
+    def estimate(self, g: Graph, src, out=None, err_out=None, **opts):
+        """(estimate, standard error) of BC from the sources `src`, taken as a
+        uniform sample without replacement (bc_sources_estimate)."""
+        s = _i32(src)
+        ptr, dev, holder = _out_buffer(out, g.n)
+        eptr, edev, eholder = _out_buffer(err_out, g.n)
+        if dev != edev:
+            raise ValueError("estimate and error outputs must both be host or both device")
+        o = make_opts(out_device=dev, **opts)
+        rc = self._lib.bc_sources_estimate(self._h, g.handle, s.ctypes.data if s.size else None,
+                                           int(s.size), ctypes.byref(o), ptr, eptr)
+        res = (holder, eholder) if dev else (holder[:g.n], eholder[:g.n])
+        return self._finish(rc, res, "bc_sources_estimate")
+
+    def adaptive(self, g: Graph, order, rel_err: float, round: int = 1024, max_k=None,
+                 min_est: float = 0.0, **opts):
+        """(estimate, standard error, sources used): sources taken from
+        `order` in rounds until every vertex with estimate >= min_est has a
+        relative standard error <= rel_err (bc_sources_adaptive)."""
+        s = _i32(order)
+        mk = int(s.size if max_k is None else max_k)
+        est = np.empty(max(g.n, 1), dtype=np.float64)
+        err = np.empty(max(g.n, 1), dtype=np.float64)
+        used = ctypes.c_int32(0)
+        o = make_opts(**opts)
+        rc = self._lib.bc_sources_adaptive(self._h, g.handle, s.ctypes.data if s.size else None,
+                                           mk, int(round), float(rel_err), float(min_est),
+                                           ctypes.byref(o), est.ctypes.data, err.ctypes.data,
+                                           ctypes.byref(used))
+        res = (est[:g.n], err[:g.n], int(used.value))
+        return self._finish(rc, res, "bc_sources_adaptive")
+
     def exact_many(self, graphs, **opts):
         hs = np.array([g.handle for g in graphs], dtype=np.int64)
         total = sum(g.n for g in graphs)

@@ -287,6 +287,8 @@ struct JobRec {
   std::unique_ptr<WsRec> ws;
   int32_t *d_src = nullptr;
   double *d_bc = nullptr;
+  double *d_bc2 = nullptr;  // squared per-source terms (estimator jobs)
+  double *acc_sum = nullptr, *acc_sumsq = nullptr; // estimator jobs: running sums to add into
   int8_t *d_ovf = nullptr;
   unsigned long long *d_cnt = nullptr;
   int32_t *h_src = nullptr;   // pinned staging
@@ -619,6 +621,8 @@ size_t job_footprint(const GraphRec &gr, int sched, const bc_opts &o, int64_t k)
 void job_free_buffers(JobRec *j) {
   if (j->d_src) cudaFreeAsync(j->d_src, j->st);
   if (j->d_bc) cudaFreeAsync(j->d_bc, j->st);
+  if (j->d_bc2) cudaFreeAsync(j->d_bc2, j->st);
+  j->d_bc2 = nullptr;
   if (j->d_ovf) cudaFreeAsync(j->d_ovf, j->st);
   if (j->d_cnt) cudaFreeAsync(j->d_cnt, j->st);
   j->d_src = nullptr;
@@ -707,10 +711,15 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   BC_TRY(cudaEventCreate(&j->ev1));
   BC_TRY(cudaEventCreateWithFlags(&j->evdone, cudaEventDisableTiming));
 
+  if (j->acc_sum) {
+    BC_TRY(cudaMallocAsync(&j->d_bc2, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
+    BC_TRY(cudaMemsetAsync(j->d_bc2, 0, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
+  }
   KParams p;
   p.g = g;
   p.w = j->ws->w;
   p.bc = j->d_bc;
+  p.bc2 = j->d_bc2;
   p.ovf_flags = j->d_ovf;
   p.job_cnt = j->d_cnt;
   if (ctx->inject_block >= 0 && batch) {
@@ -803,7 +812,13 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   double factor = 1.0;
   if (j->opts.normalize && n > 2) factor /= (double)(n - 1) * (double)(n - 2);
   if (j->opts.scale_sampled && k > 0) factor *= (double)n / (double)k;
-  if (out && n > 0) {
+  if (j->acc_sum) {
+    // estimator job: add this job's sums into the running ones (skipped on a
+    // device error, so a rerun never double counts)
+    BC_TRY(launch_accumulate(j->acc_sum, j->acc_sumsq, j->d_bc, j->d_bc2, n, &j->ws->w.ctl->err,
+                             st));
+    ++j->launches;
+  } else if (out && n > 0) {
     if (j->opts.out_device) {
       BC_TRY(launch_scale(j->d_bc, out, n, factor, st));
     } else {
@@ -891,7 +906,8 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
 }
 
 bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool all,
-                   const bc_opts *opts_in, double *out, const DebugOut *dbg) {
+                   const bc_opts *opts_in, double *out, const DebugOut *dbg,
+                   double *acc_sum = nullptr, double *acc_sumsq = nullptr) {
   bc_opts opts = opts_in ? *opts_in : default_opts();
   if (!opts_valid(opts)) return BC_ERR_ARG;
   JobRec j;
@@ -901,6 +917,8 @@ bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool
   j.all_sources = all;
   if (!all && k) j.src.assign(src, src + k);
   j.st = ctx->stream;
+  j.acc_sum = acc_sum;
+  j.acc_sumsq = acc_sumsq;
   bc_status s = kStatusRetry;
   for (int attempt = 0; attempt < 3 && s == kStatusRetry; ++attempt) {
     s = job_launch(ctx, &j, out, dbg);
@@ -1164,6 +1182,131 @@ bc_status bc_sources(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, con
   bc_status s = check_sources(g, src, k);
   if (s != BC_OK) return s;
   return run_sync(ctx, g, src, k, false, opts, bc_out, nullptr);
+}
+
+namespace {
+
+// Device buffers of the sampled-source estimator: running sums of the
+// per-source terms and of their squares, the estimate and its error.
+struct EstimateBufs {
+  cudaStream_t st = nullptr;
+  double *sum = nullptr, *sumsq = nullptr, *est = nullptr, *err = nullptr;
+  unsigned long long *stat = nullptr;
+  bc_status alloc(int64_t n) {
+    const size_t b = sizeof(double) * (size_t)std::max<int64_t>(n, 1);
+    BC_TRY(cudaMallocAsync(&sum, b, st));
+    BC_TRY(cudaMallocAsync(&sumsq, b, st));
+    BC_TRY(cudaMallocAsync(&est, b, st));
+    BC_TRY(cudaMallocAsync(&err, b, st));
+    BC_TRY(cudaMallocAsync(&stat, sizeof(unsigned long long), st));
+    BC_TRY(cudaMemsetAsync(sum, 0, b, st));
+    BC_TRY(cudaMemsetAsync(sumsq, 0, b, st));
+    return BC_OK;
+  }
+  ~EstimateBufs() {
+    for (double *q : {sum, sumsq, est, err})
+      if (q) cudaFreeAsync(q, st);
+    if (stat) cudaFreeAsync(stat, st);
+    if (st) cudaStreamSynchronize(st);
+  }
+};
+
+// Output scale of the estimate: 1, or 1/((n-1)(n-2)) when normalising.
+double estimate_factor(const bc_opts &o, int64_t n) {
+  return o.normalize && n > 2 ? 1.0 / ((double)(n - 1) * (double)(n - 2)) : 1.0;
+}
+
+bc_status estimate_out(bc_ctx *ctx, EstimateBufs &b, int64_t n, int64_t k, const bc_opts &o,
+                       double *est_out, double *err_out) {
+  cudaStream_t st = ctx->stream;
+  BC_TRY(launch_estimate(b.sum, b.sumsq, n, k, estimate_factor(o, n), b.est, b.err, st));
+  const cudaMemcpyKind kind = o.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (n > 0) {
+    BC_TRY(cudaMemcpyAsync(est_out, b.est, sizeof(double) * (size_t)n, kind, st));
+    BC_TRY(cudaMemcpyAsync(err_out, b.err, sizeof(double) * (size_t)n, kind, st));
+  }
+  BC_TRY(cudaStreamSynchronize(st));
+  return BC_OK;
+}
+
+} // namespace
+
+bc_status bc_sources_estimate(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k,
+                              const bc_opts *opts, double *est_out, double *stderr_out) {
+  if (!ctx || !est_out || !stderr_out) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  GraphRec *g;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    g = find_graph(ctx, h);
+  }
+  if (!g) return BC_ERR_GRAPH;
+  bc_status s = check_sources(g, src, k);
+  if (s != BC_OK) return s;
+  bc_opts o = opts ? *opts : default_opts();
+  if (!opts_valid(o)) return BC_ERR_ARG;
+  o.scale_sampled = 0; // the estimate carries its own n/k
+  const int64_t n = g->dev.n;
+  EstimateBufs b;
+  b.st = ctx->stream;
+  s = b.alloc(n);
+  if (s != BC_OK) return s;
+  if (k > 0) {
+    s = run_sync(ctx, g, src, k, false, &o, nullptr, nullptr, b.sum, b.sumsq);
+    if (s != BC_OK && s != BC_ERR_SIGMA_OVERFLOW) return s;
+  }
+  const bc_status so = estimate_out(ctx, b, n, k, o, est_out, stderr_out);
+  return so != BC_OK ? so : s;
+}
+
+bc_status bc_sources_adaptive(bc_ctx *ctx, bc_graph h, const int32_t *order, int32_t max_k,
+                              int32_t round, double rel_err, double min_est, const bc_opts *opts,
+                              double *est_out, double *stderr_out, int32_t *k_used) {
+  if (!ctx || !est_out || !stderr_out || !k_used || max_k < 1 || round < 1 || !(rel_err > 0.0))
+    return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  GraphRec *g;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    g = find_graph(ctx, h);
+  }
+  if (!g) return BC_ERR_GRAPH;
+  bc_status s = check_sources(g, order, max_k);
+  if (s != BC_OK) return s;
+  bc_opts o = opts ? *opts : default_opts();
+  if (!opts_valid(o)) return BC_ERR_ARG;
+  o.scale_sampled = 0;
+  const int64_t n = g->dev.n;
+  const double factor = estimate_factor(o, n);
+  EstimateBufs b;
+  b.st = ctx->stream;
+  s = b.alloc(n);
+  if (s != BC_OK) return s;
+  cudaStream_t st = ctx->stream;
+  int64_t done = 0;
+  bc_status worst = BC_OK;
+  while (done < max_k) {
+    const int64_t r = std::min<int64_t>(round, max_k - done);
+    s = run_sync(ctx, g, order + done, r, false, &o, nullptr, nullptr, b.sum, b.sumsq);
+    if (s != BC_OK && s != BC_ERR_SIGMA_OVERFLOW) return s;
+    if (s != BC_OK) worst = s;
+    done += r;
+    if (done < 2) continue;
+    // stop once every vertex whose estimate reaches min_est has a standard
+    // error of at most rel_err times its estimate
+    unsigned long long bits = 0;
+    BC_TRY(launch_estimate(b.sum, b.sumsq, n, done, factor, b.est, b.err, st));
+    BC_TRY(cudaMemsetAsync(b.stat, 0, sizeof(unsigned long long), st));
+    BC_TRY(launch_max_rel_err(b.est, b.err, n, min_est, b.stat, st));
+    BC_TRY(cudaMemcpyAsync(&bits, b.stat, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    BC_TRY(cudaStreamSynchronize(st));
+    double worst_rel;
+    std::memcpy(&worst_rel, &bits, sizeof(double));
+    if (worst_rel <= rel_err) break;
+  }
+  *k_used = (int32_t)done;
+  const bc_status so = estimate_out(ctx, b, n, done, o, est_out, stderr_out);
+  return so != BC_OK ? so : worst;
 }
 
 bc_status bc_submit(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, const bc_opts *opts,

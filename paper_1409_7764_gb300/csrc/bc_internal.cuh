@@ -120,6 +120,7 @@ struct KParams {
   int32_t k = 0;
   int64_t src_base = 0;         // position of src[0] in the job's source list
   double *bc = nullptr;         // [n] accumulator (float64)
+  double *bc2 = nullptr;        // [n] optional accumulator of squared per-source terms
   int8_t *ovf_flags = nullptr;  // [job sources] 1 = count reached 2^64
   unsigned long long *job_cnt = nullptr; // [CNT_N]
   int32_t *dbg_d = nullptr;     // [k][n] or null
@@ -156,6 +157,12 @@ cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st)
 cudaError_t launch_dense(const KParams &p, bool fp64, int grid, cudaStream_t st);
 int max_grid_dense(bool fp64, int device);
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
+cudaError_t launch_estimate(const double *sum, const double *sumsq, int64_t n, int64_t k,
+                            double factor, double *est, double *err, cudaStream_t st);
+cudaError_t launch_max_rel_err(const double *est, const double *err, int64_t n, double min_est,
+                               unsigned long long *out, cudaStream_t st);
+cudaError_t launch_accumulate(double *acc, double *acc2, const double *add, const double *add2,
+                              int64_t n, const int *err, cudaStream_t st);
 int max_grid_batch(bool fp64, int device, int words = 1);
 int max_grid_plain(bool fp64, int device);
 

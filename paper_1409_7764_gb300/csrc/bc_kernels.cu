@@ -269,7 +269,7 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
                                              double bcv, uint64_t *Wn, int lane) {
   uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
   DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * (kK * W);
-  double contrib = 0.0;
+  double contrib = 0.0, contrib2 = 0.0;
   const int n = p.g.n;
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i)
@@ -279,7 +279,10 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
       const DT dl = sf * a[i];
       crow[j] = (DT(1) + dl) / sf;
       srow[j] = 0;
-      if (__ldg(p.src + j) != v) contrib += (double)dl;
+      if (__ldg(p.src + j) != v) {
+        contrib += (double)dl;
+        if (p.bc2) contrib2 += (double)dl * (double)dl;
+      }
       if (p.dbg_d) {
         const size_t o = (size_t)j * n + v;
         p.dbg_d[o] = lvl;
@@ -289,6 +292,12 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
     }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(kFull, contrib, off);
+  if (p.bc2) {
+    // squared per-source terms for the sampled-source estimator's variance
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) contrib2 += __shfl_down_sync(kFull, contrib2, off);
+    if (lane == 0 && contrib2 != 0.0) p.bc2[v] = ldcg(p.bc2 + v) + contrib2;
+  }
   if (lane == 0) {
     if (contrib != 0.0) p.bc[v] = bcv + contrib;
     zero_mask<W>(p.w.vis, v);
@@ -1166,6 +1175,64 @@ __global__ void scale_kernel(const double *__restrict__ in, double *__restrict__
     out[i] = in[i] * factor;
 }
 
+// Sampled-source estimate from the sums of the per-source terms and of their
+// squares over k sources: est = f*n*m, err = f*n*sqrt((1 - k/n) S2 / k) with
+// m the mean, S2 = (sum of squares - k m^2)/(k - 1) the sample variance
+// (clamped at 0 against rounding) and f the output scale; err is NaN for
+// k < 2, and the finite-population factor is clamped at 0 for k > n.
+__global__ void estimate_kernel(const double *__restrict__ sum, const double *__restrict__ sumsq,
+                                int64_t n, int64_t k, double factor, double *__restrict__ est,
+                                double *__restrict__ err) {
+  const double nn = (double)n, kk = (double)k;
+  const double fpc = k >= n ? 0.0 : 1.0 - kk / nn;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const double m = k > 0 ? sum[v] / kk : 0.0;
+    est[v] = factor * nn * m;
+    if (k < 2) {
+      err[v] = nan("");
+    } else {
+      double s2 = (sumsq[v] - kk * m * m) / (kk - 1.0);
+      if (s2 < 0.0) s2 = 0.0;
+      err[v] = factor * nn * sqrt(fpc * s2 / kk);
+    }
+  }
+}
+
+// Largest err[v]/est[v] over vertices with est[v] >= min_est (> 0), as the
+// bit pattern of a non-negative double (which orders like the value).
+__global__ void max_rel_err_kernel(const double *__restrict__ est, const double *__restrict__ err,
+                                   int64_t n, double min_est, unsigned long long *out) {
+  double r = 0.0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const double e = est[v];
+    if (e >= min_est && e > 0.0) {
+      const double q = err[v] / e;
+      r = q > r ? q : r;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_down_sync(kFull, r, off);
+    r = o > r ? o : r;
+  }
+  if ((threadIdx.x & 31) == 0 && r > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(r));
+}
+
+// Adds a finished job's per-vertex sums into running accumulators, unless
+// the job recorded a device error (then its sums may be partial).
+__global__ void accumulate_kernel(double *__restrict__ acc, double *__restrict__ acc2,
+                                  const double *__restrict__ add, const double *__restrict__ add2,
+                                  int64_t n, const int *err) {
+  if (*reinterpret_cast<const volatile int *>(err) != 0) return;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    acc[v] += add[v];
+    acc2[v] += add2[v];
+  }
+}
+
 template <typename K> int max_grid_for(K kernel, int device) {
   int per_sm = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess)
@@ -1211,6 +1278,33 @@ cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor
   int grid = (int)((n + 255) / 256);
   if (grid > 4096) grid = 4096;
   scale_kernel<<<grid, 256, 0, st>>>(in, out, n, factor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(double *acc, double *acc2, const double *add, const double *add2,
+                              int64_t n, const int *err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  accumulate_kernel<<<grid, 256, 0, st>>>(acc, acc2, add, add2, n, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(const double *sum, const double *sumsq, int64_t n, int64_t k,
+                            double factor, double *est, double *err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  estimate_kernel<<<grid, 256, 0, st>>>(sum, sumsq, n, k, factor, est, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_rel_err(const double *est, const double *err, int64_t n, double min_est,
+                               unsigned long long *out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 1024) grid = 1024;
+  max_rel_err_kernel<<<grid, 256, 0, st>>>(est, err, n, min_est, out);
   return cudaGetLastError();
 }
 
