@@ -469,7 +469,8 @@ def run_many(args):
     hs = [ctx.create_graph(g.row_ptr, g.col_idx) for g in graphs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order)
+        ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order,
+                       batch_k=max(args.batch_k, 0))
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -479,7 +480,8 @@ def run_many(args):
         flush.fill_(1)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order)
+        ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order,
+                       batch_k=max(args.batch_k, 0))
         e.record(stream)
         torch.cuda.synchronize()
         ms.append(s.elapsed_time(e))
@@ -495,7 +497,7 @@ def run_many(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = [ctx.create_graph(g.row_ptr, g.col_idx) for g in graphs]
-        ctx.exact_many(h2, delta_fp64=fp64)
+        ctx.exact_many(h2, delta_fp64=fp64, batch_k=max(args.batch_k, 0))
         for h in h2:
             ctx.destroy_graph(h)
         e2e.append(time.perf_counter() - t0)

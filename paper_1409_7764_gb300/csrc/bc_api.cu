@@ -133,7 +133,6 @@ int32_t dense_levels(int32_t n) { return n <= (1 << 22) ? kDenseLevels : kDenseL
 // still gives the job kWideMinBatches batches; wider batches share each
 // (vertex, level) entry and edge scan among more sources.  Debug exports and
 // graphs that overran a wide batch's queue use 64.
-constexpr int kWideMinBatches = 8;
 struct BatchShape {
   int kb;
   int words;
@@ -142,10 +141,8 @@ BatchShape batch_shape(const bc_opts &o, int kind, int64_t k, bool narrow, bool 
   if (kind == WS_PLAIN) return {1, 1};
   if (narrow && kind == WS_QUEUE) return {o.batch_k > 0 && o.batch_k < kK ? o.batch_k : kK, 1};
   if (o.batch_k > 0) return {o.batch_k, o.batch_k <= kK ? 1 : o.batch_k <= 2 * kK ? 2 : 4};
-  if (kind == WS_QUEUE && !narrow && !dbg)
-    for (int w = kMaxWords; w > 1; w /= 2)
-      if (k >= (int64_t)kWideMinBatches * kK * w) return {kK * w, w};
-  return {kK, 1};
+  const int w = kind == WS_QUEUE && !narrow && !dbg ? auto_words(k, kMaxWords) : 1;
+  return {kK * w, w};
 }
 
 int word_index(int words) { return words == 1 ? 0 : words == 2 ? 1 : 2; }
@@ -1507,7 +1504,12 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
   if (!small.empty()) {
     // one workspace per thread block, sized for the largest small graph
     WsRec proto;
+    // widest masks any of the graphs takes (each picks its own in the kernel)
+    const int max_words = o.batch_k == 0 ? kMaxWords : 1;
+    int ws_words = 1;
+    for (int32_t i : small) ws_words = std::max(ws_words, auto_words(gs[(size_t)i]->dev.n, max_words));
     proto.kind = WS_QUEUE;
+    proto.words = ws_words;
     proto.batch = true;
     proto.n = max_n;
     proto.cap = (int64_t)max_n * kb;
@@ -1559,6 +1561,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     mp.out = d_out;
     mp.next = d_next;
     mp.kb = kb;
+    mp.max_words = ws_words;
     mp.grouped = o.source_order == 0 ? 1 : 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -1578,7 +1581,11 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     for (int c = 0; c < grid && status == BC_OK; ++c)
       if (errs[(size_t)c]) status = BC_ERR_INTERNAL;
     total.batches += 0;
-    for (int32_t i : small) total.batches += (gs[(size_t)i]->dev.n + kb - 1) / kb;
+    for (int32_t i : small) {
+      const int64_t gn = gs[(size_t)i]->dev.n;
+      const int64_t gkb = ws_words > 1 ? kK * auto_words(gn, ws_words) : kb;
+      total.batches += (gn + gkb - 1) / gkb;
+    }
     total.kernel_launches += 1;
   }
   // larger graphs, one grid-wide job each, straight into the device result

@@ -13,6 +13,17 @@ constexpr int kBlock = 256;                    // threads per CTA of the persist
 constexpr int kWarpsPerBlock = kBlock / kWarp; // 8
 constexpr int kK = 64;                         // sources per mask word (one bit each in a u64)
 constexpr int kMaxWords = 4;                   // queue kernel: up to 4 words = 256 sources per batch
+constexpr int kWideMinBatches = 8;             // automatic width: batches a job must still have
+
+// Mask words of a job of k sources when the library picks the width: the
+// widest batch (64 sources per word, up to max_words words) that still gives
+// the job kWideMinBatches batches; wider batches share each (vertex, level)
+// entry and edge scan among more sources.
+__host__ __device__ constexpr int auto_words(int64_t k, int max_words) {
+  return max_words >= 4 && k >= (int64_t)kWideMinBatches * kK * 4   ? 4
+         : max_words >= 2 && k >= (int64_t)kWideMinBatches * kK * 2 ? 2
+                                                                    : 1;
+}
 // Edges per work chunk of a high-degree vertex: candidates the per-graph
 // tuner picks from (the first is the default before tuning).
 constexpr int kChunkCandidates[3] = {256, 128, 512};
@@ -144,9 +155,10 @@ struct ManyParams {
   const Work *works = nullptr;    // [grid] one workspace per thread block
   const int32_t *iota = nullptr;  // [max n] 0, 1, 2, ...: the sources of exact BC in given order
   int32_t grouped = 1;            // 1: batches take the sources in GraphDev::order
+  int32_t max_words = 1;          // widest source masks a graph may use (auto_words)
   double *out = nullptr;          // [sum of n]
   unsigned *next = nullptr;       // graph counter
-  int32_t kb = kK;                // sources per batch
+  int32_t kb = kK;                // sources per batch when max_words == 1
 };
 
 // Host launchers (bc_kernels.cu).  Return a cudaError_t.

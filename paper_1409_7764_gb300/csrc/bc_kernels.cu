@@ -828,10 +828,30 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
   flush_counters(p.job_cnt, to_counters(cnt, dag, lane), lane);
 }
 
+// Clears what a batch stopped in its forward sweep may leave behind in a
+// block's workspace and must be clean at a batch's start: visited and level
+// masks, first-toucher claims, chunk tickets and the error code.  (Path
+// counts and coefficients are only read where this batch wrote them.)
+__device__ void block_reset_workspace(const Work &w, int n) {
+  const size_t words = (size_t)n * (size_t)w.words;
+  for (size_t i = threadIdx.x; i < words; i += blockDim.x) w.vis[i] = 0;
+  for (size_t i = threadIdx.x; i < 4 * words; i += blockDim.x) w.fr[i] = 0;
+  if (w.claim)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) w.claim[i] = 0;
+  for (int64_t i = threadIdx.x; i < w.hcap; i += blockDim.x) w.harrive[i] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->err = KERR_NONE;
+  __syncthreads();
+}
+
 // Exact BC of many small graphs in one launch: each thread block takes the
 // next graph from a shared counter (largest work first) and runs all of that
 // graph's source batches itself, with CTA barriers between levels, so every
-// graph's BC is written by one block without atomics.
+// graph's BC is written by one block without atomics.  Each graph gets its
+// own batch width (auto_words of its vertex count, up to mp.max_words); a
+// wide batch that overruns its queue (sized for 64 depths per vertex) is
+// stopped in its forward sweep, before any BC is written, and the graph's
+// remaining sources continue 64 per batch.
 template <typename DT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const ManyParams mp) {
   __shared__ int s_stage[kWarpsPerBlock][kStage];
@@ -853,13 +873,27 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
     p.g = mp.graphs[gi];
     const int64_t off = __ldg(mp.out_off + gi);
     p.bc = mp.out + off;
-    for (int b0 = 0; b0 < p.g.n; b0 += mp.kb) {
+    int words = mp.max_words > 1 ? auto_words(p.g.n, mp.max_words) : 1;
+    for (int b0 = 0; b0 < p.g.n;) {
+      const int kb = words > 1 ? kK * words : mp.kb;
       p.src = (mp.grouped && p.g.order ? p.g.order : mp.iota) + b0;
-      p.k = p.g.n - b0 < mp.kb ? p.g.n - b0 : mp.kb;
+      p.k = p.g.n - b0 < kb ? p.g.n - b0 : kb;
       p.src_base = off + b0;
-      batch_body<DT, 1>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+      if (words == 4)
+        batch_body<DT, 4>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+      else if (words == 2)
+        batch_body<DT, 2>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+      else
+        batch_body<DT, 1>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       __syncthreads();
-      if (read_err(p.w.ctl)) break;
+      const int e = read_err(p.w.ctl);
+      if ((e == KERR_QUEUE || e == KERR_HEAVY) && words > 1) {
+        block_reset_workspace(p.w, p.g.n);
+        words = 1; // redo these sources 64 per batch
+        continue;
+      }
+      if (e) break;
+      b0 += p.k;
     }
   }
   __syncwarp();

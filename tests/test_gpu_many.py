@@ -59,3 +59,24 @@ def test_many_graphs_normalised_and_batch_width(ctx):
         close(got, oracle.normalise(ref, g.n), 1e-12)
     for h in handles:
         ctx.destroy_graph(h)
+
+
+def test_many_graphs_per_graph_width_and_overrun(ctx):
+    """Graphs of 2048+ vertices run 256 sources per batch, 1024+ run 128,
+    smaller ones 64; a long path overruns a wide batch's queue in its forward
+    sweep and continues 64 sources per batch.  All match the oracle."""
+    gs = [bcgen.rmat(11, 8, seed=1), bcgen.rmat(10, 12, seed=2), bcgen.path(8000),
+          bcgen.rmat(7, 6, seed=3), bcgen.ba_directed(2500, 4, 5, 7)]
+    handles = [ctx.create_graph(g.row_ptr, g.col_idx) for g in gs]
+    for fp64, tol in ((True, 1e-12), (False, 1e-4)):
+        outs = ctx.exact_many(handles, delta_fp64=fp64)
+        for g, got in zip(gs, outs):
+            ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+            close(got, ref, tol)
+    # an explicit width keeps every graph at 64 sources per batch
+    outs = ctx.exact_many(handles, delta_fp64=True, batch_k=64)
+    for g, got in zip(gs, outs):
+        ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+        close(got, ref, 1e-12)
+    for h in handles:
+        ctx.destroy_graph(h)
