@@ -263,7 +263,7 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
 // lane's successor sums a, its path counts sg and (lane 0) the current BC
 // value bcv, all loaded by the caller ahead of the successor scan:
 // dependencies, coefficients, BC, resets.
-template <typename DT, int W>
+template <typename DT, int W, bool SQ>
 __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, const Mask<W> &F,
                                              const DT (&a)[2 * W], const uint64_t (&sg)[2 * W],
                                              double bcv, uint64_t *Wn, int lane) {
@@ -281,7 +281,7 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
       srow[j] = 0;
       if (__ldg(p.src + j) != v) {
         contrib += (double)dl;
-        if (p.bc2) contrib2 += (double)dl * (double)dl;
+        if (SQ) contrib2 += (double)dl * (double)dl;
       }
       if (p.dbg_d) {
         const size_t o = (size_t)j * n + v;
@@ -292,7 +292,7 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
     }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(kFull, contrib, off);
-  if (p.bc2) {
+  if (SQ) {
     // squared per-source terms for the sampled-source estimator's variance
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) contrib2 += __shfl_down_sync(kFull, contrib2, off);
@@ -488,7 +488,7 @@ template <int W> __device__ __forceinline__ void unit_counts(uint64_t (&s)[2 * W
 // One batch of up to 64*W sources through both sweeps, in the given scope.
 // Returns early (leaving the workspace dirty) when the job is in an error
 // state.  Warp counters accumulate into cnt (shared, lane 0) and dag (lane).
-template <typename DT, int W, typename Scope>
+template <typename DT, int W, bool SQ, typename Scope>
 __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int *stage,
                                            WarpCounters &cnt, unsigned long long &dag) {
   const int lane = threadIdx.x & 31;
@@ -764,7 +764,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
 #pragma unroll
             for (int i = 0; i < 2 * W; ++i) t[i] += ldcg(pp + (size_t)cc * kRow + 32 * i + lane);
           const EntryOwn<W> own(p, v, F, lane);
-          batch_finish<DT, W>(p, l, v, F, t, own.sg, own.bcv, Wn, lane);
+          batch_finish<DT, W, SQ>(p, l, v, F, t, own.sg, own.bcv, Wn, lane);
           if (lane == 0) p.w.harrive[h] = 0;
         }
       }
@@ -783,12 +783,12 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
             // own counts loaded ahead of the successor scan (overlapping it)
             const EntryOwn<W> own(p, v, F, lane);
             if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
-            batch_finish<DT, W>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+            batch_finish<DT, W, SQ>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           } else {
             // widest masks: loaded after it, which keeps 4W registers free
             if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
             const EntryOwn<W> own(p, v, F, lane);
-            batch_finish<DT, W>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+            batch_finish<DT, W, SQ>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           }
           if (!deepest && lane == 0) cnt.out_e += (uint64_t)(re - rs);
         }
@@ -815,7 +815,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
   }
 }
 
-template <typename DT, int W>
+template <typename DT, int W, bool SQ>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
   __shared__ int s_stage[kWarpsPerBlock][kStage]; // warp-private new-vertex stage
   __shared__ WarpCounters s_cnt[kWarpsPerBlock];
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
   WarpCounters &cnt = s_cnt[threadIdx.x >> 5];
   zero_counters(cnt, lane);
   unsigned long long dag = 0;
-  batch_body<DT, W>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+  batch_body<DT, W, SQ>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt, dag);
   __syncwarp();
   flush_counters(p.job_cnt, to_counters(cnt, dag, lane), lane);
 }
@@ -880,11 +880,11 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
       p.k = p.g.n - b0 < kb ? p.g.n - b0 : kb;
       p.src_base = off + b0;
       if (words == 4)
-        batch_body<DT, 4>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+        batch_body<DT, 4, false>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       else if (words == 2)
-        batch_body<DT, 2>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+        batch_body<DT, 2, false>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       else
-        batch_body<DT, 1>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+        batch_body<DT, 1, false>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       __syncthreads();
       const int e = read_err(p.w.ctl);
       if ((e == KERR_QUEUE || e == KERR_HEAVY) && words > 1) {
@@ -1283,22 +1283,30 @@ template <typename K> cudaError_t coop_launch(K kernel, const KParams &p, int gr
                                      dim3(kBlock), args, 0, st);
 }
 
-} // namespace
-
-cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words) {
+template <bool SQ>
+cudaError_t launch_batch_sq(const KParams &p, bool fp64, int grid, cudaStream_t st, int words) {
   switch (words) {
     case 1:
-      return fp64 ? coop_launch(batch_kernel<double, 1>, p, grid, st)
-                  : coop_launch(batch_kernel<float, 1>, p, grid, st);
+      return fp64 ? coop_launch(batch_kernel<double, 1, SQ>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 1, SQ>, p, grid, st);
     case 2:
-      return fp64 ? coop_launch(batch_kernel<double, 2>, p, grid, st)
-                  : coop_launch(batch_kernel<float, 2>, p, grid, st);
+      return fp64 ? coop_launch(batch_kernel<double, 2, SQ>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 2, SQ>, p, grid, st);
     case 4:
-      return fp64 ? coop_launch(batch_kernel<double, 4>, p, grid, st)
-                  : coop_launch(batch_kernel<float, 4>, p, grid, st);
+      return fp64 ? coop_launch(batch_kernel<double, 4, SQ>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 4, SQ>, p, grid, st);
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+} // namespace
+
+// The squared-term accumulation of the estimator is a separate
+// instantiation, so plain BC jobs carry none of its code.
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words) {
+  return p.bc2 ? launch_batch_sq<true>(p, fp64, grid, st, words)
+               : launch_batch_sq<false>(p, fp64, grid, st, words);
 }
 
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st) {
@@ -1356,14 +1364,14 @@ int max_grid_many(bool fp64, int device) {
 int max_grid_batch(bool fp64, int device, int words) {
   switch (words) {
     case 1:
-      return fp64 ? max_grid_for(batch_kernel<double, 1>, device)
-                  : max_grid_for(batch_kernel<float, 1>, device);
+      return fp64 ? max_grid_for(batch_kernel<double, 1, false>, device)
+                  : max_grid_for(batch_kernel<float, 1, false>, device);
     case 2:
-      return fp64 ? max_grid_for(batch_kernel<double, 2>, device)
-                  : max_grid_for(batch_kernel<float, 2>, device);
+      return fp64 ? max_grid_for(batch_kernel<double, 2, false>, device)
+                  : max_grid_for(batch_kernel<float, 2, false>, device);
     case 4:
-      return fp64 ? max_grid_for(batch_kernel<double, 4>, device)
-                  : max_grid_for(batch_kernel<float, 4>, device);
+      return fp64 ? max_grid_for(batch_kernel<double, 4, false>, device)
+                  : max_grid_for(batch_kernel<float, 4, false>, device);
     default:
       return 0;
   }
