@@ -77,7 +77,7 @@ typedef struct {
   int32_t delta_fp64;    /* 0: dependencies in FP32 (fast path); 1: FP64 */
   int32_t batch_k;       /* sources per batch of the batched schedules: 0 = the library picks
                             64, 128 or 256 (the widest that still gives the job eight batches;
-                            64 for debug exports and bc_exact_many); else 1..256 for
+                            64 for debug exports; per graph in bc_exact_many); else 1..256 for
                             BC_SCHED_AUTO / BATCH / BATCH_QUEUE, 1..64 for BATCH_DENSE and
                             bc_exact_many.  Bit j of a batch's source masks is its j-th
                             source; masks are 1, 2 or 4 64-bit words.  Wider batches size
@@ -228,9 +228,11 @@ bc_status bc_debug_sources(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t 
 
 /* Exact BC of `count` resident graphs.  Graphs of up to 8192 vertices run in
  * ONE persistent launch: each thread block takes the next graph (largest
- * n*(m+n) first), runs all of its source batches (opts.batch_k sources each,
- * default 64) with block-level barriers between BFS levels and writes that
- * graph's BC itself; larger graphs run one after another through the
+ * n*(m+n) first), runs all of its source batches (opts.batch_k sources each;
+ * with batch_k = 0 each graph gets 64, 128 or 256 by the automatic rule on
+ * its vertex count, and a wide batch that overruns its frontier queue
+ * continues 64 per batch) with block-level barriers between BFS levels and
+ * writes that graph's BC itself; larger graphs run one after another through the
  * grid-wide batched kernel.  bc_out receives the vectors back to back (graph
  * i at offset sum_{j<i} n_j), host or device memory per opts.out_device;
  * normalize applies per graph, scale_sampled has no effect (all sources).
