@@ -39,7 +39,7 @@ HBM_FALLBACK_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
 WORKLOADS = {
-    # R-MAT scale 16, edge factor 16, all 65,536 sources in batches of 64
+    # R-MAT scale 16, edge factor 16, all 65,536 sources (the library picks the batch width)
     "rmat16-exact": dict(kind="rmat", scale=16, ef=16, seed=1, sources="all", batch_k=0,
                          schedule="batch"),
     # R-MAT scale 20, edge factor 16, 4096 / 1024 seeded uniform sources

@@ -65,7 +65,7 @@ def test_many_graphs_per_graph_width_and_overrun(ctx):
     """Graphs of 2048+ vertices run 256 sources per batch, 1024+ run 128,
     smaller ones 64; a long path overruns a wide batch's queue in its forward
     sweep and continues 64 sources per batch.  All match the oracle."""
-    gs = [bcgen.rmat(11, 8, seed=1), bcgen.rmat(10, 12, seed=2), bcgen.path(8000),
+    gs = [bcgen.rmat(11, 8, seed=1), bcgen.rmat(10, 12, seed=2), bcgen.path(2100),
           bcgen.rmat(7, 6, seed=3), bcgen.ba_directed(2500, 4, 5, 7)]
     handles = [ctx.create_graph(g.row_ptr, g.col_idx) for g in gs]
     for fp64, tol in ((True, 1e-12), (False, 1e-4)):
