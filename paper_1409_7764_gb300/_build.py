@@ -1,6 +1,6 @@
 """Builds the CUDA library libbc_gb300.so in-tree for sm_103a (GB300).
 
-Two translation units are compiled in parallel with nvcc, then linked into a
+The translation units are compiled in parallel with nvcc, then linked into a
 shared object next to this file.  Nothing here runs at import time unless the
 library is missing or older than its sources.
 """
@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbc_gb300.so")
-SOURCES = ["bc_kernels.cu", "bc_dense.cu", "bc_api.cu", "bc_noalloc.cu"]
+SOURCES = ["bc_kernels.cu", "bc_dense.cu", "bc_graph.cu", "bc_api.cu", "bc_noalloc.cu"]
 HEADERS = ["bc_internal.cuh", "bc_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

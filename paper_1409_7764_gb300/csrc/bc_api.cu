@@ -82,9 +82,35 @@ struct GraphRec {
   // a batch wider than 64 sources overran its frontier queue or heavy list
   // (sized for 64 distinct depths per vertex): later jobs use 64 sources
   std::atomic<bool> narrow{false};
-  // batch composition: every vertex in grouping order, and its position there
-  std::vector<int32_t> order, pos;
+  // batch composition (see batch_key_less): host copies of the out-CSR
+  // offsets and of the two-hop walk counts; every vertex in batch order, made
+  // on first need (kept on the host and in d_order)
+  std::vector<int32_t> row_ptr;
+  std::vector<int64_t> two;
+  std::vector<int32_t> order;
+  int32_t *d_order = nullptr;
+  std::mutex order_mu;
 };
+
+// Batch composition order of the vertices as sources.  A batch advances
+// the union of its sources' frontiers, so its cost grows with the (vertex,
+// level) entries and edge scans of that union; sources whose traversals
+// reach the same vertices at the same depths share them.  The key: sources
+// without out-edges (a traversal of one vertex) last, the others by the
+// number of two-hop walks leaving them (a proxy for how fast the traversal
+// fans out into the graph's core), descending; ties by out-degree, then
+// vertex id.
+inline bool batch_key_less(const GraphRec &g, int32_t a, int32_t b) {
+  const int32_t da = g.row_ptr[(size_t)a + 1] - g.row_ptr[(size_t)a];
+  const int32_t db = g.row_ptr[(size_t)b + 1] - g.row_ptr[(size_t)b];
+  if ((da == 0) != (db == 0)) return db == 0;
+  if (g.two[(size_t)a] != g.two[(size_t)b]) return g.two[(size_t)a] > g.two[(size_t)b];
+  if (da != db) return da > db;
+  return a < b;
+}
+
+// Graphs up to this many vertices get their batch order at creation.
+constexpr int32_t kEagerOrderN = 1 << 16;
 
 // Launch configurations the tuner compares: (chunk variant, items per fetch).
 struct TuneCandidate {
@@ -369,6 +395,21 @@ int pick_grid(const bc_ctx *ctx, const GraphDev &g, int kind, bool fp64, int wor
 
 // ---- graphs -----------------------------------------------------------------
 
+// Makes the graph's batch order (host and device copies) if it has none yet.
+bc_status ensure_order(GraphRec *g, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g->order_mu);
+  const int32_t n = g->dev.n;
+  if (!g->order.empty() || n == 0) return BC_OK;
+  std::vector<int32_t> ord((size_t)n);
+  for (int32_t v = 0; v < n; ++v) ord[(size_t)v] = v;
+  std::sort(ord.begin(), ord.end(), [g](int32_t a, int32_t b) { return batch_key_less(*g, a, b); });
+  BC_TRY(cudaMemcpyAsync(g->d_order, ord.data(), sizeof(int32_t) * (size_t)n,
+                         cudaMemcpyHostToDevice, st));
+  BC_TRY(cudaStreamSynchronize(st));
+  g->order = std::move(ord);
+  return BC_OK;
+}
+
 bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
                       int64_t m, std::unique_ptr<GraphRec> &out, int64_t *m_eff) {
   if (n < 0 || m < 0 || m >= ((int64_t)1 << 31)) return BC_ERR_GRAPH;
@@ -376,24 +417,74 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != m) return BC_ERR_GRAPH;
   for (int32_t v = 0; v < n; ++v)
     if (row_ptr[v + 1] < row_ptr[v]) return BC_ERR_GRAPH;
-  for (int64_t e = 0; e < m; ++e)
-    if (col_idx[e] < 0 || col_idx[e] >= n) return BC_ERR_GRAPH;
-
-  // canonical out-CSR: rows sorted, unique, no self-loop
-  std::vector<int32_t> rp((size_t)n + 1), ci;
-  bool canonical = true;
-  for (int32_t v = 0; v < n && canonical; ++v)
-    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
-      if (col_idx[e] == v || (e > row_ptr[v] && col_idx[e] <= col_idx[e - 1])) {
-        canonical = false;
-        break;
-      }
-  if (canonical) {
-    std::memcpy(rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1));
-    ci.assign(col_idx, col_idx + m);
-  } else {
-    ci.reserve((size_t)m);
-    rp[0] = 0;
+  cudaStream_t st = ctx->stream;
+  // The graph's device block, laid out for `me` canonical edges.
+  struct Block {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    int32_t *rp = nullptr, *ci = nullptr, *ip = nullptr, *ii = nullptr, *nc = nullptr,
+            *ord = nullptr;
+  };
+  auto carve = [n](Block &b, int64_t me, char *base) {
+    Carver c;
+    c.base = base;
+    b.rp = c.take<int32_t>((size_t)n + 1);
+    b.ci = c.take<int32_t>((size_t)me);
+    b.ip = c.take<int32_t>((size_t)n + 1);
+    b.ii = c.take<int32_t>((size_t)me);
+    b.nc = c.take<int32_t>((size_t)n * kChunkVariants);
+    b.ord = c.take<int32_t>((size_t)n);
+    b.bytes = align_up(c.off, 256);
+  };
+  auto alloc_upload = [&](Block &b, const int32_t *rp, const int32_t *ci, int64_t me) -> bc_status {
+    carve(b, me, nullptr);
+    if (ctx->used + b.bytes > ctx->budget) return BC_ERR_ADMISSION;
+    BC_TRY(cudaMalloc(&b.mem, b.bytes));
+    carve(b, me, static_cast<char *>(b.mem));
+    cudaError_t r = cudaMemcpyAsync(b.rp, rp, sizeof(int32_t) * ((size_t)n + 1),
+                                    cudaMemcpyHostToDevice, st);
+    if (r == cudaSuccess && me)
+      r = cudaMemcpyAsync(b.ci, ci, sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
+    if (r != cudaSuccess) {
+      cudaFree(b.mem);
+      b.mem = nullptr;
+      return cuda_status(r);
+    }
+    return BC_OK;
+  };
+  // upload as given and check on the device: ids in range, rows canonical
+  // (sorted, no duplicates, no self-loops)
+  Block blk;
+  bc_status bs = alloc_upload(blk, row_ptr, col_idx, m);
+  if (bs != BC_OK) return bs;
+  int flags_h[2] = {0, 0};
+  {
+    int *d_flags = nullptr;
+    cudaError_t r = cudaMallocAsync(&d_flags, sizeof(flags_h), st);
+    if (r == cudaSuccess) r = cudaMemsetAsync(d_flags, 0, sizeof(flags_h), st);
+    if (r == cudaSuccess) r = launch_check_csr(blk.rp, blk.ci, n, d_flags, st);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(flags_h, d_flags, sizeof(flags_h), cudaMemcpyDeviceToHost, st);
+    if (d_flags) cudaFreeAsync(d_flags, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    if (r != cudaSuccess) {
+      cudaFree(blk.mem);
+      return cuda_status(r);
+    }
+  }
+  if (flags_h[0]) {
+    cudaFree(blk.mem);
+    return BC_ERR_GRAPH;
+  }
+  // canonical out-CSR: the caller's arrays as they are, else sorted,
+  // de-duplicated rows without self-loops (made on the host, uploaded again)
+  std::vector<int32_t> crp, cci;
+  const int32_t *rp = row_ptr, *ci = col_idx;
+  if (flags_h[1]) {
+    cudaFree(blk.mem);
+    crp.resize((size_t)n + 1);
+    cci.reserve((size_t)m);
+    crp[0] = 0;
     std::vector<int32_t> row;
     for (int32_t v = 0; v < n; ++v) {
       row.assign(col_idx + row_ptr[v], col_idx + row_ptr[v + 1]);
@@ -401,105 +492,116 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
       int32_t prev = -1;
       for (int32_t x : row)
         if (x != v && x != prev) {
-          ci.push_back(x);
+          cci.push_back(x);
           prev = x;
         }
-      rp[(size_t)v + 1] = (int32_t)ci.size();
+      crp[(size_t)v + 1] = (int32_t)cci.size();
     }
+    rp = crp.data();
+    ci = cci.data();
+    blk = Block();
+    bs = alloc_upload(blk, rp, ci, (int64_t)crp[n]);
+    if (bs != BC_OK) return bs;
   }
-  const int64_t me = (int64_t)ci.size();
-  // in-CSR by counting sort over destinations (sources stay ascending)
-  std::vector<int32_t> ip((size_t)n + 1, 0), ii((size_t)std::max<int64_t>(me, 1));
-  for (int64_t e = 0; e < me; ++e) ip[(size_t)ci[e] + 1]++;
-  for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
-  {
-    std::vector<int32_t> fill(ip.begin(), ip.end() - 1);
-    for (int32_t v = 0; v < n; ++v)
-      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) ii[(size_t)fill[ci[e]]++] = v;
-  }
-  std::vector<std::vector<int32_t>> nchv(kChunkVariants,
-                                         std::vector<int32_t>((size_t)std::max<int32_t>(n, 1), 0));
-  int64_t hvv[kChunkVariants] = {}, hcv[kChunkVariants] = {};
-  for (int c = 0; c < kChunkVariants; ++c) {
-    const int64_t ch = kChunkCandidates[c];
-    for (int32_t v = 0; v < n; ++v) {
-      const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (ip[(size_t)v + 1] - ip[v]);
-      if (cost > ch) {
-        nchv[(size_t)c][(size_t)v] = (int32_t)((cost + ch - 1) / ch);
-        ++hvv[c];
-        hcv[c] += nchv[(size_t)c][(size_t)v];
-      }
-    }
-  }
-  // Batch composition order of the vertices as sources.  A batch advances
-  // the union of its sources' frontiers, so its cost grows with the (vertex,
-  // level) entries and edge scans of that union; sources whose traversals
-  // reach the same vertices at the same depths share them.  The key: sources
-  // without out-edges (a traversal of one vertex) last, the others by the
-  // number of two-hop walks leaving them (a proxy for how fast the traversal
-  // fans out into the graph's core), descending; ties by out-degree, then
-  // vertex id.
-  std::vector<int32_t> order((size_t)n), pos((size_t)n);
-  {
-    std::vector<int64_t> two((size_t)n, 0);
-    for (int32_t v = 0; v < n; ++v) {
-      int64_t t = 0;
-      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e)
-        t += rp[(size_t)ci[(size_t)e] + 1] - rp[ci[(size_t)e]];
-      two[(size_t)v] = t;
-    }
-    for (int32_t v = 0; v < n; ++v) order[(size_t)v] = v;
-    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-      const int32_t da = rp[(size_t)a + 1] - rp[a], db = rp[(size_t)b + 1] - rp[b];
-      if ((da == 0) != (db == 0)) return db == 0;
-      if (two[(size_t)a] != two[(size_t)b]) return two[(size_t)a] > two[(size_t)b];
-      if (da != db) return da > db;
-      return a < b;
-    });
-    for (int32_t i = 0; i < n; ++i) pos[(size_t)order[(size_t)i]] = i;
-  }
-  int64_t hv = 0, hc = 0; // maxima over the variants (workspace sizing)
-  for (int c = 0; c < kChunkVariants; ++c) {
-    hv = std::max(hv, hvv[c]);
-    hc = std::max(hc, hcv[c]);
-  }
+  const int64_t me = (int64_t)rp[n];
 
   auto g = std::make_unique<GraphRec>();
-  Carver c;
-  int32_t *d_rp = c.take<int32_t>((size_t)n + 1);
-  int32_t *d_ci = c.take<int32_t>((size_t)me);
-  int32_t *d_ip = c.take<int32_t>((size_t)n + 1);
-  int32_t *d_ii = c.take<int32_t>((size_t)me);
-  int32_t *d_nc = c.take<int32_t>((size_t)n * kChunkVariants);
-  int32_t *d_ord = c.take<int32_t>((size_t)n);
-  (void)d_rp; (void)d_ci; (void)d_ip; (void)d_ii; (void)d_nc; (void)d_ord;
-  const size_t bytes = align_up(c.off, 256);
-  if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
-  void *mem = nullptr;
-  BC_TRY(cudaMalloc(&mem, bytes));
-  Carver c2;
-  c2.base = static_cast<char *>(mem);
-  d_rp = c2.take<int32_t>((size_t)n + 1);
-  d_ci = c2.take<int32_t>((size_t)me);
-  d_ip = c2.take<int32_t>((size_t)n + 1);
-  d_ii = c2.take<int32_t>((size_t)me);
-  d_nc = c2.take<int32_t>((size_t)n * kChunkVariants);
-  d_ord = c2.take<int32_t>((size_t)n);
-  cudaStream_t st = ctx->stream;
+  void *mem = blk.mem;
+  const size_t bytes = blk.bytes;
+  int32_t *d_rp = blk.rp, *d_ci = blk.ci, *d_ip = blk.ip, *d_ii = blk.ii, *d_nc = blk.nc,
+          *d_ord = blk.ord;
+  // device: in-degree counts -> (host prefix sum) -> in-CSR scatter; chunk
+  // counts per candidate size, heavy totals and the two-hop keys
+  std::vector<int32_t> ip((size_t)n + 1, 0);
+  g->two.assign((size_t)n, 0);
+  unsigned long long totals[2 * kChunkVariants] = {};
+  int32_t *d_fill = nullptr;
+  int64_t *d_two = nullptr;
+  unsigned long long *d_tot = nullptr;
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && me) e = cudaMemcpyAsync(d_ci, ci.data(), sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && me) e = cudaMemcpyAsync(d_ii, ii.data(), sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
-  for (int c = 0; c < kChunkVariants && e == cudaSuccess && n; ++c)
-    e = cudaMemcpyAsync(d_nc + (size_t)c * n, nchv[(size_t)c].data(), sizeof(int32_t) * (size_t)n,
-                        cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && n)
-    e = cudaMemcpyAsync(d_ord, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  auto step = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  step(cudaMallocAsync(&d_fill, sizeof(int32_t) * ((size_t)n + 1), st));
+  step(cudaMallocAsync(&d_two, sizeof(int64_t) * (size_t)std::max<int32_t>(n, 1), st));
+  step(cudaMallocAsync(&d_tot, sizeof(totals), st));
+  if (e == cudaSuccess) {
+    step(cudaMemsetAsync(d_ip, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+    step(cudaMemsetAsync(d_tot, 0, sizeof(totals), st));
+    step(launch_in_degree(d_ci, me, d_ip, st));
+    step(cudaMemcpyAsync(ip.data(), d_ip, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost,
+                         st));
+    step(cudaStreamSynchronize(st));
+  }
+  if (e == cudaSuccess) {
+    for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
+    step(cudaMemcpyAsync(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
+                         st));
+    step(cudaMemcpyAsync(d_fill, d_ip, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice,
+                         st));
+    step(launch_in_scatter(d_rp, d_ci, n, d_fill, d_ii, st));
+    step(launch_graph_keys(d_rp, d_ci, d_ip, n, d_nc, d_two, d_tot, st));
+  }
+  // in-rows back in ascending source order (the scatter's atomics left them
+  // in arbitrary order): short rows by warps, medium rows by blocks, the few
+  // longest on the host
+  std::vector<int32_t> wrows, brows, hrows;
+  for (int32_t x = 0; x < n && e == cudaSuccess; ++x) {
+    const int32_t len = ip[(size_t)x + 1] - ip[x];
+    if (len >= 2 && len <= 32) wrows.push_back(x);
+    else if (len > 32 && len <= sort_block_max()) brows.push_back(x);
+    else if (len > sort_block_max()) hrows.push_back(x);
+  }
+  int32_t *d_rows = nullptr;
+  if (e == cudaSuccess && (!wrows.empty() || !brows.empty())) {
+    step(cudaMallocAsync(&d_rows, sizeof(int32_t) * (wrows.size() + brows.size()), st));
+    if (!wrows.empty())
+      step(cudaMemcpyAsync(d_rows, wrows.data(), sizeof(int32_t) * wrows.size(),
+                           cudaMemcpyHostToDevice, st));
+    if (!brows.empty())
+      step(cudaMemcpyAsync(d_rows + wrows.size(), brows.data(), sizeof(int32_t) * brows.size(),
+                           cudaMemcpyHostToDevice, st));
+    step(launch_sort_rows(d_ip, d_ii, d_rows, (int32_t)wrows.size(), d_rows + wrows.size(),
+                          (int32_t)brows.size(), st));
+  }
+  if (!hrows.empty() && e == cudaSuccess) {
+    std::vector<std::vector<int32_t>> rows(hrows.size());
+    for (size_t r = 0; r < hrows.size(); ++r) {
+      const int32_t x = hrows[r], b = ip[x], len = ip[(size_t)x + 1] - b;
+      rows[r].resize((size_t)len);
+      step(cudaMemcpyAsync(rows[r].data(), d_ii + b, sizeof(int32_t) * (size_t)len,
+                           cudaMemcpyDeviceToHost, st));
+    }
+    step(cudaStreamSynchronize(st));
+    for (size_t r = 0; r < hrows.size() && e == cudaSuccess; ++r) {
+      std::sort(rows[r].begin(), rows[r].end());
+      step(cudaMemcpyAsync(d_ii + ip[hrows[r]], rows[r].data(), sizeof(int32_t) * rows[r].size(),
+                           cudaMemcpyHostToDevice, st));
+    }
+    step(cudaStreamSynchronize(st));
+  }
+  if (e == cudaSuccess) {
+    if (n) step(cudaMemcpyAsync(g->two.data(), d_two, sizeof(int64_t) * (size_t)n,
+                                cudaMemcpyDeviceToHost, st));
+    step(cudaMemcpyAsync(totals, d_tot, sizeof(totals), cudaMemcpyDeviceToHost, st));
+  }
+  if (d_fill) cudaFreeAsync(d_fill, st);
+  if (d_rows) cudaFreeAsync(d_rows, st);
+  if (d_two) cudaFreeAsync(d_two, st);
+  if (d_tot) cudaFreeAsync(d_tot, st);
+  step(cudaStreamSynchronize(st));
   if (e != cudaSuccess) {
     cudaFree(mem);
     return cuda_status(e);
+  }
+  g->row_ptr.assign(rp, rp + (size_t)n + 1);
+  int64_t hv = 0, hc = 0; // maxima over the variants (workspace sizing)
+  for (int v = 0; v < kChunkVariants; ++v) {
+    g->heavy_v[v] = (int64_t)totals[2 * v];
+    g->heavy_c[v] = (int64_t)totals[2 * v + 1];
+    hv = std::max(hv, g->heavy_v[v]);
+    hc = std::max(hc, g->heavy_c[v]);
+    g->nch_variant[v] = d_nc + (size_t)v * n;
   }
   g->mem = mem;
   g->bytes = bytes;
@@ -513,12 +615,15 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   g->dev.heavy_vertices = hv;
   g->dev.heavy_chunks = hc;
   g->dev.order = d_ord;
-  g->order = std::move(order);
-  g->pos = std::move(pos);
-  for (int c = 0; c < kChunkVariants; ++c) {
-    g->nch_variant[c] = d_nc + (size_t)c * n;
-    g->heavy_v[c] = hvv[c];
-    g->heavy_c[c] = hcv[c];
+  g->d_order = d_ord;
+  // small graphs (the many-graph launch reads the order on the device) get
+  // their batch order now; larger ones on their first exact job
+  if (n <= kEagerOrderN) {
+    const bc_status so = ensure_order(g.get(), st);
+    if (so != BC_OK) {
+      cudaFree(mem);
+      return so;
+    }
   }
   ctx->used += bytes;
   if (m_eff) *m_eff = me;
@@ -683,16 +788,19 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   // order, since their rows follow it
   const bool grouped = batch && !dbg && j->opts.source_order == 0 && k > kb;
   if (j->all_sources) {
-    if (grouped)
+    if (grouped) {
+      s = ensure_order(j->g, st);
+      if (s != BC_OK) return s;
       std::memcpy(j->h_src, j->g->order.data(), sizeof(int32_t) * (size_t)k);
-    else
+    } else {
       for (int64_t i = 0; i < k; ++i) j->h_src[i] = (int32_t)i;
+    }
   } else if (k) {
     std::memcpy(j->h_src, j->src.data(), sizeof(int32_t) * (size_t)k);
     if (grouped) {
-      const int32_t *pos = j->g->pos.data();
+      const GraphRec *g = j->g;
       std::stable_sort(j->h_src, j->h_src + k,
-                       [pos](int32_t a, int32_t b) { return pos[a] < pos[b]; });
+                       [g](int32_t a, int32_t b) { return batch_key_less(*g, a, b); });
     }
   }
   BC_TRY(cudaMallocAsync(&j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));
