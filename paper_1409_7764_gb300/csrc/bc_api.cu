@@ -118,6 +118,12 @@ struct TuneCandidate {
   int grab;
 };
 constexpr TuneCandidate kTuneCandidates[] = {{0, 2}, {1, 2}, {2, 2}, {0, 1}};
+constexpr bool grabs_fit() {
+  for (const TuneCandidate &c : kTuneCandidates)
+    if (c.grab < 1 || c.grab > kGrabMax) return false;
+  return kGrabDefault <= kGrabMax;
+}
+static_assert(grabs_fit(), "a fetch larger than the kernels' header rounds hold");
 constexpr int kNumTune = 4;
 constexpr int kTuneRounds = 2; // trial batches per candidate
 

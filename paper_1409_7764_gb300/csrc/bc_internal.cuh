@@ -33,6 +33,7 @@ constexpr int kChunk = kChunkCandidates[0];    // chunk size of the plain and no
 #define BC_PREFETCH_GROUPS 0 // 1: fetch the next item group before processing the current one
 #endif
 constexpr int kGrabDefault = 2;                // work items a warp takes per counter fetch
+constexpr int kGrabMax = 2;                    // largest fetch the kernels' header rounds hold
 #ifndef BC_BATCH_MIN_BLOCKS
 #define BC_BATCH_MIN_BLOCKS 4                  // resident CTAs per SM the batch kernel is built for
 #endif
@@ -46,6 +47,7 @@ enum : int {
   KERR_HEAVY = 3,    // heavy-entry list capacity exceeded
   KERR_CHUNKS = 4,   // heavy chunk scratch exceeded
   KERR_LEVELS = 5,   // dense kernel: more levels than the per-level masks hold
+  KERR_GRAB = 6,     // more work items per fetch than a header round holds (host bug)
 };
 
 // Job-level counters (uint64 each), accumulated by the kernels.

@@ -347,6 +347,10 @@ __device__ __forceinline__ EntryHeaders<W, FwdField<W>::kCount>
 fwd_headers(const KParams &p, const uint64_t *A, int64_t e0, int cnt, int lane) {
   using F = FwdField<W>;
   using H = EntryHeaders<W, F::kCount>;
+  if (cnt > H::kEntries) { // more items per fetch than one header round holds
+    set_err(p.w.ctl, KERR_GRAB);
+    cnt = H::kEntries;
+  }
   int wv = 0;
   if (lane < cnt) wv = ldcg(p.w.qv + e0 + lane);
   const int i = lane % H::kEntries, f = lane / H::kEntries;
@@ -377,6 +381,10 @@ __device__ __forceinline__ EntryHeaders<W, BwdField<W>::kCount>
 bwd_headers(const KParams &p, int64_t e0, int cnt, int lane) {
   using F = BwdField<W>;
   using H = EntryHeaders<W, F::kCount>;
+  if (cnt > H::kEntries) {
+    set_err(p.w.ctl, KERR_GRAB);
+    cnt = H::kEntries;
+  }
   int wv = 0;
   if (lane < cnt) wv = ldcg(p.w.qv + e0 + lane);
   const int i = lane % H::kEntries, f = lane / H::kEntries;
