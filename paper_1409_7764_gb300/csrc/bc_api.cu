@@ -409,10 +409,147 @@ bc_status ensure_order(GraphRec *g, cudaStream_t st) {
   std::vector<int32_t> ord((size_t)n);
   for (int32_t v = 0; v < n; ++v) ord[(size_t)v] = v;
   std::sort(ord.begin(), ord.end(), [g](int32_t a, int32_t b) { return batch_key_less(*g, a, b); });
-  BC_TRY(cudaMemcpyAsync(g->d_order, ord.data(), sizeof(int32_t) * (size_t)n,
-                         cudaMemcpyHostToDevice, st));
-  BC_TRY(cudaStreamSynchronize(st));
   g->order = std::move(ord);
+  // the source stays alive with the graph, which outlives the copy (it is
+  // freed on the context's stream, and never while a job uses it)
+  BC_TRY(cudaMemcpyAsync(g->d_order, g->order.data(), sizeof(int32_t) * (size_t)n,
+                         cudaMemcpyHostToDevice, st));
+  return BC_OK;
+}
+
+// Graphs up to this many edges are prepared on the host: a few microseconds
+// of host work and one upload beat the device path's launches and
+// synchronisations (many small graphs are created one after another).
+constexpr int64_t kHostPrepMaxEdges = (int64_t)1 << 18;
+
+// Host preparation of a small graph (offsets already checked): validation,
+// canonicalisation, in-CSR by counting sort, chunk counts, two-hop keys and
+// the batch order, then one upload.
+bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx,
+                            int32_t n, int64_t m, std::unique_ptr<GraphRec> &out,
+                            int64_t *m_eff) {
+  bool canonical = true;
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      const int32_t x = col_idx[e];
+      if (x < 0 || x >= n) return BC_ERR_GRAPH;
+      if (x == v || (e > row_ptr[v] && x <= col_idx[e - 1])) canonical = false;
+    }
+  std::vector<int32_t> crp, cci;
+  const int32_t *rp = row_ptr, *ci = col_idx;
+  if (!canonical) {
+    crp.resize((size_t)n + 1);
+    cci.reserve((size_t)m);
+    crp[0] = 0;
+    std::vector<int32_t> row;
+    for (int32_t v = 0; v < n; ++v) {
+      row.assign(col_idx + row_ptr[v], col_idx + row_ptr[v + 1]);
+      std::sort(row.begin(), row.end());
+      int32_t prev = -1;
+      for (int32_t x : row)
+        if (x != v && x != prev) {
+          cci.push_back(x);
+          prev = x;
+        }
+      crp[(size_t)v + 1] = (int32_t)cci.size();
+    }
+    rp = crp.data();
+    ci = cci.data();
+  }
+  const int64_t me = (int64_t)rp[n];
+  // in-CSR by counting sort over destinations (sources stay ascending)
+  std::vector<int32_t> ip((size_t)n + 1, 0), ii((size_t)std::max<int64_t>(me, 1));
+  for (int64_t e = 0; e < me; ++e) ip[(size_t)ci[e] + 1]++;
+  for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
+  {
+    std::vector<int32_t> fill(ip.begin(), ip.end() - 1);
+    for (int32_t v = 0; v < n; ++v)
+      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) ii[(size_t)fill[ci[e]]++] = v;
+  }
+  auto g = std::make_unique<GraphRec>();
+  std::vector<int32_t> nc((size_t)n * kChunkVariants, 0);
+  int64_t hv = 0, hc = 0;
+  for (int c = 0; c < kChunkVariants; ++c) {
+    const int64_t ch = kChunkCandidates[c];
+    for (int32_t v = 0; v < n; ++v) {
+      const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (ip[(size_t)v + 1] - ip[v]);
+      if (cost > ch) {
+        const int32_t k = (int32_t)((cost + ch - 1) / ch);
+        nc[(size_t)c * n + v] = k;
+        g->heavy_v[c]++;
+        g->heavy_c[c] += k;
+      }
+    }
+    hv = std::max(hv, g->heavy_v[c]);
+    hc = std::max(hc, g->heavy_c[c]);
+  }
+  g->row_ptr.assign(rp, rp + (size_t)n + 1);
+  g->two.assign((size_t)n, 0);
+  for (int32_t v = 0; v < n; ++v) {
+    int64_t t = 0;
+    for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) t += rp[(size_t)ci[e] + 1] - rp[ci[e]];
+    g->two[(size_t)v] = t;
+  }
+  std::vector<int32_t> ord((size_t)n);
+  for (int32_t v = 0; v < n; ++v) ord[(size_t)v] = v;
+  {
+    const GraphRec *gr = g.get();
+    std::sort(ord.begin(), ord.end(), [gr](int32_t a, int32_t b) { return batch_key_less(*gr, a, b); });
+  }
+  // one allocation, one upload
+  Carver c;
+  (void)c.take<int32_t>((size_t)n + 1);
+  (void)c.take<int32_t>((size_t)me);
+  (void)c.take<int32_t>((size_t)n + 1);
+  (void)c.take<int32_t>((size_t)me);
+  (void)c.take<int32_t>((size_t)n * kChunkVariants);
+  (void)c.take<int32_t>((size_t)n);
+  const size_t bytes = align_up(c.off, 256);
+  if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
+  cudaStream_t st = ctx->stream;
+  void *mem = nullptr;
+  BC_TRY(cudaMallocAsync(&mem, bytes, st));
+  Carver c2;
+  c2.base = static_cast<char *>(mem);
+  int32_t *d_rp = c2.take<int32_t>((size_t)n + 1);
+  int32_t *d_ci = c2.take<int32_t>((size_t)me);
+  int32_t *d_ip = c2.take<int32_t>((size_t)n + 1);
+  int32_t *d_ii = c2.take<int32_t>((size_t)me);
+  int32_t *d_nc = c2.take<int32_t>((size_t)n * kChunkVariants);
+  int32_t *d_ord = c2.take<int32_t>((size_t)n);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void *dst, const void *src, size_t b) {
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st);
+  };
+  up(d_rp, rp, sizeof(int32_t) * ((size_t)n + 1));
+  up(d_ci, ci, sizeof(int32_t) * (size_t)me);
+  up(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1));
+  up(d_ii, ii.data(), sizeof(int32_t) * (size_t)me);
+  up(d_nc, nc.data(), sizeof(int32_t) * (size_t)n * kChunkVariants);
+  up(d_ord, ord.data(), sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, st);
+    return cuda_status(e);
+  }
+  for (int v = 0; v < kChunkVariants; ++v) g->nch_variant[v] = d_nc + (size_t)v * n;
+  g->mem = mem;
+  g->bytes = bytes;
+  g->dev.n = n;
+  g->dev.m = me;
+  g->dev.row_ptr = d_rp;
+  g->dev.col_idx = d_ci;
+  g->dev.in_ptr = d_ip;
+  g->dev.in_idx = d_ii;
+  g->dev.nchunks = d_nc;
+  g->dev.heavy_vertices = hv;
+  g->dev.heavy_chunks = hc;
+  g->dev.order = d_ord;
+  g->d_order = d_ord;
+  g->order = std::move(ord);
+  ctx->used += bytes;
+  if (m_eff) *m_eff = me;
+  out = std::move(g);
   return BC_OK;
 }
 
@@ -423,6 +560,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != m) return BC_ERR_GRAPH;
   for (int32_t v = 0; v < n; ++v)
     if (row_ptr[v + 1] < row_ptr[v]) return BC_ERR_GRAPH;
+  if (m <= kHostPrepMaxEdges) return build_graph_small(ctx, row_ptr, col_idx, n, m, out, m_eff);
   cudaStream_t st = ctx->stream;
   // The graph's device block, laid out for `me` canonical edges.
   struct Block {
@@ -445,18 +583,37 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   auto alloc_upload = [&](Block &b, const int32_t *rp, const int32_t *ci, int64_t me) -> bc_status {
     carve(b, me, nullptr);
     if (ctx->used + b.bytes > ctx->budget) return BC_ERR_ADMISSION;
-    BC_TRY(cudaMalloc(&b.mem, b.bytes));
+    BC_TRY(cudaMallocAsync(&b.mem, b.bytes, st));
     carve(b, me, static_cast<char *>(b.mem));
     cudaError_t r = cudaMemcpyAsync(b.rp, rp, sizeof(int32_t) * ((size_t)n + 1),
                                     cudaMemcpyHostToDevice, st);
     if (r == cudaSuccess && me)
       r = cudaMemcpyAsync(b.ci, ci, sizeof(int32_t) * (size_t)me, cudaMemcpyHostToDevice, st);
     if (r != cudaSuccess) {
-      cudaFree(b.mem);
+      cudaFreeAsync(b.mem, st);
       b.mem = nullptr;
       return cuda_status(r);
     }
     return BC_OK;
+  };
+  // The device check (flags: id out of range, row not canonical) and the
+  // in-degree counts, read back with one synchronisation.
+  std::vector<int32_t> ip((size_t)n + 1, 0);
+  auto check_and_count = [&](Block &b, int64_t me, int (&flags)[2]) -> cudaError_t {
+    int *d_flags = nullptr;
+    cudaError_t r = cudaMallocAsync(&d_flags, sizeof(flags), st);
+    if (r == cudaSuccess) r = cudaMemsetAsync(d_flags, 0, sizeof(flags), st);
+    if (r == cudaSuccess) r = launch_check_csr(b.rp, b.ci, n, d_flags, st);
+    if (r == cudaSuccess) r = cudaMemsetAsync(b.ip, 0, sizeof(int32_t) * ((size_t)n + 1), st);
+    if (r == cudaSuccess) r = launch_in_degree(b.ci, me, b.ip, st);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(ip.data(), b.ip, sizeof(int32_t) * ((size_t)n + 1),
+                          cudaMemcpyDeviceToHost, st);
+    if (d_flags) cudaFreeAsync(d_flags, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    return r;
   };
   // upload as given and check on the device: ids in range, rows canonical
   // (sorted, no duplicates, no self-loops)
@@ -465,21 +622,14 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   if (bs != BC_OK) return bs;
   int flags_h[2] = {0, 0};
   {
-    int *d_flags = nullptr;
-    cudaError_t r = cudaMallocAsync(&d_flags, sizeof(flags_h), st);
-    if (r == cudaSuccess) r = cudaMemsetAsync(d_flags, 0, sizeof(flags_h), st);
-    if (r == cudaSuccess) r = launch_check_csr(blk.rp, blk.ci, n, d_flags, st);
-    if (r == cudaSuccess)
-      r = cudaMemcpyAsync(flags_h, d_flags, sizeof(flags_h), cudaMemcpyDeviceToHost, st);
-    if (d_flags) cudaFreeAsync(d_flags, st);
-    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    const cudaError_t r = check_and_count(blk, m, flags_h);
     if (r != cudaSuccess) {
-      cudaFree(blk.mem);
+      cudaFreeAsync(blk.mem, st);
       return cuda_status(r);
     }
   }
   if (flags_h[0]) {
-    cudaFree(blk.mem);
+    cudaFreeAsync(blk.mem, st);
     return BC_ERR_GRAPH;
   }
   // canonical out-CSR: the caller's arrays as they are, else sorted,
@@ -487,7 +637,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   std::vector<int32_t> crp, cci;
   const int32_t *rp = row_ptr, *ci = col_idx;
   if (flags_h[1]) {
-    cudaFree(blk.mem);
+    cudaFreeAsync(blk.mem, st);
     crp.resize((size_t)n + 1);
     cci.reserve((size_t)m);
     crp[0] = 0;
@@ -508,6 +658,12 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
     blk = Block();
     bs = alloc_upload(blk, rp, ci, (int64_t)crp[n]);
     if (bs != BC_OK) return bs;
+    int again[2] = {0, 0};
+    const cudaError_t r = check_and_count(blk, (int64_t)crp[n], again);
+    if (r != cudaSuccess) {
+      cudaFreeAsync(blk.mem, st);
+      return cuda_status(r);
+    }
   }
   const int64_t me = (int64_t)rp[n];
 
@@ -518,7 +674,6 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
           *d_ord = blk.ord;
   // device: in-degree counts -> (host prefix sum) -> in-CSR scatter; chunk
   // counts per candidate size, heavy totals and the two-hop keys
-  std::vector<int32_t> ip((size_t)n + 1, 0);
   g->two.assign((size_t)n, 0);
   unsigned long long totals[2 * kChunkVariants] = {};
   int32_t *d_fill = nullptr;
@@ -531,14 +686,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   step(cudaMallocAsync(&d_fill, sizeof(int32_t) * ((size_t)n + 1), st));
   step(cudaMallocAsync(&d_two, sizeof(int64_t) * (size_t)std::max<int32_t>(n, 1), st));
   step(cudaMallocAsync(&d_tot, sizeof(totals), st));
-  if (e == cudaSuccess) {
-    step(cudaMemsetAsync(d_ip, 0, sizeof(int32_t) * ((size_t)n + 1), st));
-    step(cudaMemsetAsync(d_tot, 0, sizeof(totals), st));
-    step(launch_in_degree(d_ci, me, d_ip, st));
-    step(cudaMemcpyAsync(ip.data(), d_ip, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost,
-                         st));
-    step(cudaStreamSynchronize(st));
-  }
+  step(cudaMemsetAsync(d_tot, 0, sizeof(totals), st));
   if (e == cudaSuccess) {
     for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
     step(cudaMemcpyAsync(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
@@ -597,7 +745,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   if (d_tot) cudaFreeAsync(d_tot, st);
   step(cudaStreamSynchronize(st));
   if (e != cudaSuccess) {
-    cudaFree(mem);
+    cudaFreeAsync(mem, st);
     return cuda_status(e);
   }
   g->row_ptr.assign(rp, rp + (size_t)n + 1);
@@ -627,7 +775,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   if (n <= kEagerOrderN) {
     const bc_status so = ensure_order(g.get(), st);
     if (so != BC_OK) {
-      cudaFree(mem);
+      cudaFreeAsync(mem, st);
       return so;
     }
   }
@@ -1227,7 +1375,8 @@ bc_status bc_shutdown(bc_ctx *ctx) {
   ctx->jobs.clear();
   for (auto &w : ctx->free_ws) cudaFree(w->mem);
   ctx->free_ws.clear();
-  for (auto &kv : ctx->graphs) cudaFree(kv.second->mem);
+  for (auto &kv : ctx->graphs) cudaFreeAsync(kv.second->mem, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
   ctx->graphs.clear();
   for (int i = 0; i < kMaxSlots; ++i)
     if (ctx->slot_stream[i]) cudaStreamDestroy(ctx->slot_stream[i]);
@@ -1262,8 +1411,10 @@ bc_status bc_destroy_graph(bc_ctx *ctx, bc_graph h) {
     g = std::move(it->second);
     ctx->graphs.erase(it);
   }
+  // graph memory comes from the stream-ordered pool: freed after every
+  // earlier operation on the context's stream
+  cudaFreeAsync(g->mem, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
-  cudaFree(g->mem);
   ctx->used -= g->bytes;
   return BC_OK;
 }
