@@ -6,7 +6,9 @@ complete BC job over the workload's source list (forward BFS with path
 counts, backward dependency sweep, BC accumulation, output scaling) through
 the library's C ABI with inputs resident in HBM; the `e2e` figure repeats the
 step through the same C ABI starting from host buffers (graph upload, compute,
-result download).
+result download).  `precision` states the run's error against the FP64 CPU
+oracle: the sources the CPU baseline timed are run again in the timed batch
+width with FP32 and FP64 dependencies and compared element by element.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--impl ours|reference]
@@ -199,30 +201,52 @@ class ClockSampler:
 # ---- CPU oracle baseline ----------------------------------------------------------
 
 def _oracle_chunk(args):
-    n, rp, ci, srcs = args
+    n, rp, ci, srcs = args[:4]
+    keep = len(args) > 4 and args[4]
     import oracle
-    oracle.bc(n, rp, ci, srcs)
-    return len(srcs)
+    bc, _ = oracle.bc(n, rp, ci, srcs)
+    return (len(srcs), bc) if keep else len(srcs)
 
 
-def cpu_oracle_run(pool, cores, g, srcs, target_s):
+def cpu_oracle_run(pool, cores, g, srcs, target_s, keep_bc=False):
     """Times the oracle (as it stands) on a bounded sample of the workload's
-    sources, split over `cores` spawned worker processes."""
+    sources, split over `cores` spawned worker processes.  With keep_bc the
+    oracle's BC over the sample is returned too (key "bc", "sample_sources")."""
     import oracle
     t0 = time.perf_counter()
     oracle.bc(g.n, g.row_ptr, g.col_idx, srcs[:1])
     t1 = max(time.perf_counter() - t0, 1e-4)
     count = int(max(cores, min(len(srcs), target_s * cores / t1)))
     sample = srcs[:count]
-    parts = [(g.n, g.row_ptr, g.col_idx, s) for s in np.array_split(sample, cores) if len(s)]
+    parts = [(g.n, g.row_ptr, g.col_idx, s, keep_bc) for s in np.array_split(sample, cores)
+             if len(s)]
     t0 = time.perf_counter()
-    done = sum(pool.map(_oracle_chunk, parts))
+    res = pool.map(_oracle_chunk, parts)
     wall = time.perf_counter() - t0
-    return {"value": done * g.m / wall / 1e9, "unit": "GTEPS", "cores": len(parts),
-            "kind": "oracle",
-            "sample": f"first {done} of the workload's {len(srcs)} sources "
-                      f"(sequential Brandes in C, one process per core)",
-            "seconds": wall}
+    done = sum(r[0] for r in res) if keep_bc else sum(res)
+    out = {"value": done * g.m / wall / 1e9, "unit": "GTEPS", "cores": len(parts),
+           "kind": "oracle",
+           "sample": f"first {done} of the workload's {len(srcs)} sources "
+                     f"(sequential Brandes in C, one process per core)",
+           "seconds": wall}
+    if keep_bc:
+        bc = np.zeros(g.n)
+        for r in res:  # fixed order: the partial sums of consecutive source ranges
+            bc += r[1]
+        out["bc"] = bc
+        out["sample_sources"] = sample
+    return out
+
+
+def rel_errors(got, ref):
+    """Max and 99th-percentile relative error where the reference is not 0,
+    and whether the reference's exact zeros are exact zeros."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    zero = ref == 0
+    nz = ~zero
+    rel = np.abs(got[nz] - ref[nz]) / np.abs(ref[nz]) if nz.any() else np.zeros(1)
+    return {"max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99)),
+            "zeros_exact": bool(np.array_equal(got[zero], ref[zero]))}
 
 
 # ---- reference arm ------------------------------------------------------------------
@@ -396,10 +420,19 @@ def run_ours(args, w, name):
                 "value": len(srcs) * g.m / (oms / 1e3) / 1e9, "unit": "GTEPS"}
 
     cpu = None
+    precision = None
     if pool is not None:
-        cpu = cpu_oracle_run(pool, cores, g, srcs, args.cpu_seconds)
+        cpu = cpu_oracle_run(pool, cores, g, srcs, args.cpu_seconds, keep_bc=True)
         pool.close()
         cpu.pop("seconds", None)
+        # the run's error against the FP64 oracle: the same sampled sources in
+        # the timed run's batch width, with FP32 and FP64 dependencies
+        ref_bc, sample = cpu.pop("bc"), cpu.pop("sample_sources")
+        kb = int(st.get("batch_sources") or 0)
+        precision = {"sources": int(len(sample)), "reference": "CPU oracle (FP64 dependencies)"}
+        for name_, f64 in (("fp32_delta", False), ("fp64_delta", True)):
+            ctx.sources(G, sample, out=out, **dict(opts, delta_fp64=f64, batch_k=kb))
+            precision[name_] = rel_errors(out.cpu().numpy(), ref_bc)
 
     if rank == 0:
         line = {
@@ -421,6 +454,7 @@ def run_ours(args, w, name):
                          "algo_bytes_per_launch": algo_bytes / launches,
                          "launch_ms": my_ms / launches},
             "cpu_baseline": cpu,
+            "precision": precision,
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(st["kernel_launches"]) * args.steps,
