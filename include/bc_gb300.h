@@ -213,6 +213,15 @@ bc_status bc_wait(bc_ctx *ctx, bc_job job, int64_t timeout_ms, double *bc_out, b
  * bc_exact_many / bc_debug_*) on this context. */
 bc_status bc_last_stats(bc_ctx *ctx, bc_stats *stats);
 
+/* The sources whose shortest-path count reached 2^64 in the last synchronous
+ * call on this context (bc_exact, bc_sources, bc_sources_estimate and the
+ * like; each flagged occurrence of a repeated source listed), ascending.
+ * Writes up to `capacity` ids to src_out (host int32) and the full number to
+ * count.  Errors: BC_ERR_ARG for null count or a null src_out with
+ * capacity > 0. */
+bc_status bc_last_overflow_sources(bc_ctx *ctx, int32_t *src_out, int32_t capacity,
+                                   int32_t *count);
+
 /* Per-source vectors of one source through the PLAIN schedule: depth d
  * (int32, -1 unreached), path count sigma (uint64, 0 unreached) and
  * dependency delta (float64; delta[s] is the source's own dependency, which

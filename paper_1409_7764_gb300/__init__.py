@@ -168,6 +168,16 @@ class Context:
         res = holder if dev else holder[:g.n]
         return self._finish(rc, res, "bc_sources")
 
+    def last_overflow_sources(self) -> np.ndarray:
+        """Sources whose path count reached 2^64 in the last synchronous call."""
+        cnt = ctypes.c_int32(0)
+        _check(self._lib.bc_last_overflow_sources(self._h, None, 0, ctypes.byref(cnt)),
+               "bc_last_overflow_sources")
+        out = np.empty(max(cnt.value, 1), dtype=np.int32)
+        _check(self._lib.bc_last_overflow_sources(self._h, out.ctypes.data, cnt.value,
+                                                  ctypes.byref(cnt)), "bc_last_overflow_sources")
+        return out[:cnt.value].copy()
+
     def estimate(self, g: Graph, src, out=None, err_out=None, **opts):
         """(estimate, standard error) of BC from the sources `src`, taken as a
         uniform sample without replacement (bc_sources_estimate)."""

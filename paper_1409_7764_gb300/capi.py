@@ -33,7 +33,7 @@ EXPORTED = [
     "bc_init", "bc_shutdown", "bc_create_graph", "bc_destroy_graph", "bc_exact", "bc_sources",
     "bc_submit", "bc_poll", "bc_wait", "bc_last_stats", "bc_debug_source", "bc_debug_sources",
     "bc_exact_many", "bc_debug_inject_barrier_skip", "bc_status_str", "bc_sources_noalloc",
-    "bc_sources_estimate", "bc_sources_adaptive",
+    "bc_sources_estimate", "bc_sources_adaptive", "bc_last_overflow_sources",
 ]
 
 BC_NOALLOC_MAX_N = 8192
@@ -104,6 +104,7 @@ def load(path: str | None = None):
         "bc_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "bc_sources_noalloc": ([vp, vp, vp, vp, i32, i64, vp, i32, i32, vp, vp], ctypes.c_int),
         "bc_sources_estimate": ([vp, i64, vp, i32, ctypes.POINTER(bc_opts), vp, vp], ctypes.c_int),
+        "bc_last_overflow_sources": ([vp, vp, i32, i32p], ctypes.c_int),
         "bc_sources_adaptive": ([vp, i64, vp, i32, i32, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(bc_opts), vp, vp, i32p], ctypes.c_int),
     }

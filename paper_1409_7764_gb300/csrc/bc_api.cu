@@ -284,6 +284,7 @@ struct bc_ctx {
   std::vector<std::unique_ptr<WsRec>> free_ws;
 
   bc_stats last{};
+  std::vector<int32_t> last_ovf; // sources whose path count reached 2^64 in the last call
   int32_t inject_block = -1;
   int32_t inject_timeout_ms = 0;
 
@@ -325,6 +326,7 @@ struct JobRec {
   unsigned long long *h_cnt = nullptr; // pinned: counters + err + ovf count
   int *h_err = nullptr;
   int8_t *h_ovf = nullptr;
+  std::vector<int32_t> ovf_sources; // flagged source ids, ascending (set by job_finish)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evdone = nullptr;
   unsigned long long *d_trace = nullptr; // per-step trace of one batch (BC_TRACE)
   unsigned long long *h_trace = nullptr;
@@ -1121,7 +1123,13 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.mask_words = j->words;
   s.grab = kTuneCandidates[j->cand].grab;
   int32_t novf = 0;
-  for (int64_t i = 0; i < j->k; ++i) novf += j->h_ovf[i] ? 1 : 0;
+  j->ovf_sources.clear();
+  for (int64_t i = 0; i < j->k; ++i)
+    if (j->h_ovf[i]) {
+      ++novf;
+      j->ovf_sources.push_back(j->h_src[i]); // flags follow the launched source order
+    }
+  std::sort(j->ovf_sources.begin(), j->ovf_sources.end());
   if (j->h_trace && (j->h_cnt[CNT_BUSY] || j->h_cnt[CNT_IDLE])) {
     const double b = (double)j->h_cnt[CNT_BUSY], i = (double)j->h_cnt[CNT_IDLE];
     std::fprintf(stderr, "# phase clocks: items %.1f%%, waiting for the step end %.1f%%\n",
@@ -1199,6 +1207,7 @@ bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool
   }
   if (s == kStatusRetry) s = BC_ERR_INTERNAL;
   ctx->last = j.stats;
+  ctx->last_ovf = j.ovf_sources;
   return s;
 }
 
@@ -1547,11 +1556,13 @@ bc_status bc_sources_adaptive(bc_ctx *ctx, bc_graph h, const int32_t *order, int
   cudaStream_t st = ctx->stream;
   int64_t done = 0;
   bc_status worst = BC_OK;
+  std::vector<int32_t> flagged; // overflowing sources of every round
   while (done < max_k) {
     const int64_t r = std::min<int64_t>(round, max_k - done);
     s = run_sync(ctx, g, order + done, r, false, &o, nullptr, nullptr, b.sum, b.sumsq);
     if (s != BC_OK && s != BC_ERR_SIGMA_OVERFLOW) return s;
     if (s != BC_OK) worst = s;
+    flagged.insert(flagged.end(), ctx->last_ovf.begin(), ctx->last_ovf.end());
     done += r;
     if (done < 2) continue;
     // stop once every vertex whose estimate reaches min_est has a standard
@@ -1567,6 +1578,8 @@ bc_status bc_sources_adaptive(bc_ctx *ctx, bc_graph h, const int32_t *order, int
     if (worst_rel <= rel_err) break;
   }
   *k_used = (int32_t)done;
+  std::sort(flagged.begin(), flagged.end());
+  ctx->last_ovf = std::move(flagged);
   const bc_status so = estimate_out(ctx, b, n, done, o, est_out, stderr_out);
   return so != BC_OK ? so : worst;
 }
@@ -1654,6 +1667,15 @@ bc_status bc_wait(bc_ctx *ctx, bc_job job, int64_t timeout_ms, double *bc_out, b
 bc_status bc_last_stats(bc_ctx *ctx, bc_stats *stats) {
   if (!ctx || !stats) return BC_ERR_ARG;
   *stats = ctx->last;
+  return BC_OK;
+}
+
+bc_status bc_last_overflow_sources(bc_ctx *ctx, int32_t *src_out, int32_t capacity,
+                                   int32_t *count) {
+  if (!ctx || !count || capacity < 0 || (capacity > 0 && !src_out)) return BC_ERR_ARG;
+  *count = (int32_t)ctx->last_ovf.size();
+  const size_t w = std::min<size_t>((size_t)capacity, ctx->last_ovf.size());
+  if (w) std::memcpy(src_out, ctx->last_ovf.data(), sizeof(int32_t) * w);
   return BC_OK;
 }
 

@@ -122,6 +122,7 @@ def test_sigma_overflow(ctx, schedule):
         ctx.sources(G, [0, 1], schedule=schedule)
     assert ei.value.status == bc.BC_ERR_SIGMA_OVERFLOW
     assert ei.value.stats["overflow_sources"] == 1
+    assert ctx.last_overflow_sources().tolist() == [0]
     # saturated counts still match the oracle's saturating counts bit for bit
     d, sig, _ = ctx.debug_sources(G, [0], schedule=schedule, delta_fp64=True)
     od, osig, _, ovf = oracle.single_source(bad.n, bad.row_ptr, bad.col_idx, 0)
@@ -336,6 +337,8 @@ def test_wide_batch_overflow_flags(ctx):
     assert ei.value.status == bc.BC_ERR_SIGMA_OVERFLOW
     assert ei.value.stats["overflow_sources"] == int(np.count_nonzero(ovf))
     assert ei.value.stats["mask_words"] == 4
+    # the flagged sources, each flagged occurrence listed, as the oracle flags them
+    assert ctx.last_overflow_sources().tolist() == sorted(srcs[np.nonzero(ovf)[0]].tolist())
     ctx.destroy_graph(G)
 
 
