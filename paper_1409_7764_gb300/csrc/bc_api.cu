@@ -397,7 +397,9 @@ int pick_grid(const bc_ctx *ctx, const GraphDev &g, int kind, bool fp64, int wor
     int v = std::atoi(env);
     if (v > 0) return std::min(v, gmax);
   }
-  const int64_t want = std::max<int64_t>(2, ((int64_t)g.n + 127) / 128);
+  // about eight threads per vertex, at least two CTAs (graphs of 16K+
+  // vertices take every SM)
+  const int64_t want = std::max<int64_t>(2, ((int64_t)g.n * 8 + kBlock - 1) / kBlock);
   return (int)std::min<int64_t>(gmax, want);
 }
 

@@ -185,7 +185,7 @@ extern "C" bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *c
   if (e == cudaSuccess) e = cudaMemsetAsync(bc_out, 0, 8 * nn, st);
   if (e != cudaSuccess) return to_status(e);
 
-  const int64_t want = ((int64_t)n + 127) / 128;
+  const int64_t want = ((int64_t)n * 8 + kBlock - 1) / kBlock; // ~8 threads per vertex
   const int grid = (int)std::min<int64_t>(ds.grid[fp64], std::max<int64_t>(2, want));
   for (int32_t b0 = 0; b0 < k; b0 += kK) {
     const int32_t kb = std::min<int32_t>(kK, k - b0);
