@@ -115,17 +115,6 @@ __device__ __forceinline__ long long phase_clock() {
 #endif
 }
 
-// Up to four set lanes of a ballot, in lane order; missing ones are -1.
-struct Lanes4 {
-  int l[4];
-  __device__ __forceinline__ explicit Lanes4(unsigned &bal) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      l[i] = bal ? __ffs(bal) - 1 : -1;
-      bal &= bal - 1;
-    }
-  }
-};
 
 template <typename T> __device__ __forceinline__ T shfl_or_zero(T v, int src) {
   return src >= 0 ? __shfl_sync(kFull, v, src) : T(0);
@@ -194,12 +183,6 @@ __device__ __forceinline__ void gather_coeffs(const DT *row, uint64_t S, DT *acc
   }
 }
 
-__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v |= __shfl_xor_sync(kFull, v, off);
-  return v;
-}
-
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
@@ -252,31 +235,6 @@ __device__ __forceinline__ void gather_counts_full(const uint64_t *base, int u, 
       s1 += x1[i];
       c1 |= s1 < x1[i];
     }
-  }
-}
-
-// Dependency coefficients, added in edge order.
-template <int U, typename DT>
-__device__ __forceinline__ void gather_coeffs_full(const DT *base, int x, uint64_t S, int lane,
-                                                   DT &a0, DT &a1) {
-  unsigned bal = __ballot_sync(kFull, S != 0);
-  while (bal) {
-    const LanesU<U> q(bal);
-    DT y0[U], y1[U];
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-      const int xx = shfl_or_zero(x, q.l[i]);
-      const uint64_t SS = shfl_or_zero(S, q.l[i]);
-      const DT *row = base + (size_t)xx * kK;
-      y0[i] = ((SS >> lane) & 1ull) ? ldcg(row + lane) : DT(0);
-      y1[i] = ((SS >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : DT(0);
-    }
-#pragma unroll
-    for (int i = 0; i < U; ++i)
-      if (q.l[i] >= 0) {
-        a0 += y0[i];
-        a1 += y1[i];
-      }
   }
 }
 
