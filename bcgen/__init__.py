@@ -148,6 +148,22 @@ def ba_directed(n: int, out_edges: int = 8, m0: int = 9, seed: int = 1) -> Graph
     return csr_from_edges(n, src, dst, name=f"ba-n{n}-out{out_edges}-seed{seed}")
 
 
+def ba_undirected(n: int, beta: int, seed: int = 1) -> Graph:
+    """Undirected preferential attachment with every edge stored in both
+    directions (the paper's synthetic workload, Section III: m is about
+    2*beta*n directed edges, edge density d = m/n from 2 to 60).  Seed: a
+    clique on beta+1 vertices; then each new vertex joins beta distinct
+    existing vertices drawn with probability proportional to their degree.
+    Built from the directed generator (whose total degree is the undirected
+    degree) by adding the reverse of every edge."""
+    if beta < 1 or n < beta + 1:
+        raise ValueError("need beta >= 1 and n >= beta + 1")
+    g = ba_directed(n, beta, beta + 1, seed)
+    a, b = g.edges()
+    return csr_from_edges(n, np.concatenate([a, b]), np.concatenate([b, a]),
+                          name=f"ba-undirected-n{n}-beta{beta}-seed{seed}")
+
+
 def sample_sources(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct sources uniform over [0, n) (seeded partial Fisher-Yates)."""
     out = np.empty(max(k, 1), dtype=np.int32)

@@ -52,6 +52,10 @@ WORKLOADS = {
     # directed preferential attachment n = 2^20, 8 out-edges, 4096 sources
     "ba20-sampled4096": dict(kind="ba", n=1 << 20, out=8, seed=1, sources=4096, src_seed=1,
                              batch_k=0, schedule="batch"),
+    # the paper's largest input: undirected preferential attachment, n = 30,000,
+    # 30 edges per arrival stored both ways (edge density m/n = 60), all sources
+    "ba30k-d60-exact": dict(kind="ba_undirected", n=30000, beta=30, seed=1, sources="all",
+                            batch_k=0, schedule="batch"),
     # R-MAT scale 10, edge factor 8, all 1024 sources, one source per launch
     "rmat10-exact-plain": dict(kind="rmat", scale=10, ef=8, seed=1, sources="all", batch_k=1,
                                schedule="plain", fp64=True),
@@ -61,6 +65,8 @@ WORKLOADS = {
 def make_graph(w):
     if w["kind"] == "rmat":
         return bcgen.rmat(w["scale"], w["ef"], seed=w["seed"])
+    if w["kind"] == "ba_undirected":
+        return bcgen.ba_undirected(w["n"], w["beta"], seed=w["seed"])
     return bcgen.ba_directed(w["n"], w["out"], 9, seed=w["seed"])
 
 
@@ -89,8 +95,9 @@ def bytes_model(stats, delta_bytes):
            mask, BC read-modify-write), 12 B per scanned in-edge (column + the
            predecessor's mask), 16 B per scanned out-edge (column + one or two
            masks), (8 + b) B per (source, DAG edge) (predecessor path count,
-           successor coefficient), (24 + b) B per (source, reached vertex)
-           (path count write, read, reset; coefficient write).
+           successor coefficient), (16 + b) B per (source, reached vertex)
+           (path count write and read; coefficient write; counts need no
+           reset, since a count is only read where its batch wrote it).
     queue batch kernel (2): 124 B per entry (queue id/mask, CSR offsets, dense
            mask read/write/clear, visited, BC), 12 B per scanned edge, same
            per-pair terms.
@@ -104,9 +111,9 @@ def bytes_model(stats, delta_bytes):
     kind = stats.get("kernel_kind", 2)
     if kind == 3:
         return (24 * stats["n"] * stats["levels_sum"] + 72 * E + 12 * I + 16 * O +
-                (8 + b) * D + (24 + b) * R)
+                (8 + b) * D + (16 + b) * R)
     if kind == 2:
-        return 124 * E + 12 * (I + O) + (8 + b) * D + (24 + b) * R
+        return 124 * E + 12 * (I + O) + (8 + b) * D + (16 + b) * R
     return (84 + b) * E + 8 * (I + O) + (8 + b) * D
 
 

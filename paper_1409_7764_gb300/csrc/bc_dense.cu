@@ -125,11 +125,12 @@ __device__ __forceinline__ bool dense_discover(const KParams &p, const HeavyLeve
 }
 
 // Closes one backward entry (vertex v, mask F) from the lane's successor sums:
-// dependencies, coefficients, resets; returns the lane's BC contribution.
+// dependencies and coefficients (path counts need no reset: they are only
+// read where the same batch wrote them); returns the lane's BC contribution.
 template <typename DT>
 __device__ __forceinline__ double dense_close(const KParams &p, int lvl, int v, uint64_t F, DT a0,
                                               DT a1, int s_lo, int s_hi, int lane) {
-  uint64_t *srow = p.w.sigma + (size_t)v * kK;
+  const uint64_t *srow = p.w.sigma + (size_t)v * kK;
   DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * kK;
   double contrib = 0.0;
   const int n = p.g.n;
@@ -138,7 +139,6 @@ __device__ __forceinline__ double dense_close(const KParams &p, int lvl, int v, 
     const DT sf = u64_to<DT>(sg);
     const DT dl = sf * a0;
     crow[lane] = (DT(1) + dl) / sf;
-    srow[lane] = 0;
     if (s_lo != v) contrib += (double)dl;
     if (p.dbg_d) {
       const size_t o = (size_t)lane * n + v;
@@ -152,7 +152,6 @@ __device__ __forceinline__ double dense_close(const KParams &p, int lvl, int v, 
     const DT sf = u64_to<DT>(sg);
     const DT dl = sf * a1;
     crow[32 + lane] = (DT(1) + dl) / sf;
-    srow[32 + lane] = 0;
     if (s_hi != v) contrib += (double)dl;
     if (p.dbg_d) {
       const size_t o = (size_t)(lane + 32) * n + v;

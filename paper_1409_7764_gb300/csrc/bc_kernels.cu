@@ -262,12 +262,13 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
 // Batch: closes entry v (mask F) at level l of the backward sweep given the
 // lane's successor sums a, its path counts sg and (lane 0) the current BC
 // value bcv, all loaded by the caller ahead of the successor scan:
-// dependencies, coefficients, BC, resets.
+// dependencies, coefficients, BC, resets.  (Path counts need no reset: a
+// count is only read where the same batch wrote it, for a source whose mask
+// bit marks the vertex reached.)
 template <typename DT, int W, bool SQ>
 __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, const Mask<W> &F,
                                              const DT (&a)[2 * W], const uint64_t (&sg)[2 * W],
                                              double bcv, uint64_t *Wn, int lane) {
-  uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
   DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * (kK * W);
   double contrib = 0.0, contrib2 = 0.0;
   const int n = p.g.n;
@@ -278,7 +279,6 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
       const DT sf = u64_to<DT>(sg[i]);
       const DT dl = sf * a[i];
       crow[j] = (DT(1) + dl) / sf;
-      srow[j] = 0;
       if (__ldg(p.src + j) != v) {
         contrib += (double)dl;
         if (SQ) contrib2 += (double)dl * (double)dl;

@@ -172,12 +172,12 @@ extern "C" bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *c
   p.src_base = 0;
 
   // The array keeps whatever the previous call left; everything the kernel
-  // expects to start at zero is cleared here, as is the output.
+  // expects to start at zero is cleared here, as is the output.  (Path counts
+  // and coefficients are only read where the same batch wrote them.)
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.vis, 0, 8 * nn, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.fr, 0, 8 * 4 * nn, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.sigma, 0, 8 * nn * kK, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.harrive, 0, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_ovf, 0, kK, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.job_cnt, 0, 8 * CNT_N, st);

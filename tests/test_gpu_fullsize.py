@@ -100,3 +100,23 @@ def test_many_graphs_full_size_sampled(ctx):
         close(outs[i], ref, 1e-4)
     for h in hs:
         ctx.destroy_graph(h)
+
+
+def test_ba_undirected_30k_d60_full_size(ctx):
+    """The paper's largest preferential-attachment input (n = 30,000, edge
+    density 60: 30 undirected edges per arrival, stored both ways), exact BC
+    as the benchmark runs it (256 sources per batch), checked on a 256-source
+    subset in the same configuration and on properties of the full run."""
+    g = bcgen.ba_undirected(30000, 30, seed=1)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    full = ctx.exact(G).copy()
+    st = ctx.last_stats()
+    assert st["sources"] == g.n and st["batch_sources"] == 256
+    assert np.all(full >= 0)
+    # every source reaches every vertex (the graph is connected)
+    assert st["reached_pairs"] == g.n * g.n
+    src = np.concatenate([np.arange(8), bcgen.sample_sources(g.n, 248, seed=9)]).astype(np.int32)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, src)
+    for fp64 in (False, True):
+        close(ctx.sources(G, src, batch_k=256, delta_fp64=fp64), ref, TOL[fp64])
+    bit_exact(ctx, G, g, src[:4], 256)

@@ -40,7 +40,8 @@ def graphs_small():
         bcgen.path(37), bcgen.path(16, bidirected=True), bcgen.cycle(21), bcgen.star(40, "bi"),
         bcgen.star(30, "out"), bcgen.complete(9), bcgen.grid(6, 7), bcgen.rmat(8, 8, seed=1),
         bcgen.rmat(10, 8, seed=1), bcgen.ba_directed(700, 4, 5, seed=2),
-        bcgen.random_digraph(50, 0.08, 3),
+        bcgen.random_digraph(50, 0.08, 3), bcgen.ba_undirected(600, 3, seed=2),
+        bcgen.ba_undirected(400, 1, seed=3),
     ]
 
 
@@ -130,6 +131,28 @@ def test_sigma_overflow(ctx, schedule):
     np.testing.assert_array_equal(d[0], od)
     np.testing.assert_array_equal(sig[0], osig)
     ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("schedule", ["batch_queue", "batch_dense"])
+def test_counts_left_by_earlier_jobs_are_never_read(schedule):
+    """Path counts are not reset after a batch (a count is only read where the
+    same batch wrote it).  Jobs that first fill a workspace with huge counts
+    (2^30 paths, 91 vertices) and then reuse it for smaller graphs whose
+    counts are small still match the oracle, in both batched kernels."""
+    import paper_1409_7764_gb300 as bc
+    chain = bcgen.layered_chain(30, 2)
+    others = [bcgen.rmat(6, 8, seed=2), bcgen.ba_undirected(90, 2, seed=1)]
+    with bc.Context(0) as fresh:
+        for g in [chain] + others + [chain]:
+            G = fresh.create_graph(g.row_ptr, g.col_idx)
+            ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+            assert_bc_close(fresh.exact(G, delta_fp64=True, schedule=schedule), ref, True)
+            d, sig, _ = fresh.debug_sources(G, [1, 2], schedule=schedule, delta_fp64=True)
+            for j, s_ in enumerate([1, 2]):
+                od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, s_)
+                np.testing.assert_array_equal(d[j], od)
+                np.testing.assert_array_equal(sig[j], osig)
+            fresh.destroy_graph(G)
 
 
 @pytest.mark.parametrize("fp64", [True, False])

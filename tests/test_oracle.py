@@ -126,6 +126,7 @@ def _small_graphs():
                                 (20, 0.3, 5)]]
     out.append(bcgen.rmat(5, 4, seed=3))
     out.append(bcgen.ba_directed(30, out_edges=3, m0=4, seed=2))
+    out.append(bcgen.ba_undirected(28, beta=2, seed=4))
     return out
 
 
@@ -180,7 +181,8 @@ def _all_pairs_hops(g):
 
 
 @pytest.mark.parametrize("g", [bcgen.rmat(8, 8, seed=1), bcgen.rmat(9, 4, seed=2),
-                               bcgen.ba_directed(400, 4, 5, seed=3)], ids=lambda g: g.name)
+                               bcgen.ba_directed(400, 4, 5, seed=3),
+                               bcgen.ba_undirected(400, 3, seed=3)], ids=lambda g: g.name)
 def test_sum_invariant(g):
     """sum_v BC[v] = sum over reachable ordered pairs s != t of (d(s,t) - 1):
     each shortest s-t path has d(s,t) - 1 interior vertices."""
@@ -233,6 +235,21 @@ def test_networkx_cross_check():
         refn = nx.betweenness_centrality(G, normalized=True)
         np.testing.assert_allclose(oracle.normalise(bc, g.n), [refn[v] for v in range(g.n)],
                                    rtol=1e-11, atol=1e-12)
+
+
+def test_networkx_undirected_cross_check():
+    """On a graph with every edge in both directions (the paper's undirected
+    preferential-attachment inputs), the sum over ordered pairs counts each
+    unordered pair twice: BC = 2 x NetworkX's undirected betweenness."""
+    nx = pytest.importorskip("networkx")
+    for g in [bcgen.ba_undirected(200, 1, seed=1), bcgen.ba_undirected(150, 4, seed=2)]:
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        s, d = g.edges()
+        G.add_edges_from(zip(s.tolist(), d.tolist()))
+        ref = nx.betweenness_centrality(G, normalized=False)
+        bc, _ = obc(g)
+        np.testing.assert_allclose(bc, [2 * ref[v] for v in range(g.n)], rtol=1e-11, atol=1e-9)
 
 
 # ---- input handling ------------------------------------------------------------
