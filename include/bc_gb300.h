@@ -235,6 +235,16 @@ bc_status bc_debug_sources(bc_ctx *ctx, bc_graph g, const int32_t *src, int32_t 
                            const bc_opts *opts, int32_t *d_out, uint64_t *sigma_out,
                            double *delta_out);
 
+/* The graph as the library holds it on the device: the canonical out-CSR
+ * row_ptr[n+1], col_idx[m] (m = the canonical edge count; every row
+ * ascending, no duplicates or self-loops) and its transpose in_ptr[n+1],
+ * in_idx[m] (in-neighbours of v in in_idx[in_ptr[v] .. in_ptr[v+1]),
+ * ascending).  Host arrays owned by the caller; any may be NULL.  For tests
+ * and debugging.  Errors: BC_ERR_ARG (null ctx), BC_ERR_GRAPH (unknown
+ * handle), BC_ERR_CUDA. */
+bc_status bc_debug_graph(bc_ctx *ctx, bc_graph g, int32_t *row_ptr, int32_t *col_idx,
+                         int32_t *in_ptr, int32_t *in_idx);
+
 /* Exact BC of `count` resident graphs.  Graphs of up to 8192 vertices run in
  * ONE persistent launch: each thread block takes the next graph (largest
  * n*(m+n) first), runs all of its source batches (opts.batch_k sources each;

@@ -278,6 +278,16 @@ class Context:
             _check(rc, "bc_debug_sources")
         return d, sig, dl
 
+    def debug_graph(self, g: Graph):
+        """(row_ptr, col_idx, in_ptr, in_idx) as the library holds the graph."""
+        rp = np.empty(g.n + 1, dtype=np.int32)
+        ci = np.empty(max(g.m, 1), dtype=np.int32)
+        ip = np.empty(g.n + 1, dtype=np.int32)
+        ii = np.empty(max(g.m, 1), dtype=np.int32)
+        _check(self._lib.bc_debug_graph(self._h, g.handle, rp.ctypes.data, ci.ctypes.data,
+                                        ip.ctypes.data, ii.ctypes.data), "bc_debug_graph")
+        return rp, ci[:g.m], ip, ii[:g.m]
+
     def debug_source(self, g: Graph, s: int):
         d = np.empty(g.n, dtype=np.int32)
         sig = np.empty(g.n, dtype=np.uint64)

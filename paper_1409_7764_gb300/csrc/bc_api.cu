@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -107,6 +108,54 @@ inline bool batch_key_less(const GraphRec &g, int32_t a, int32_t b) {
   if (g.two[(size_t)a] != g.two[(size_t)b]) return g.two[(size_t)a] > g.two[(size_t)b];
   if (da != db) return da > db;
   return a < b;
+}
+
+// The same order as two words compared in turn (smaller first): dead flag
+// and descending two-hop count, then descending out-degree and the id.
+struct OrderKey {
+  uint64_t hi, lo;
+  bool operator<(const OrderKey &o) const { return hi != o.hi ? hi < o.hi : lo < o.lo; }
+};
+inline OrderKey order_key(const std::vector<int32_t> &row_ptr, const std::vector<int64_t> &two,
+                          int32_t v) {
+  const int32_t d = row_ptr[(size_t)v + 1] - row_ptr[(size_t)v];
+  const uint64_t t = (uint64_t)std::max<int64_t>(two[(size_t)v], 0); // < 2^63
+  return {(d == 0 ? 1ull << 63 : 0ull) | ((uint64_t)INT64_MAX - t),
+          ((uint64_t)(uint32_t)(INT32_MAX - d) << 32) | (uint32_t)v};
+}
+
+// Every vertex in batch order (batch_key_less): packed keys sorted in
+// chunks on up to eight threads, then merged pairwise.
+std::vector<int32_t> batch_order(const std::vector<int32_t> &row_ptr,
+                                 const std::vector<int64_t> &two, int32_t n) {
+  std::vector<OrderKey> keys((size_t)n);
+  for (int32_t v = 0; v < n; ++v) keys[(size_t)v] = order_key(row_ptr, two, v);
+  const int chunks = (int)std::min<int64_t>(8, std::max<int64_t>(1, n / 8192));
+  std::vector<size_t> cut((size_t)chunks + 1);
+  for (int c = 0; c <= chunks; ++c) cut[(size_t)c] = (size_t)n * (size_t)c / (size_t)chunks;
+  auto run = [](int count, const std::function<void(int)> &f) {
+    std::vector<std::thread> th;
+    for (int i = 1; i < count; ++i) th.emplace_back(f, i);
+    f(0);
+    for (auto &t : th) t.join();
+  };
+  run(chunks, [&](int c) {
+    std::sort(keys.begin() + (ptrdiff_t)cut[(size_t)c], keys.begin() + (ptrdiff_t)cut[(size_t)c + 1]);
+  });
+  for (int width = 1; width < chunks; width *= 2) {
+    const int pairs = (chunks + 2 * width - 1) / (2 * width);
+    run(pairs, [&](int p_) {
+      const int c0 = 2 * width * p_;
+      const int c1 = std::min(c0 + width, chunks), c2 = std::min(c0 + 2 * width, chunks);
+      if (c1 < c2)
+        std::inplace_merge(keys.begin() + (ptrdiff_t)cut[(size_t)c0],
+                           keys.begin() + (ptrdiff_t)cut[(size_t)c1],
+                           keys.begin() + (ptrdiff_t)cut[(size_t)c2]);
+    });
+  }
+  std::vector<int32_t> ord((size_t)n);
+  for (int32_t i = 0; i < n; ++i) ord[(size_t)i] = (int32_t)(uint32_t)keys[(size_t)i].lo;
+  return ord;
 }
 
 // Graphs up to this many vertices get their batch order at creation.
@@ -410,10 +459,7 @@ bc_status ensure_order(GraphRec *g, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g->order_mu);
   const int32_t n = g->dev.n;
   if (!g->order.empty() || n == 0) return BC_OK;
-  std::vector<int32_t> ord((size_t)n);
-  for (int32_t v = 0; v < n; ++v) ord[(size_t)v] = v;
-  std::sort(ord.begin(), ord.end(), [g](int32_t a, int32_t b) { return batch_key_less(*g, a, b); });
-  g->order = std::move(ord);
+  g->order = batch_order(g->row_ptr, g->two, n);
   // the source stays alive with the graph, which outlives the copy (it is
   // freed on the context's stream, and never while a job uses it)
   BC_TRY(cudaMemcpyAsync(g->d_order, g->order.data(), sizeof(int32_t) * (size_t)n,
@@ -494,12 +540,7 @@ bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *
     for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) t += rp[(size_t)ci[e] + 1] - rp[ci[e]];
     g->two[(size_t)v] = t;
   }
-  std::vector<int32_t> ord((size_t)n);
-  for (int32_t v = 0; v < n; ++v) ord[(size_t)v] = v;
-  {
-    const GraphRec *gr = g.get();
-    std::sort(ord.begin(), ord.end(), [gr](int32_t a, int32_t b) { return batch_key_less(*gr, a, b); });
-  }
+  std::vector<int32_t> ord = batch_order(g->row_ptr, g->two, n);
   // one allocation, one upload
   Carver c;
   (void)c.take<int32_t>((size_t)n + 1);
@@ -566,6 +607,18 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
     if (row_ptr[v + 1] < row_ptr[v]) return BC_ERR_GRAPH;
   if (m <= kHostPrepMaxEdges) return build_graph_small(ctx, row_ptr, col_idx, n, m, out, m_eff);
   cudaStream_t st = ctx->stream;
+  // BC_PREP_TRACE=1: per-phase times of the preparation to stderr (each mark
+  // synchronises the stream, so the traced run is slower than a plain one)
+  const bool trace = std::getenv("BC_PREP_TRACE") != nullptr;
+  const auto t_start = std::chrono::steady_clock::now();
+  auto mark = [&](const char *what) {
+    if (!trace) return;
+    cudaStreamSynchronize(st);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                                 t_start).count();
+    std::fprintf(stderr, "# graph prep n=%d m=%lld: %-28s %8.3f ms\n", n, (long long)m, what, ms);
+  };
+  mark("host offsets checked");
   // The graph's device block, laid out for `me` canonical edges.
   struct Block {
     void *mem = nullptr;
@@ -600,33 +653,70 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
     }
     return BC_OK;
   };
-  // The device check (flags: id out of range, row not canonical) and the
-  // in-degree counts, read back with one synchronisation.
-  std::vector<int32_t> ip((size_t)n + 1, 0);
-  auto check_and_count = [&](Block &b, int64_t me, int (&flags)[2]) -> cudaError_t {
+  // The whole device pipeline on the uploaded block, read back with one
+  // synchronisation: validation flags (id out of range, row not canonical),
+  // in-degrees -> scan -> in-CSR scatter, row sorts, chunk counts and totals,
+  // two-hop keys.  Every kernel skips out-of-range ids, so a bad graph is only
+  // reported.
+  auto prepare = [&](Block &b, int64_t me, int (&flags)[2], std::vector<int64_t> &two,
+                     unsigned long long (&totals)[2 * kChunkVariants]) -> cudaError_t {
     int *d_flags = nullptr;
-    cudaError_t r = cudaMallocAsync(&d_flags, sizeof(flags), st);
-    if (r == cudaSuccess) r = cudaMemsetAsync(d_flags, 0, sizeof(flags), st);
-    if (r == cudaSuccess) r = launch_check_csr(b.rp, b.ci, n, d_flags, st);
-    if (r == cudaSuccess) r = cudaMemsetAsync(b.ip, 0, sizeof(int32_t) * ((size_t)n + 1), st);
-    if (r == cudaSuccess) r = launch_in_degree(b.ci, me, b.ip, st);
-    if (r == cudaSuccess)
-      r = cudaMemcpyAsync(flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
-    if (r == cudaSuccess)
-      r = cudaMemcpyAsync(ip.data(), b.ip, sizeof(int32_t) * ((size_t)n + 1),
-                          cudaMemcpyDeviceToHost, st);
+    int32_t *d_fill = nullptr, *d_rows = nullptr;
+    int64_t *d_two = nullptr;
+    unsigned long long *d_tot = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto step = [&](cudaError_t r) {
+      if (e == cudaSuccess) e = r;
+    };
+    step(cudaMallocAsync(&d_flags, sizeof(int) * 2 + 3 * sizeof(int32_t), st));
+    step(cudaMallocAsync(&d_fill, sizeof(int32_t) * ((size_t)n + 1), st));
+    step(cudaMallocAsync(&d_rows, sizeof(int32_t) * 3 * (size_t)n, st));
+    step(cudaMallocAsync(&d_two, sizeof(int64_t) * (size_t)n, st));
+    step(cudaMallocAsync(&d_tot, sizeof(totals), st));
+    if (e == cudaSuccess) {
+      int32_t *d_rcnt = reinterpret_cast<int32_t *>(d_flags + 2);
+      step(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2, st));
+      step(cudaMemsetAsync(d_tot, 0, sizeof(totals), st));
+      step(launch_check_csr(b.rp, b.ci, n, d_flags, st));
+      step(cudaMemsetAsync(b.ip, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+      step(launch_in_degree(b.ci, me, n, b.ip, st));
+      mark("checked, in-degrees counted");
+      step(launch_scan_inclusive(b.ip, (int64_t)n + 1, st));
+      step(cudaMemcpyAsync(d_fill, b.ip, sizeof(int32_t) * ((size_t)n + 1),
+                           cudaMemcpyDeviceToDevice, st));
+      mark("in-degrees scanned");
+      step(launch_in_scatter(b.rp, b.ci, n, d_fill, b.ii, st));
+      mark("in-edges scattered");
+      step(launch_graph_keys(b.rp, b.ci, b.ip, n, b.nc, d_two, d_tot, st));
+      mark("chunk counts and keys");
+      // in-rows back in ascending source order (the scatter's atomics left
+      // them in arbitrary order)
+      step(launch_sort_rows(b.ip, b.ii, n, me, d_rows, d_rcnt, st));
+      mark("in-rows sorted");
+      step(cudaMemcpyAsync(flags, d_flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+      step(cudaMemcpyAsync(two.data(), d_two, sizeof(int64_t) * (size_t)n,
+                           cudaMemcpyDeviceToHost, st));
+      step(cudaMemcpyAsync(totals, d_tot, sizeof(totals), cudaMemcpyDeviceToHost, st));
+    }
     if (d_flags) cudaFreeAsync(d_flags, st);
-    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
-    return r;
+    if (d_fill) cudaFreeAsync(d_fill, st);
+    if (d_rows) cudaFreeAsync(d_rows, st);
+    if (d_two) cudaFreeAsync(d_two, st);
+    if (d_tot) cudaFreeAsync(d_tot, st);
+    step(cudaStreamSynchronize(st));
+    mark("flags, keys and totals read");
+    return e;
   };
-  // upload as given and check on the device: ids in range, rows canonical
-  // (sorted, no duplicates, no self-loops)
+  auto g = std::make_unique<GraphRec>();
+  g->two.assign((size_t)n, 0);
+  unsigned long long totals[2 * kChunkVariants] = {};
   Block blk;
   bc_status bs = alloc_upload(blk, row_ptr, col_idx, m);
   if (bs != BC_OK) return bs;
+  mark("uploaded");
   int flags_h[2] = {0, 0};
   {
-    const cudaError_t r = check_and_count(blk, m, flags_h);
+    const cudaError_t r = prepare(blk, m, flags_h, g->two, totals);
     if (r != cudaSuccess) {
       cudaFreeAsync(blk.mem, st);
       return cuda_status(r);
@@ -637,9 +727,10 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
     return BC_ERR_GRAPH;
   }
   // canonical out-CSR: the caller's arrays as they are, else sorted,
-  // de-duplicated rows without self-loops (made on the host, uploaded again)
+  // de-duplicated rows without self-loops (made on the host, uploaded and
+  // prepared again)
   std::vector<int32_t> crp, cci;
-  const int32_t *rp = row_ptr, *ci = col_idx;
+  const int32_t *rp = row_ptr;
   if (flags_h[1]) {
     cudaFreeAsync(blk.mem, st);
     crp.resize((size_t)n + 1);
@@ -658,100 +749,21 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
       crp[(size_t)v + 1] = (int32_t)cci.size();
     }
     rp = crp.data();
-    ci = cci.data();
     blk = Block();
-    bs = alloc_upload(blk, rp, ci, (int64_t)crp[n]);
+    bs = alloc_upload(blk, rp, cci.data(), (int64_t)crp[n]);
     if (bs != BC_OK) return bs;
     int again[2] = {0, 0};
-    const cudaError_t r = check_and_count(blk, (int64_t)crp[n], again);
+    const cudaError_t r = prepare(blk, (int64_t)crp[n], again, g->two, totals);
     if (r != cudaSuccess) {
       cudaFreeAsync(blk.mem, st);
       return cuda_status(r);
     }
   }
   const int64_t me = (int64_t)rp[n];
-
-  auto g = std::make_unique<GraphRec>();
   void *mem = blk.mem;
   const size_t bytes = blk.bytes;
   int32_t *d_rp = blk.rp, *d_ci = blk.ci, *d_ip = blk.ip, *d_ii = blk.ii, *d_nc = blk.nc,
           *d_ord = blk.ord;
-  // device: in-degree counts -> (host prefix sum) -> in-CSR scatter; chunk
-  // counts per candidate size, heavy totals and the two-hop keys
-  g->two.assign((size_t)n, 0);
-  unsigned long long totals[2 * kChunkVariants] = {};
-  int32_t *d_fill = nullptr;
-  int64_t *d_two = nullptr;
-  unsigned long long *d_tot = nullptr;
-  cudaError_t e = cudaSuccess;
-  auto step = [&](cudaError_t r) {
-    if (e == cudaSuccess) e = r;
-  };
-  step(cudaMallocAsync(&d_fill, sizeof(int32_t) * ((size_t)n + 1), st));
-  step(cudaMallocAsync(&d_two, sizeof(int64_t) * (size_t)std::max<int32_t>(n, 1), st));
-  step(cudaMallocAsync(&d_tot, sizeof(totals), st));
-  step(cudaMemsetAsync(d_tot, 0, sizeof(totals), st));
-  if (e == cudaSuccess) {
-    for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
-    step(cudaMemcpyAsync(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
-                         st));
-    step(cudaMemcpyAsync(d_fill, d_ip, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice,
-                         st));
-    step(launch_in_scatter(d_rp, d_ci, n, d_fill, d_ii, st));
-    step(launch_graph_keys(d_rp, d_ci, d_ip, n, d_nc, d_two, d_tot, st));
-  }
-  // in-rows back in ascending source order (the scatter's atomics left them
-  // in arbitrary order): short rows by warps, medium rows by blocks, the few
-  // longest on the host
-  std::vector<int32_t> wrows, brows, hrows;
-  for (int32_t x = 0; x < n && e == cudaSuccess; ++x) {
-    const int32_t len = ip[(size_t)x + 1] - ip[x];
-    if (len >= 2 && len <= 32) wrows.push_back(x);
-    else if (len > 32 && len <= sort_block_max()) brows.push_back(x);
-    else if (len > sort_block_max()) hrows.push_back(x);
-  }
-  int32_t *d_rows = nullptr;
-  if (e == cudaSuccess && (!wrows.empty() || !brows.empty())) {
-    step(cudaMallocAsync(&d_rows, sizeof(int32_t) * (wrows.size() + brows.size()), st));
-    if (!wrows.empty())
-      step(cudaMemcpyAsync(d_rows, wrows.data(), sizeof(int32_t) * wrows.size(),
-                           cudaMemcpyHostToDevice, st));
-    if (!brows.empty())
-      step(cudaMemcpyAsync(d_rows + wrows.size(), brows.data(), sizeof(int32_t) * brows.size(),
-                           cudaMemcpyHostToDevice, st));
-    step(launch_sort_rows(d_ip, d_ii, d_rows, (int32_t)wrows.size(), d_rows + wrows.size(),
-                          (int32_t)brows.size(), st));
-  }
-  if (!hrows.empty() && e == cudaSuccess) {
-    std::vector<std::vector<int32_t>> rows(hrows.size());
-    for (size_t r = 0; r < hrows.size(); ++r) {
-      const int32_t x = hrows[r], b = ip[x], len = ip[(size_t)x + 1] - b;
-      rows[r].resize((size_t)len);
-      step(cudaMemcpyAsync(rows[r].data(), d_ii + b, sizeof(int32_t) * (size_t)len,
-                           cudaMemcpyDeviceToHost, st));
-    }
-    step(cudaStreamSynchronize(st));
-    for (size_t r = 0; r < hrows.size() && e == cudaSuccess; ++r) {
-      std::sort(rows[r].begin(), rows[r].end());
-      step(cudaMemcpyAsync(d_ii + ip[hrows[r]], rows[r].data(), sizeof(int32_t) * rows[r].size(),
-                           cudaMemcpyHostToDevice, st));
-    }
-    step(cudaStreamSynchronize(st));
-  }
-  if (e == cudaSuccess) {
-    if (n) step(cudaMemcpyAsync(g->two.data(), d_two, sizeof(int64_t) * (size_t)n,
-                                cudaMemcpyDeviceToHost, st));
-    step(cudaMemcpyAsync(totals, d_tot, sizeof(totals), cudaMemcpyDeviceToHost, st));
-  }
-  if (d_fill) cudaFreeAsync(d_fill, st);
-  if (d_rows) cudaFreeAsync(d_rows, st);
-  if (d_two) cudaFreeAsync(d_two, st);
-  if (d_tot) cudaFreeAsync(d_tot, st);
-  step(cudaStreamSynchronize(st));
-  if (e != cudaSuccess) {
-    cudaFreeAsync(mem, st);
-    return cuda_status(e);
-  }
   g->row_ptr.assign(rp, rp + (size_t)n + 1);
   int64_t hv = 0, hc = 0; // maxima over the variants (workspace sizing)
   for (int v = 0; v < kChunkVariants; ++v) {
@@ -783,6 +795,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
       return so;
     }
   }
+  mark("done");
   ctx->used += bytes;
   if (m_eff) *m_eff = me;
   out = std::move(g);
@@ -1728,6 +1741,27 @@ bc_status bc_debug_source(bc_ctx *ctx, bc_graph h, int32_t s, int32_t *d_out, ui
   o.schedule = BC_SCHED_PLAIN;
   o.delta_fp64 = 1;
   return bc_debug_sources(ctx, h, &s, 1, &o, d_out, sigma_out, delta_out);
+}
+
+bc_status bc_debug_graph(bc_ctx *ctx, bc_graph h, int32_t *row_ptr, int32_t *col_idx,
+                         int32_t *in_ptr, int32_t *in_idx) {
+  if (!ctx) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  GraphRec *g = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    g = find_graph(ctx, h);
+  }
+  if (!g) return BC_ERR_GRAPH;
+  const GraphDev &d = g->dev;
+  cudaStream_t st = ctx->stream;
+  const size_t np1 = sizeof(int32_t) * ((size_t)d.n + 1), mb = sizeof(int32_t) * (size_t)d.m;
+  if (row_ptr) BC_TRY(cudaMemcpyAsync(row_ptr, d.row_ptr, np1, cudaMemcpyDeviceToHost, st));
+  if (col_idx && mb) BC_TRY(cudaMemcpyAsync(col_idx, d.col_idx, mb, cudaMemcpyDeviceToHost, st));
+  if (in_ptr) BC_TRY(cudaMemcpyAsync(in_ptr, d.in_ptr, np1, cudaMemcpyDeviceToHost, st));
+  if (in_idx && mb) BC_TRY(cudaMemcpyAsync(in_idx, d.in_idx, mb, cudaMemcpyDeviceToHost, st));
+  BC_TRY(cudaStreamSynchronize(st));
+  return BC_OK;
 }
 
 bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, const bc_opts *opts,

@@ -186,13 +186,13 @@ cudaError_t launch_accumulate(double *acc, double *acc2, const double *add, cons
 // Graph preparation (bc_graph.cu).
 cudaError_t launch_check_csr(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int *flags,
                              cudaStream_t st);
-cudaError_t launch_in_degree(const int32_t *col_idx, int64_t m, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_in_degree(const int32_t *col_idx, int64_t m, int32_t n, int32_t *cnt,
+                             cudaStream_t st);
+cudaError_t launch_scan_inclusive(int32_t *a, int64_t len, cudaStream_t st);
 cudaError_t launch_in_scatter(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
                               int32_t *fill, int32_t *in_idx, cudaStream_t st);
-cudaError_t launch_sort_rows(const int32_t *in_ptr, int32_t *in_idx, const int32_t *warp_rows,
-                             int32_t n_warp_rows, const int32_t *block_rows, int32_t n_block_rows,
-                             cudaStream_t st);
-int sort_block_max();
+cudaError_t launch_sort_rows(const int32_t *in_ptr, int32_t *in_idx, int32_t n, int64_t m,
+                             int32_t *rows, int32_t *counts, cudaStream_t st);
 cudaError_t launch_graph_keys(const int32_t *row_ptr, const int32_t *col_idx,
                               const int32_t *in_ptr, int32_t n, int32_t *nchunks, int64_t *two,
                               unsigned long long *totals, cudaStream_t st);

@@ -198,6 +198,90 @@ def test_edge_cases(ctx):
     assert ei.value.status == bc.BC_ERR_GRAPH
 
 
+def check_resident(ctx, G, g):
+    """The graph as the library holds it equals the canonical CSR of g and
+    its transpose with ascending in-rows, bit for bit."""
+    rp, ci, ip, ii = ctx.debug_graph(G)
+    np.testing.assert_array_equal(rp, g.row_ptr)
+    np.testing.assert_array_equal(ci, g.col_idx)
+    src, dst = g.edges()
+    cnt = np.zeros(g.n + 1, dtype=np.int64)
+    np.add.at(cnt, np.asarray(dst, dtype=np.int64) + 1, 1)
+    np.testing.assert_array_equal(ip, np.cumsum(cnt))
+    np.testing.assert_array_equal(ii, np.asarray(src)[np.lexsort((src, dst))])
+
+
+def test_resident_graph_small_host_prepared(ctx):
+    for g in (bcgen.rmat(8, 8, seed=1), bcgen.star(300, "bi"), bcgen.csr_from_edges(5, [], [])):
+        G = ctx.create_graph(g.row_ptr, g.col_idx)
+        check_resident(ctx, G, g)
+        ctx.destroy_graph(G)
+
+
+def test_large_graphs_validated_and_canonicalised_on_the_device(ctx):
+    """Graphs above 2^18 edges are prepared on the device: a column id out of
+    range (past the end, or negative) is rejected, and rows with duplicates
+    and self-loops are canonicalised, with the same BC as the canonical
+    graph."""
+    import paper_1409_7764_gb300 as bc
+    g = bcgen.rmat(14, 20, seed=4)
+    assert g.m > 1 << 18
+    for bad in (g.n, -1):
+        ci = g.col_idx.copy()
+        ci[g.m // 2] = bad
+        with pytest.raises(bc.BCError) as ei:
+            ctx.create_graph(g.row_ptr, ci)
+        assert ei.value.status == bc.BC_ERR_GRAPH
+    src, dst = g.edges()
+    rs = np.random.default_rng(8)
+    dup = rs.integers(0, g.m, 30000)
+    loops = rs.integers(0, g.n, 2000)
+    raw = bcgen.raw_csr_from_edges(g.n, np.concatenate([src, src[dup], loops]),
+                                   np.concatenate([dst, dst[dup], loops]))
+    G = ctx.create_graph(raw.row_ptr, raw.col_idx)
+    assert G.m == g.m
+    check_resident(ctx, G, g)
+    G2 = ctx.create_graph(g.row_ptr, g.col_idx)
+    check_resident(ctx, G2, g)
+    ctx.destroy_graph(G2)
+    srcs = bcgen.sample_sources(g.n, 300, seed=2)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    assert_bc_close(ctx.sources(G, srcs, delta_fp64=True), ref, True)
+    d, sig, _ = ctx.debug_sources(G, srcs[:3], delta_fp64=True)
+    for j, s_ in enumerate(srcs[:3]):
+        od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, int(s_))
+        np.testing.assert_array_equal(d[j], od)
+        np.testing.assert_array_equal(sig[j], osig)
+    ctx.destroy_graph(G)
+
+
+def test_device_prepared_graph_with_long_in_rows(ctx):
+    """In-rows longer than the shared-memory sort (8192 entries) are sorted in
+    place on the device: a graph whose hubs have 10,000-40,000 in-edges gives
+    the oracle's BC and the oracle's path counts."""
+    n = 60000
+    rs = np.random.default_rng(3)
+    hubs = np.array([7, 500, 59999])
+    src = [rs.integers(0, n, 40000), rs.integers(0, n, 10000), rs.integers(0, n, 8193),
+           rs.integers(0, n, 300000)]
+    dst = [np.full(40000, hubs[0]), np.full(10000, hubs[1]), np.full(8193, hubs[2]),
+           rs.integers(0, n, 300000)]
+    g = bcgen.csr_from_edges(n, np.concatenate(src), np.concatenate(dst), name="long-in-rows")
+    assert g.m > 1 << 18
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    check_resident(ctx, G, g)
+    srcs = np.concatenate([bcgen.sample_sources(n, 200, seed=4), hubs]).astype(np.int32)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    for fp64 in (True, False):
+        assert_bc_close(ctx.sources(G, srcs, delta_fp64=fp64), ref, fp64)
+    d, sig, _ = ctx.debug_sources(G, srcs[:4], delta_fp64=True)
+    for j, s_ in enumerate(srcs[:4]):
+        od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, int(s_))
+        np.testing.assert_array_equal(d[j], od)
+        np.testing.assert_array_equal(sig[j], osig)
+    ctx.destroy_graph(G)
+
+
 def test_canonicalisation_in_library(ctx):
     rs = np.random.default_rng(5)
     n = 300
