@@ -579,7 +579,9 @@ def run_many(args):
                    "scales": "6..12 uniform", "edge_factors": "4..16 uniform",
                    "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs)),
                    "l2": "flushed between timed steps (512 MiB write)",
-                   "schedule": "one persistent launch, one block per graph, 64 sources/batch"},
+                   "schedule": "one persistent launch, one block per graph, "
+                               + (f"{args.batch_k} sources per batch" if args.batch_k > 0
+                                  else "64, 128 or 256 sources per batch by graph size")},
         "roofline": {"bound": "hbm", "achieved": algo / (ms_step / 1e3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": algo / (ms_step / 1e3) / 1e9 / peak,
                      "traffic": None, "peak_kind": peak_kind, "kernel": "many_kernel"},

@@ -326,6 +326,15 @@ struct bc_ctx {
   int grid_dense[2] = {0, 0};
   int grid_many[2] = {0, 0};
   int grid_plain[2] = {0, 0};
+  // Stream-ordered allocations of this context (graphs, job buffers, prep
+  // scratch) come from its own pool, which keeps up to kPoolKeepBytes of
+  // freed memory mapped: with the default pool's threshold of 0 every
+  // synchronisation returns freed memory to the system and the next
+  // allocation maps it again (about 0.1 ms per graph or job).
+  cudaMemPool_t pool = nullptr;
+  // pinned staging for the single upload of a host-prepared graph
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
 
   std::mutex mu;
   std::unordered_map<int64_t, std::unique_ptr<GraphRec>> graphs;
@@ -350,6 +359,13 @@ struct bc_ctx {
 };
 
 namespace {
+
+constexpr uint64_t kPoolKeepBytes = (uint64_t)2 << 30;
+
+// Stream-ordered allocation from the context's pool.
+template <typename T> cudaError_t pool_alloc(bc_ctx *ctx, T **p, size_t bytes, cudaStream_t st) {
+  return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, ctx->pool, st);
+}
 
 // One BC job: a graph, a source list and options; runs on one stream.
 struct JobRec {
@@ -553,7 +569,7 @@ bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *
   if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
   cudaStream_t st = ctx->stream;
   void *mem = nullptr;
-  BC_TRY(cudaMallocAsync(&mem, bytes, st));
+  BC_TRY(pool_alloc(ctx, &mem, bytes, st));
   Carver c2;
   c2.base = static_cast<char *>(mem);
   int32_t *d_rp = c2.take<int32_t>((size_t)n + 1);
@@ -562,16 +578,31 @@ bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *
   int32_t *d_ii = c2.take<int32_t>((size_t)me);
   int32_t *d_nc = c2.take<int32_t>((size_t)n * kChunkVariants);
   int32_t *d_ord = c2.take<int32_t>((size_t)n);
+  // the arrays laid out as on the device in pinned staging, one copy
   cudaError_t e = cudaSuccess;
-  auto up = [&](void *dst, const void *src, size_t b) {
-    if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st);
-  };
-  up(d_rp, rp, sizeof(int32_t) * ((size_t)n + 1));
-  up(d_ci, ci, sizeof(int32_t) * (size_t)me);
-  up(d_ip, ip.data(), sizeof(int32_t) * ((size_t)n + 1));
-  up(d_ii, ii.data(), sizeof(int32_t) * (size_t)me);
-  up(d_nc, nc.data(), sizeof(int32_t) * (size_t)n * kChunkVariants);
-  up(d_ord, ord.data(), sizeof(int32_t) * (size_t)n);
+  if (ctx->stage_bytes < bytes) {
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    const size_t want = std::max<size_t>(bytes, (size_t)1 << 20);
+    e = cudaMallocHost(&ctx->stage, want);
+    if (e == cudaSuccess) ctx->stage_bytes = want;
+  }
+  if (e == cudaSuccess) {
+    Carver c3;
+    c3.base = static_cast<char *>(ctx->stage);
+    auto put = [&](const int32_t *src, size_t count) {
+      int32_t *dst = c3.take<int32_t>(count);
+      if (count) std::memcpy(dst, src, sizeof(int32_t) * count);
+    };
+    put(rp, (size_t)n + 1);
+    put(ci, (size_t)me);
+    put(ip.data(), (size_t)n + 1);
+    put(ii.data(), (size_t)me);
+    put(nc.data(), (size_t)n * kChunkVariants);
+    put(ord.data(), (size_t)n);
+    e = cudaMemcpyAsync(mem, ctx->stage, c3.off, cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFreeAsync(mem, st);
@@ -640,7 +671,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   auto alloc_upload = [&](Block &b, const int32_t *rp, const int32_t *ci, int64_t me) -> bc_status {
     carve(b, me, nullptr);
     if (ctx->used + b.bytes > ctx->budget) return BC_ERR_ADMISSION;
-    BC_TRY(cudaMallocAsync(&b.mem, b.bytes, st));
+    BC_TRY(pool_alloc(ctx, &b.mem, b.bytes, st));
     carve(b, me, static_cast<char *>(b.mem));
     cudaError_t r = cudaMemcpyAsync(b.rp, rp, sizeof(int32_t) * ((size_t)n + 1),
                                     cudaMemcpyHostToDevice, st);
@@ -661,18 +692,19 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
   auto prepare = [&](Block &b, int64_t me, int (&flags)[2], std::vector<int64_t> &two,
                      unsigned long long (&totals)[2 * kChunkVariants]) -> cudaError_t {
     int *d_flags = nullptr;
-    int32_t *d_fill = nullptr, *d_rows = nullptr;
+    int32_t *d_fill = nullptr, *d_rows = nullptr, *d_scan = nullptr;
     int64_t *d_two = nullptr;
     unsigned long long *d_tot = nullptr;
     cudaError_t e = cudaSuccess;
     auto step = [&](cudaError_t r) {
       if (e == cudaSuccess) e = r;
     };
-    step(cudaMallocAsync(&d_flags, sizeof(int) * 2 + 3 * sizeof(int32_t), st));
-    step(cudaMallocAsync(&d_fill, sizeof(int32_t) * ((size_t)n + 1), st));
-    step(cudaMallocAsync(&d_rows, sizeof(int32_t) * 3 * (size_t)n, st));
-    step(cudaMallocAsync(&d_two, sizeof(int64_t) * (size_t)n, st));
-    step(cudaMallocAsync(&d_tot, sizeof(totals), st));
+    step(pool_alloc(ctx, &d_flags, sizeof(int) * 2 + 3 * sizeof(int32_t), st));
+    step(pool_alloc(ctx, &d_fill, sizeof(int32_t) * ((size_t)n + 1), st));
+    step(pool_alloc(ctx, &d_rows, sizeof(int32_t) * 3 * (size_t)n, st));
+    step(pool_alloc(ctx, &d_two, sizeof(int64_t) * (size_t)n, st));
+    step(pool_alloc(ctx, &d_tot, sizeof(totals), st));
+    step(pool_alloc(ctx, &d_scan, sizeof(int32_t) * (size_t)scan_scratch_elems((int64_t)n + 1), st));
     if (e == cudaSuccess) {
       int32_t *d_rcnt = reinterpret_cast<int32_t *>(d_flags + 2);
       step(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2, st));
@@ -681,7 +713,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
       step(cudaMemsetAsync(b.ip, 0, sizeof(int32_t) * ((size_t)n + 1), st));
       step(launch_in_degree(b.ci, me, n, b.ip, st));
       mark("checked, in-degrees counted");
-      step(launch_scan_inclusive(b.ip, (int64_t)n + 1, st));
+      step(launch_scan_inclusive(b.ip, (int64_t)n + 1, d_scan, st));
       step(cudaMemcpyAsync(d_fill, b.ip, sizeof(int32_t) * ((size_t)n + 1),
                            cudaMemcpyDeviceToDevice, st));
       mark("in-degrees scanned");
@@ -703,6 +735,7 @@ bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_id
     if (d_rows) cudaFreeAsync(d_rows, st);
     if (d_two) cudaFreeAsync(d_two, st);
     if (d_tot) cudaFreeAsync(d_tot, st);
+    if (d_scan) cudaFreeAsync(d_scan, st);
     step(cudaStreamSynchronize(st));
     mark("flags, keys and totals read");
     return e;
@@ -974,10 +1007,10 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
                        [g](int32_t a, int32_t b) { return batch_key_less(*g, a, b); });
     }
   }
-  BC_TRY(cudaMallocAsync(&j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));
-  BC_TRY(cudaMallocAsync(&j->d_bc, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
-  BC_TRY(cudaMallocAsync(&j->d_ovf, (size_t)std::max<int64_t>(k, 1), st));
-  BC_TRY(cudaMallocAsync(&j->d_cnt, sizeof(unsigned long long) * CNT_N, st));
+  BC_TRY(pool_alloc(ctx, &j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));
+  BC_TRY(pool_alloc(ctx, &j->d_bc, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
+  BC_TRY(pool_alloc(ctx, &j->d_ovf, (size_t)std::max<int64_t>(k, 1), st));
+  BC_TRY(pool_alloc(ctx, &j->d_cnt, sizeof(unsigned long long) * CNT_N, st));
   if (k) BC_TRY(cudaMemcpyAsync(j->d_src, j->h_src, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st));
   BC_TRY(cudaMemsetAsync(j->d_bc, 0, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
   BC_TRY(cudaMemsetAsync(j->d_ovf, 0, (size_t)std::max<int64_t>(k, 1), st));
@@ -988,7 +1021,7 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   BC_TRY(cudaEventCreateWithFlags(&j->evdone, cudaEventDisableTiming));
 
   if (j->acc_sum) {
-    BC_TRY(cudaMallocAsync(&j->d_bc2, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
+    BC_TRY(pool_alloc(ctx, &j->d_bc2, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
     BC_TRY(cudaMemsetAsync(j->d_bc2, 0, sizeof(double) * (size_t)std::max<int64_t>(n, 1), st));
   }
   KParams p;
@@ -1010,7 +1043,7 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
     // per-step timing of one batch (index BC_TRACE, -1 = last) to stderr
     j->trace_batch = std::atoll(tr);
     if (j->trace_batch < 0) j->trace_batch = (k + kb - 1) / kb - 1;
-    BC_TRY(cudaMallocAsync(&j->d_trace, sizeof(unsigned long long) * 4 * kTraceCap, st));
+    BC_TRY(pool_alloc(ctx, &j->d_trace, sizeof(unsigned long long) * 4 * kTraceCap, st));
     BC_TRY(cudaMemsetAsync(j->d_trace, 0, sizeof(unsigned long long) * 4 * kTraceCap, st));
     BC_TRY(cudaMallocHost(&j->h_trace, sizeof(unsigned long long) * 4 * kTraceCap));
   }
@@ -1363,6 +1396,15 @@ bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx
   size_t freeb = 0, totalb = 0;
   BC_TRY(cudaMemGetInfo(&freeb, &totalb));
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)freeb);
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    BC_TRY(cudaMemPoolCreate(&ctx->pool, &props));
+    uint64_t keep = std::min<uint64_t>(kPoolKeepBytes, ctx->budget);
+    BC_TRY(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  }
   BC_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
   for (int f = 0; f < 2; ++f) {
     for (int wi = 0; wi < 3; ++wi) {
@@ -1402,6 +1444,8 @@ bc_status bc_shutdown(bc_ctx *ctx) {
   for (auto &kv : ctx->graphs) cudaFreeAsync(kv.second->mem, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   ctx->graphs.clear();
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  if (ctx->stage) cudaFreeHost(ctx->stage);
   for (int i = 0; i < kMaxSlots; ++i)
     if (ctx->slot_stream[i]) cudaStreamDestroy(ctx->slot_stream[i]);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1475,16 +1519,17 @@ namespace {
 // Device buffers of the sampled-source estimator: running sums of the
 // per-source terms and of their squares, the estimate and its error.
 struct EstimateBufs {
+  bc_ctx *ctx = nullptr;
   cudaStream_t st = nullptr;
   double *sum = nullptr, *sumsq = nullptr, *est = nullptr, *err = nullptr;
   unsigned long long *stat = nullptr;
   bc_status alloc(int64_t n) {
     const size_t b = sizeof(double) * (size_t)std::max<int64_t>(n, 1);
-    BC_TRY(cudaMallocAsync(&sum, b, st));
-    BC_TRY(cudaMallocAsync(&sumsq, b, st));
-    BC_TRY(cudaMallocAsync(&est, b, st));
-    BC_TRY(cudaMallocAsync(&err, b, st));
-    BC_TRY(cudaMallocAsync(&stat, sizeof(unsigned long long), st));
+    BC_TRY(pool_alloc(ctx, &sum, b, st));
+    BC_TRY(pool_alloc(ctx, &sumsq, b, st));
+    BC_TRY(pool_alloc(ctx, &est, b, st));
+    BC_TRY(pool_alloc(ctx, &err, b, st));
+    BC_TRY(pool_alloc(ctx, &stat, sizeof(unsigned long long), st));
     BC_TRY(cudaMemsetAsync(sum, 0, b, st));
     BC_TRY(cudaMemsetAsync(sumsq, 0, b, st));
     return BC_OK;
@@ -1534,6 +1579,7 @@ bc_status bc_sources_estimate(bc_ctx *ctx, bc_graph h, const int32_t *src, int32
   o.scale_sampled = 0; // the estimate carries its own n/k
   const int64_t n = g->dev.n;
   EstimateBufs b;
+  b.ctx = ctx;
   b.st = ctx->stream;
   s = b.alloc(n);
   if (s != BC_OK) return s;
@@ -1565,6 +1611,7 @@ bc_status bc_sources_adaptive(bc_ctx *ctx, bc_graph h, const int32_t *order, int
   const int64_t n = g->dev.n;
   const double factor = estimate_factor(o, n);
   EstimateBufs b;
+  b.ctx = ctx;
   b.st = ctx->stream;
   s = b.alloc(n);
   if (s != BC_OK) return s;
@@ -1712,9 +1759,9 @@ bc_status bc_debug_sources(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t 
   const size_t cells = (size_t)k * (size_t)g->dev.n;
   DebugOut dbg;
   cudaStream_t st = ctx->stream;
-  BC_TRY(cudaMallocAsync(&dbg.d, sizeof(int32_t) * std::max<size_t>(cells, 1), st));
-  BC_TRY(cudaMallocAsync(&dbg.sigma, sizeof(uint64_t) * std::max<size_t>(cells, 1), st));
-  BC_TRY(cudaMallocAsync(&dbg.delta, sizeof(double) * std::max<size_t>(cells, 1), st));
+  BC_TRY(pool_alloc(ctx, &dbg.d, sizeof(int32_t) * std::max<size_t>(cells, 1), st));
+  BC_TRY(pool_alloc(ctx, &dbg.sigma, sizeof(uint64_t) * std::max<size_t>(cells, 1), st));
+  BC_TRY(pool_alloc(ctx, &dbg.delta, sizeof(double) * std::max<size_t>(cells, 1), st));
   BC_TRY(cudaMemsetAsync(dbg.d, 0xff, sizeof(int32_t) * cells, st));
   BC_TRY(cudaMemsetAsync(dbg.sigma, 0, sizeof(uint64_t) * cells, st));
   BC_TRY(cudaMemsetAsync(dbg.delta, 0, sizeof(double) * cells, st));
@@ -1808,9 +1855,9 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
   double *d_out = nullptr;
   int8_t *d_ovf = nullptr;
   unsigned long long *d_cnt = nullptr;
-  BC_TRY(cudaMallocAsync(&d_out, sizeof(double) * (size_t)std::max<int64_t>(total_n, 1), st));
-  BC_TRY(cudaMallocAsync(&d_ovf, (size_t)std::max<int64_t>(total_n, 1), st));
-  BC_TRY(cudaMallocAsync(&d_cnt, sizeof(unsigned long long) * (CNT_N + 1), st));
+  BC_TRY(pool_alloc(ctx, &d_out, sizeof(double) * (size_t)std::max<int64_t>(total_n, 1), st));
+  BC_TRY(pool_alloc(ctx, &d_ovf, (size_t)std::max<int64_t>(total_n, 1), st));
+  BC_TRY(pool_alloc(ctx, &d_cnt, sizeof(unsigned long long) * (CNT_N + 1), st));
   BC_TRY(cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)std::max<int64_t>(total_n, 1), st));
   BC_TRY(cudaMemsetAsync(d_ovf, 0, (size_t)std::max<int64_t>(total_n, 1), st));
   BC_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * (CNT_N + 1), st));
@@ -1857,7 +1904,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     for (int32_t i = 0; i < max_n; ++i) iota[(size_t)i] = i;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
-      if (e == cudaSuccess) e = cudaMallocAsync(ptr, std::max<size_t>(bytes, 1), st);
+      if (e == cudaSuccess) e = pool_alloc(ctx, ptr, std::max<size_t>(bytes, 1), st);
     };
     alloc(reinterpret_cast<void **>(&d_works), sizeof(Work) * works.size());
     alloc(reinterpret_cast<void **>(&d_graphs), sizeof(GraphDev) * table.size());

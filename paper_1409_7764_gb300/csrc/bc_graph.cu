@@ -340,24 +340,33 @@ cudaError_t launch_in_degree(const int32_t *col_idx, int64_t m, int32_t n, int32
   return cudaGetLastError();
 }
 
+// Scratch (int32 elements) the scan of len elements needs: the tile totals
+// of every level.
+int64_t scan_scratch_elems(int64_t len) {
+  int64_t total = 0;
+  while (len > 1) {
+    len = (len + kScanTile - 1) / kScanTile;
+    total += len;
+  }
+  return total > 0 ? total : 1;
+}
+
 // In-place inclusive scan of a[0, len): tiles, then (recursively) the tile
-// totals, then the carry into each tile.
-cudaError_t launch_scan_inclusive(int32_t *a, int64_t len, cudaStream_t st) {
+// totals, then the carry into each tile.  scratch holds
+// scan_scratch_elems(len) int32.
+cudaError_t launch_scan_inclusive(int32_t *a, int64_t len, int32_t *scratch, cudaStream_t st) {
   if (len <= 0) return cudaSuccess;
   const int64_t tiles = (len + kScanTile - 1) / kScanTile;
-  int32_t *sums = nullptr;
-  cudaError_t e = cudaMallocAsync(&sums, sizeof(int32_t) * (size_t)tiles, st);
-  if (e != cudaSuccess) return e;
+  int32_t *sums = scratch;
   scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(a, len, sums);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && tiles > 1) {
-    e = launch_scan_inclusive(sums, tiles, st);
+    e = launch_scan_inclusive(sums, tiles, scratch + tiles, st);
     if (e == cudaSuccess) {
       scan_add_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(a, len, sums);
       e = cudaGetLastError();
     }
   }
-  cudaFreeAsync(sums, st);
   return e;
 }
 

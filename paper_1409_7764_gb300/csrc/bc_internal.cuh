@@ -188,7 +188,8 @@ cudaError_t launch_check_csr(const int32_t *row_ptr, const int32_t *col_idx, int
                              cudaStream_t st);
 cudaError_t launch_in_degree(const int32_t *col_idx, int64_t m, int32_t n, int32_t *cnt,
                              cudaStream_t st);
-cudaError_t launch_scan_inclusive(int32_t *a, int64_t len, cudaStream_t st);
+int64_t scan_scratch_elems(int64_t len);
+cudaError_t launch_scan_inclusive(int32_t *a, int64_t len, int32_t *scratch, cudaStream_t st);
 cudaError_t launch_in_scatter(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
                               int32_t *fill, int32_t *in_idx, cudaStream_t st);
 cudaError_t launch_sort_rows(const int32_t *in_ptr, int32_t *in_idx, int32_t n, int64_t m,
