@@ -542,7 +542,7 @@ def run_many(args):
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2 = [ctx.create_graph(g.row_ptr, g.col_idx) for g in graphs]
+        h2 = ctx.create_graphs([(g.row_ptr, g.col_idx) for g in graphs])
         ctx.exact_many(h2, delta_fp64=fp64, batch_k=max(args.batch_k, 0))
         for h in h2:
             ctx.destroy_graph(h)

@@ -144,6 +144,20 @@ bc_status bc_shutdown(bc_ctx *ctx);
 bc_status bc_create_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx,
                           int32_t n, int64_t m, bc_graph *out, int64_t *m_effective);
 
+/* Uploads `count` graphs at once, as bc_create_graph does one by one:
+ * graph i is row_ptrs[i] (ns[i]+1 entries) and col_idxs[i] (ms[i] entries),
+ * host memory, validated and canonicalised the same way.  Graphs of up to
+ * 2^18 edges are prepared on host threads in parallel and uploaded in
+ * groups (one transfer per graph, one synchronisation per group), which is
+ * what makes creating many small graphs cheap; larger ones take the device
+ * path one by one.  All or nothing: on any error no graph is kept and the
+ * status is that of the first failing step (BC_ERR_GRAPH for a malformed
+ * graph, BC_ERR_ADMISSION past the HBM budget).  out[i] receives graph i's
+ * handle and m_effective[i] (may be NULL) its canonical edge count. */
+bc_status bc_create_graphs(bc_ctx *ctx, int32_t count, const int32_t *const *row_ptrs,
+                           const int32_t *const *col_idxs, const int32_t *ns, const int64_t *ms,
+                           bc_graph *out, int64_t *m_effective);
+
 /* Frees a graph.  Fails with BC_ERR_ARG while a submitted job still uses it. */
 bc_status bc_destroy_graph(bc_ctx *ctx, bc_graph g);
 

@@ -139,6 +139,23 @@ class Context:
                                          ctypes.byref(me)), "bc_create_graph")
         return Graph(g.value, n, me.value)
 
+    def create_graphs(self, graphs) -> list:
+        """Uploads many graphs with one call; graphs is a sequence of
+        (row_ptr, col_idx) pairs (host arrays).  All or nothing."""
+        arrs = [(_i32(rp), _i32(ci)) for rp, ci in graphs]
+        count = len(arrs)
+        if count == 0:
+            return []
+        rps = (ctypes.c_void_p * count)(*[rp.ctypes.data for rp, _ in arrs])
+        cis = (ctypes.c_void_p * count)(*[ci.ctypes.data if ci.size else None for _, ci in arrs])
+        ns = np.array([rp.shape[0] - 1 for rp, _ in arrs], dtype=np.int32)
+        ms = np.array([ci.shape[0] for _, ci in arrs], dtype=np.int64)
+        out = np.empty(count, dtype=np.int64)
+        meff = np.empty(count, dtype=np.int64)
+        _check(self._lib.bc_create_graphs(self._h, count, rps, cis, ns.ctypes.data, ms.ctypes.data,
+                                          out.ctypes.data, meff.ctypes.data), "bc_create_graphs")
+        return [Graph(int(h), int(n), int(me)) for h, n, me in zip(out, ns, meff)]
+
     def destroy_graph(self, g: Graph):
         _check(self._lib.bc_destroy_graph(self._h, g.handle), "bc_destroy_graph")
 

@@ -31,7 +31,7 @@ BC_SCHED_BATCH_DENSE = 4
 # every symbol include/bc_gb300.h declares
 EXPORTED = [
     "bc_init", "bc_shutdown", "bc_create_graph", "bc_destroy_graph", "bc_exact", "bc_sources",
-    "bc_submit", "bc_poll", "bc_wait", "bc_last_stats", "bc_debug_source", "bc_debug_sources", "bc_debug_graph",
+    "bc_submit", "bc_poll", "bc_wait", "bc_last_stats", "bc_debug_source", "bc_debug_sources", "bc_debug_graph", "bc_create_graphs",
     "bc_exact_many", "bc_debug_inject_barrier_skip", "bc_status_str", "bc_sources_noalloc",
     "bc_sources_estimate", "bc_sources_adaptive", "bc_last_overflow_sources",
 ]
@@ -98,6 +98,7 @@ def load(path: str | None = None):
         "bc_last_stats": ([vp, ctypes.POINTER(bc_stats)], ctypes.c_int),
         "bc_debug_source": ([vp, i64, i32, vp, vp, vp], ctypes.c_int),
         "bc_debug_graph": ([vp, i64, vp, vp, vp, vp], ctypes.c_int),
+        "bc_create_graphs": ([vp, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "bc_debug_sources": ([vp, i64, vp, i32, ctypes.POINTER(bc_opts), vp, vp, vp],
                              ctypes.c_int),
         "bc_exact_many": ([vp, vp, i32, ctypes.POINTER(bc_opts), vp], ctypes.c_int),

@@ -488,12 +488,32 @@ bc_status ensure_order(GraphRec *g, cudaStream_t st) {
 // synchronisations (many small graphs are created one after another).
 constexpr int64_t kHostPrepMaxEdges = (int64_t)1 << 18;
 
-// Host preparation of a small graph (offsets already checked): validation,
-// canonicalisation, in-CSR by counting sort, chunk counts, two-hop keys and
-// the batch order, then one upload.
-bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx,
-                            int32_t n, int64_t m, std::unique_ptr<GraphRec> &out,
-                            int64_t *m_eff) {
+// A graph prepared on the host (offsets already checked): validated,
+// canonicalised, in-CSR by counting sort, chunk counts, two-hop keys and the
+// batch order.  Touches no CUDA state, so several run at once.
+struct HostPrep {
+  int32_t n = 0;
+  int64_t me = 0;
+  size_t bytes = 0;                  // device block size
+  std::vector<int32_t> crp, cci;     // canonical CSR when the input was not canonical
+  const int32_t *rp = nullptr, *ci = nullptr;
+  std::vector<int32_t> ip, ii, nc, ord;
+  std::vector<int64_t> two;
+  int64_t heavy_v[kChunkVariants] = {}, heavy_c[kChunkVariants] = {}, hv = 0, hc = 0;
+};
+
+// The device block of a graph: offsets of its arrays (Carver order).
+template <typename F> void block_layout(int32_t n, int64_t me, F &&take) {
+  take((size_t)n + 1);             // row_ptr
+  take((size_t)me);                // col_idx
+  take((size_t)n + 1);             // in_ptr
+  take((size_t)me);                // in_idx
+  take((size_t)n * kChunkVariants); // nchunks
+  take((size_t)n);                 // order
+}
+
+bc_status prep_host(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t m,
+                    HostPrep &h) {
   bool canonical = true;
   for (int32_t v = 0; v < n; ++v)
     for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
@@ -501,12 +521,13 @@ bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *
       if (x < 0 || x >= n) return BC_ERR_GRAPH;
       if (x == v || (e > row_ptr[v] && x <= col_idx[e - 1])) canonical = false;
     }
-  std::vector<int32_t> crp, cci;
-  const int32_t *rp = row_ptr, *ci = col_idx;
+  h.n = n;
+  h.rp = row_ptr;
+  h.ci = col_idx;
   if (!canonical) {
-    crp.resize((size_t)n + 1);
-    cci.reserve((size_t)m);
-    crp[0] = 0;
+    h.crp.resize((size_t)n + 1);
+    h.cci.reserve((size_t)m);
+    h.crp[0] = 0;
     std::vector<int32_t> row;
     for (int32_t v = 0; v < n; ++v) {
       row.assign(col_idx + row_ptr[v], col_idx + row_ptr[v + 1]);
@@ -514,128 +535,160 @@ bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *
       int32_t prev = -1;
       for (int32_t x : row)
         if (x != v && x != prev) {
-          cci.push_back(x);
+          h.cci.push_back(x);
           prev = x;
         }
-      crp[(size_t)v + 1] = (int32_t)cci.size();
+      h.crp[(size_t)v + 1] = (int32_t)h.cci.size();
     }
-    rp = crp.data();
-    ci = cci.data();
+    h.rp = h.crp.data();
+    h.ci = h.cci.data();
   }
+  const int32_t *rp = h.rp, *ci = h.ci;
   const int64_t me = (int64_t)rp[n];
+  h.me = me;
   // in-CSR by counting sort over destinations (sources stay ascending)
-  std::vector<int32_t> ip((size_t)n + 1, 0), ii((size_t)std::max<int64_t>(me, 1));
-  for (int64_t e = 0; e < me; ++e) ip[(size_t)ci[e] + 1]++;
-  for (int32_t v = 0; v < n; ++v) ip[(size_t)v + 1] += ip[v];
+  h.ip.assign((size_t)n + 1, 0);
+  h.ii.resize((size_t)std::max<int64_t>(me, 1));
+  for (int64_t e = 0; e < me; ++e) h.ip[(size_t)ci[e] + 1]++;
+  for (int32_t v = 0; v < n; ++v) h.ip[(size_t)v + 1] += h.ip[v];
   {
-    std::vector<int32_t> fill(ip.begin(), ip.end() - 1);
+    std::vector<int32_t> fill(h.ip.begin(), h.ip.end() - 1);
     for (int32_t v = 0; v < n; ++v)
-      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) ii[(size_t)fill[ci[e]]++] = v;
+      for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) h.ii[(size_t)fill[ci[e]]++] = v;
   }
-  auto g = std::make_unique<GraphRec>();
-  std::vector<int32_t> nc((size_t)n * kChunkVariants, 0);
-  int64_t hv = 0, hc = 0;
+  h.nc.assign((size_t)n * kChunkVariants, 0);
   for (int c = 0; c < kChunkVariants; ++c) {
     const int64_t ch = kChunkCandidates[c];
     for (int32_t v = 0; v < n; ++v) {
-      const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (ip[(size_t)v + 1] - ip[v]);
+      const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (h.ip[(size_t)v + 1] - h.ip[v]);
       if (cost > ch) {
         const int32_t k = (int32_t)((cost + ch - 1) / ch);
-        nc[(size_t)c * n + v] = k;
-        g->heavy_v[c]++;
-        g->heavy_c[c] += k;
+        h.nc[(size_t)c * n + v] = k;
+        h.heavy_v[c]++;
+        h.heavy_c[c] += k;
       }
     }
-    hv = std::max(hv, g->heavy_v[c]);
-    hc = std::max(hc, g->heavy_c[c]);
+    h.hv = std::max(h.hv, h.heavy_v[c]);
+    h.hc = std::max(h.hc, h.heavy_c[c]);
   }
-  g->row_ptr.assign(rp, rp + (size_t)n + 1);
-  g->two.assign((size_t)n, 0);
+  h.two.assign((size_t)n, 0);
   for (int32_t v = 0; v < n; ++v) {
     int64_t t = 0;
     for (int32_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) t += rp[(size_t)ci[e] + 1] - rp[ci[e]];
-    g->two[(size_t)v] = t;
+    h.two[(size_t)v] = t;
   }
-  std::vector<int32_t> ord = batch_order(g->row_ptr, g->two, n);
-  // one allocation, one upload
+  {
+    std::vector<int32_t> rpv(rp, rp + (size_t)n + 1);
+    h.ord = batch_order(rpv, h.two, n);
+  }
   Carver c;
-  (void)c.take<int32_t>((size_t)n + 1);
-  (void)c.take<int32_t>((size_t)me);
-  (void)c.take<int32_t>((size_t)n + 1);
-  (void)c.take<int32_t>((size_t)me);
-  (void)c.take<int32_t>((size_t)n * kChunkVariants);
-  (void)c.take<int32_t>((size_t)n);
-  const size_t bytes = align_up(c.off, 256);
-  if (ctx->used + bytes > ctx->budget) return BC_ERR_ADMISSION;
+  block_layout(n, me, [&](size_t cnt) { (void)c.take<int32_t>(cnt); });
+  h.bytes = align_up(c.off, 256);
+  return BC_OK;
+}
+
+// Writes the device image of a prepared graph (its arrays at their block
+// offsets) to dst, which holds h.bytes.
+void prep_image(const HostPrep &h, char *dst) {
+  Carver c;
+  c.base = dst;
+  const int32_t *src[6] = {h.rp, h.ci, h.ip.data(), h.ii.data(), h.nc.data(), h.ord.data()};
+  int a = 0;
+  block_layout(h.n, h.me, [&](size_t cnt) {
+    int32_t *d = c.take<int32_t>(cnt);
+    const size_t real = a == 1 || a == 3 ? (size_t)h.me : cnt; // edge arrays may be empty
+    if (real) std::memcpy(d, src[a], sizeof(int32_t) * real);
+    ++a;
+  });
+}
+
+// The resident graph of a prepared one whose image was copied to mem.
+std::unique_ptr<GraphRec> prep_graph(HostPrep &h, void *mem) {
+  auto g = std::make_unique<GraphRec>();
+  int32_t *ptr[6];
+  Carver c;
+  c.base = static_cast<char *>(mem);
+  int a = 0;
+  block_layout(h.n, h.me, [&](size_t cnt) { ptr[a++] = c.take<int32_t>(cnt); });
+  const int32_t n = h.n;
+  for (int v = 0; v < kChunkVariants; ++v) {
+    g->heavy_v[v] = h.heavy_v[v];
+    g->heavy_c[v] = h.heavy_c[v];
+    g->nch_variant[v] = ptr[4] + (size_t)v * n;
+  }
+  g->row_ptr.assign(h.rp, h.rp + (size_t)n + 1);
+  g->two = std::move(h.two);
+  g->mem = mem;
+  g->bytes = h.bytes;
+  g->dev.n = n;
+  g->dev.m = h.me;
+  g->dev.row_ptr = ptr[0];
+  g->dev.col_idx = ptr[1];
+  g->dev.in_ptr = ptr[2];
+  g->dev.in_idx = ptr[3];
+  g->dev.nchunks = ptr[4];
+  g->dev.heavy_vertices = h.hv;
+  g->dev.heavy_chunks = h.hc;
+  g->dev.order = ptr[5];
+  g->d_order = ptr[5];
+  g->order = std::move(h.ord);
+  return g;
+}
+
+// Room for `bytes` in the context's pinned staging buffer.
+bc_status ensure_stage(bc_ctx *ctx, size_t bytes) {
+  if (ctx->stage_bytes >= bytes) return BC_OK;
+  if (ctx->stage) cudaFreeHost(ctx->stage);
+  ctx->stage = nullptr;
+  ctx->stage_bytes = 0;
+  const size_t want = std::max<size_t>(bytes, (size_t)1 << 20);
+  BC_TRY(cudaMallocHost(&ctx->stage, want));
+  ctx->stage_bytes = want;
+  return BC_OK;
+}
+
+// Host preparation of a small graph, then one upload of its image from the
+// pinned staging buffer.
+bc_status build_graph_small(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx,
+                            int32_t n, int64_t m, std::unique_ptr<GraphRec> &out,
+                            int64_t *m_eff) {
+  HostPrep h;
+  bc_status s = prep_host(row_ptr, col_idx, n, m, h);
+  if (s != BC_OK) return s;
+  if (ctx->used + h.bytes > ctx->budget) return BC_ERR_ADMISSION;
+  s = ensure_stage(ctx, h.bytes);
+  if (s != BC_OK) return s;
+  prep_image(h, static_cast<char *>(ctx->stage));
   cudaStream_t st = ctx->stream;
   void *mem = nullptr;
-  BC_TRY(pool_alloc(ctx, &mem, bytes, st));
-  Carver c2;
-  c2.base = static_cast<char *>(mem);
-  int32_t *d_rp = c2.take<int32_t>((size_t)n + 1);
-  int32_t *d_ci = c2.take<int32_t>((size_t)me);
-  int32_t *d_ip = c2.take<int32_t>((size_t)n + 1);
-  int32_t *d_ii = c2.take<int32_t>((size_t)me);
-  int32_t *d_nc = c2.take<int32_t>((size_t)n * kChunkVariants);
-  int32_t *d_ord = c2.take<int32_t>((size_t)n);
-  // the arrays laid out as on the device in pinned staging, one copy
-  cudaError_t e = cudaSuccess;
-  if (ctx->stage_bytes < bytes) {
-    if (ctx->stage) cudaFreeHost(ctx->stage);
-    ctx->stage = nullptr;
-    ctx->stage_bytes = 0;
-    const size_t want = std::max<size_t>(bytes, (size_t)1 << 20);
-    e = cudaMallocHost(&ctx->stage, want);
-    if (e == cudaSuccess) ctx->stage_bytes = want;
-  }
-  if (e == cudaSuccess) {
-    Carver c3;
-    c3.base = static_cast<char *>(ctx->stage);
-    auto put = [&](const int32_t *src, size_t count) {
-      int32_t *dst = c3.take<int32_t>(count);
-      if (count) std::memcpy(dst, src, sizeof(int32_t) * count);
-    };
-    put(rp, (size_t)n + 1);
-    put(ci, (size_t)me);
-    put(ip.data(), (size_t)n + 1);
-    put(ii.data(), (size_t)me);
-    put(nc.data(), (size_t)n * kChunkVariants);
-    put(ord.data(), (size_t)n);
-    e = cudaMemcpyAsync(mem, ctx->stage, c3.off, cudaMemcpyHostToDevice, st);
-  }
+  BC_TRY(pool_alloc(ctx, &mem, h.bytes, st));
+  cudaError_t e = cudaMemcpyAsync(mem, ctx->stage, h.bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFreeAsync(mem, st);
     return cuda_status(e);
   }
-  for (int v = 0; v < kChunkVariants; ++v) g->nch_variant[v] = d_nc + (size_t)v * n;
-  g->mem = mem;
-  g->bytes = bytes;
-  g->dev.n = n;
-  g->dev.m = me;
-  g->dev.row_ptr = d_rp;
-  g->dev.col_idx = d_ci;
-  g->dev.in_ptr = d_ip;
-  g->dev.in_idx = d_ii;
-  g->dev.nchunks = d_nc;
-  g->dev.heavy_vertices = hv;
-  g->dev.heavy_chunks = hc;
-  g->dev.order = d_ord;
-  g->d_order = d_ord;
-  g->order = std::move(ord);
-  ctx->used += bytes;
-  if (m_eff) *m_eff = me;
-  out = std::move(g);
+  if (m_eff) *m_eff = h.me;
+  ctx->used += h.bytes;
+  out = prep_graph(h, mem);
   return BC_OK;
 }
 
-bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
-                      int64_t m, std::unique_ptr<GraphRec> &out, int64_t *m_eff) {
+// Host checks of a CSR's sizes and offsets (column ids are checked where the
+// graph is prepared).
+bc_status check_offsets(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t m) {
   if (n < 0 || m < 0 || m >= ((int64_t)1 << 31)) return BC_ERR_GRAPH;
   if (!row_ptr || (m > 0 && !col_idx)) return BC_ERR_ARG;
   if (row_ptr[0] != 0 || (int64_t)row_ptr[n] != m) return BC_ERR_GRAPH;
   for (int32_t v = 0; v < n; ++v)
     if (row_ptr[v + 1] < row_ptr[v]) return BC_ERR_GRAPH;
+  return BC_OK;
+}
+
+bc_status build_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                      int64_t m, std::unique_ptr<GraphRec> &out, int64_t *m_eff) {
+  const bc_status chk = check_offsets(row_ptr, col_idx, n, m);
+  if (chk != BC_OK) return chk;
   if (m <= kHostPrepMaxEdges) return build_graph_small(ctx, row_ptr, col_idx, n, m, out, m_eff);
   cudaStream_t st = ctx->stream;
   // BC_PREP_TRACE=1: per-phase times of the preparation to stderr (each mark
@@ -1464,6 +1517,118 @@ bc_status bc_create_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *co
   g->handle = ctx->next_graph++;
   *out = g->handle;
   ctx->graphs.emplace(g->handle, std::move(g));
+  return BC_OK;
+}
+
+bc_status bc_create_graphs(bc_ctx *ctx, int32_t count, const int32_t *const *row_ptrs,
+                           const int32_t *const *col_idxs, const int32_t *ns, const int64_t *ms,
+                           bc_graph *out, int64_t *m_effective) {
+  if (!ctx || count < 0) return BC_ERR_ARG;
+  if (count > 0 && (!row_ptrs || !col_idxs || !ns || !ms || !out)) return BC_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t st = ctx->stream;
+  std::vector<std::unique_ptr<GraphRec>> made((size_t)count);
+  std::vector<int64_t> meff((size_t)count, 0);
+  auto fail = [&](bc_status s) {
+    cudaStreamSynchronize(st);
+    for (auto &g : made)
+      if (g) {
+        cudaFreeAsync(g->mem, st);
+        ctx->used -= g->bytes;
+      }
+    cudaStreamSynchronize(st);
+    return s;
+  };
+  for (int32_t i = 0; i < count; ++i) {
+    const bc_status s = check_offsets(row_ptrs[i], col_idxs[i], ns[i], ms[i]);
+    if (s != BC_OK) return s;
+  }
+  // Graphs prepared on the host go in groups of up to kGroupBytes of device
+  // image: prepared on up to 16 threads, written to the pinned staging
+  // buffer, copied with one transfer each and one synchronisation per group.
+  // Larger graphs take the device path one by one.
+  constexpr size_t kGroupBytes = (size_t)64 << 20;
+  const int threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  auto parallel = [&](int items, const std::function<void(int)> &f) {
+    std::atomic<int> next{0};
+    auto work = [&]() {
+      for (int t = next++; t < items; t = next++) f(t);
+    };
+    std::vector<std::thread> th;
+    for (int i = 1; i < std::min(threads, items); ++i) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
+  };
+  int32_t i = 0;
+  while (i < count) {
+    if (ms[i] > kHostPrepMaxEdges) {
+      const bc_status s = build_graph(ctx, row_ptrs[i], col_idxs[i], ns[i], ms[i], made[(size_t)i],
+                                      &meff[(size_t)i]);
+      if (s != BC_OK) return fail(s);
+      ++i;
+      continue;
+    }
+    int32_t j = i;
+    size_t bound = 0;
+    while (j < count && ms[j] <= kHostPrepMaxEdges) {
+      Carver c;
+      block_layout(ns[j], ms[j], [&](size_t cnt) { (void)c.take<int32_t>(cnt); });
+      if (j > i && bound + c.off > kGroupBytes) break;
+      bound += align_up(c.off, 256);
+      ++j;
+    }
+    const int items = j - i;
+    std::vector<HostPrep> hp((size_t)items);
+    std::vector<bc_status> res((size_t)items, BC_OK);
+    parallel(items, [&](int t) {
+      res[(size_t)t] = prep_host(row_ptrs[i + t], col_idxs[i + t], ns[i + t], ms[i + t], hp[(size_t)t]);
+    });
+    for (bc_status s : res)
+      if (s != BC_OK) return fail(s);
+    std::vector<size_t> off((size_t)items + 1, 0);
+    for (int t = 0; t < items; ++t) off[(size_t)t + 1] = off[(size_t)t] + hp[(size_t)t].bytes;
+    bc_status s = ensure_stage(ctx, off[(size_t)items]);
+    if (s != BC_OK) return fail(s);
+    char *stage = static_cast<char *>(ctx->stage);
+    parallel(items, [&](int t) { prep_image(hp[(size_t)t], stage + off[(size_t)t]); });
+    std::vector<void *> mem((size_t)items, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < items && e == cudaSuccess && s == BC_OK; ++t) {
+      if (ctx->used + hp[(size_t)t].bytes > ctx->budget) {
+        s = BC_ERR_ADMISSION;
+        break;
+      }
+      e = pool_alloc(ctx, &mem[(size_t)t], hp[(size_t)t].bytes, st);
+      if (e == cudaSuccess) {
+        ctx->used += hp[(size_t)t].bytes;
+        e = cudaMemcpyAsync(mem[(size_t)t], stage + off[(size_t)t], hp[(size_t)t].bytes,
+                            cudaMemcpyHostToDevice, st);
+      } else {
+        mem[(size_t)t] = nullptr;
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || s != BC_OK) {
+      for (int t = 0; t < items; ++t)
+        if (mem[(size_t)t]) {
+          cudaFreeAsync(mem[(size_t)t], st);
+          ctx->used -= hp[(size_t)t].bytes;
+        }
+      return fail(s != BC_OK ? s : cuda_status(e));
+    }
+    for (int t = 0; t < items; ++t) {
+      meff[(size_t)(i + t)] = hp[(size_t)t].me;
+      made[(size_t)(i + t)] = prep_graph(hp[(size_t)t], mem[(size_t)t]);
+    }
+    i = j;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  for (int32_t t = 0; t < count; ++t) {
+    made[(size_t)t]->handle = ctx->next_graph++;
+    out[t] = made[(size_t)t]->handle;
+    if (m_effective) m_effective[t] = meff[(size_t)t];
+    ctx->graphs.emplace(out[t], std::move(made[(size_t)t]));
+  }
   return BC_OK;
 }
 

@@ -80,3 +80,47 @@ def test_many_graphs_per_graph_width_and_overrun(ctx):
         close(got, ref, 1e-12)
     for h in handles:
         ctx.destroy_graph(h)
+
+
+def test_create_graphs_in_one_call(ctx):
+    """bc_create_graphs: small graphs prepared on host threads, a large one on
+    the device, a non-canonical one canonicalised; each resident graph equals
+    the canonical CSR and its transpose bit for bit, BC matches the oracle,
+    and one malformed graph rejects the whole call."""
+    import paper_1409_7764_gb300 as bc
+    rs = np.random.default_rng(2)
+    src, dst = rs.integers(0, 300, 3000), rs.integers(0, 300, 3000)
+    raw = bcgen.raw_csr_from_edges(300, np.concatenate([src, src[:400], np.arange(40)]),
+                                   np.concatenate([dst, dst[:400], np.arange(40)]))
+    canon_raw = bcgen.csr_from_edges(300, src, dst)
+    gs = [bcgen.rmat(s_, ef, sd) for (s_, ef, sd) in bcgen.small_rmat_specs(300, master_seed=3)]
+    gs += [bcgen.csr_from_edges(1, [], []), bcgen.star(900, "bi"), bcgen.rmat(14, 20, seed=4)]
+    inputs = [(g.row_ptr, g.col_idx) for g in gs] + [(raw.row_ptr, raw.col_idx)]
+    canon = gs + [canon_raw]
+    hs = ctx.create_graphs(inputs)
+    assert [h.m for h in hs] == [g.m for g in canon]
+    for h, g in zip(hs, canon):
+        rp, ci, ip, ii = ctx.debug_graph(h)
+        np.testing.assert_array_equal(rp, g.row_ptr)
+        np.testing.assert_array_equal(ci, g.col_idx)
+        s_, d_ = g.edges()
+        cnt = np.zeros(g.n + 1, dtype=np.int64)
+        np.add.at(cnt, np.asarray(d_, dtype=np.int64) + 1, 1)
+        np.testing.assert_array_equal(ip, np.cumsum(cnt))
+        np.testing.assert_array_equal(ii, np.asarray(s_)[np.lexsort((s_, d_))])
+    small = [i for i, g in enumerate(canon) if g.n <= 4096]
+    outs = ctx.exact_many([hs[i] for i in small], delta_fp64=True)
+    for i, got in list(zip(small, outs))[::7]:
+        ref, _ = oracle.bc(canon[i].n, canon[i].row_ptr, canon[i].col_idx)
+        close(got, ref, 1e-12)
+    for h in hs:
+        ctx.destroy_graph(h)
+    bad = gs[5].col_idx.copy()
+    bad[0] = gs[5].n
+    with pytest.raises(bc.BCError) as ei:
+        ctx.create_graphs(inputs[:5] + [(gs[5].row_ptr, bad)] + inputs[6:10])
+    assert ei.value.status == bc.BC_ERR_GRAPH
+    hs = ctx.create_graphs(inputs[:10])
+    assert len(hs) == 10
+    for h in hs:
+        ctx.destroy_graph(h)
