@@ -335,6 +335,12 @@ struct bc_ctx {
   // pinned staging for the single upload of a host-prepared graph
   void *stage = nullptr;
   size_t stage_bytes = 0;
+  // pinned host blocks of finished jobs kept for reuse (power-of-two size
+  // classes, up to kPinKeepBytes): pinning and unpinning cost tens to
+  // hundreds of microseconds per call
+  std::mutex pin_mu;
+  std::multimap<size_t, void *> pin_free;
+  size_t pin_free_bytes = 0;
 
   std::mutex mu;
   std::unordered_map<int64_t, std::unique_ptr<GraphRec>> graphs;
@@ -361,6 +367,50 @@ struct bc_ctx {
 namespace {
 
 constexpr uint64_t kPoolKeepBytes = (uint64_t)2 << 30;
+
+constexpr size_t kPinKeepBytes = (size_t)64 << 20;
+
+size_t pin_class(size_t bytes) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+// Pinned host block of at least `bytes`, from the context's cache if one of
+// its size class is free.
+template <typename T> cudaError_t pin_get(bc_ctx *ctx, T **p, size_t bytes) {
+  const size_t cls = pin_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(ctx->pin_mu);
+    auto it = ctx->pin_free.find(cls);
+    if (it != ctx->pin_free.end()) {
+      *p = static_cast<T *>(it->second);
+      ctx->pin_free.erase(it);
+      ctx->pin_free_bytes -= cls;
+      return cudaSuccess;
+    }
+  }
+  void *q = nullptr;
+  const cudaError_t e = cudaMallocHost(&q, cls);
+  *p = static_cast<T *>(q);
+  return e;
+}
+
+// Returns a block from pin_get (asked for `bytes`) to the cache, or unpins
+// it when the cache is full.
+void pin_put(bc_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  const size_t cls = pin_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(ctx->pin_mu);
+    if (ctx->pin_free_bytes + cls <= kPinKeepBytes) {
+      ctx->pin_free.emplace(cls, p);
+      ctx->pin_free_bytes += cls;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
 
 // Stream-ordered allocation from the context's pool.
 template <typename T> cudaError_t pool_alloc(bc_ctx *ctx, T **p, size_t bytes, cudaStream_t st) {
@@ -977,7 +1027,7 @@ size_t job_footprint(const GraphRec &gr, int sched, const bc_opts &o, int64_t k)
   return ws_layout(r, nullptr) + sizeof(double) * (size_t)g.n + (size_t)k * 5 + 4096;
 }
 
-void job_free_buffers(JobRec *j) {
+void job_free_buffers(bc_ctx *ctx, JobRec *j) {
   if (j->d_src) cudaFreeAsync(j->d_src, j->st);
   if (j->d_bc) cudaFreeAsync(j->d_bc, j->st);
   if (j->d_bc2) cudaFreeAsync(j->d_bc2, j->st);
@@ -988,9 +1038,9 @@ void job_free_buffers(JobRec *j) {
   j->d_bc = nullptr;
   j->d_ovf = nullptr;
   j->d_cnt = nullptr;
-  if (j->h_src) cudaFreeHost(j->h_src);
-  if (j->h_cnt) cudaFreeHost(j->h_cnt);
-  if (j->h_ovf) cudaFreeHost(j->h_ovf);
+  pin_put(ctx, j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(j->k, 1));
+  pin_put(ctx, j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1));
+  pin_put(ctx, j->h_ovf, (size_t)std::max<int64_t>(j->k, 1));
   j->h_src = nullptr;
   j->h_cnt = nullptr;
   j->h_ovf = nullptr;
@@ -1037,9 +1087,9 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
 
   bc_status s = ws_acquire(ctx, ws_need(g, kind, kb, words), st, j->ws);
   if (s != BC_OK) return s;
-  BC_TRY(cudaMallocHost(&j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
-  BC_TRY(cudaMallocHost(&j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
-  BC_TRY(cudaMallocHost(&j->h_ovf, (size_t)std::max<int64_t>(k, 1)));
+  BC_TRY(pin_get(ctx, &j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
+  BC_TRY(pin_get(ctx, &j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
+  BC_TRY(pin_get(ctx, &j->h_ovf, (size_t)std::max<int64_t>(k, 1)));
   j->h_err = reinterpret_cast<int *>(j->h_cnt + CNT_N);
   // batch composition (bc_opts.source_order); debug exports keep the given
   // order, since their rows follow it
@@ -1055,9 +1105,24 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   } else if (k) {
     std::memcpy(j->h_src, j->src.data(), sizeof(int32_t) * (size_t)k);
     if (grouped) {
-      const GraphRec *g = j->g;
-      std::stable_sort(j->h_src, j->h_src + k,
-                       [g](int32_t a, int32_t b) { return batch_key_less(*g, a, b); });
+      GraphRec *g = j->g;
+      if (k >= (int64_t)n / 8) {
+        // many sources: walk the graph's batch order once, emitting each
+        // vertex as often as the list holds it (O(n + k))
+        s = ensure_order(g, st);
+        if (s != BC_OK) return s;
+        std::vector<int32_t> cnt((size_t)n, 0);
+        for (int64_t i = 0; i < k; ++i) cnt[(size_t)j->h_src[i]]++;
+        int64_t w = 0;
+        for (int32_t v : g->order)
+          for (int32_t c = cnt[(size_t)v]; c > 0; --c) j->h_src[w++] = v;
+      } else {
+        // few sources: their packed keys, sorted (equal keys are equal ids)
+        std::vector<OrderKey> keys((size_t)k);
+        for (int64_t i = 0; i < k; ++i) keys[(size_t)i] = order_key(g->row_ptr, g->two, j->h_src[i]);
+        std::sort(keys.begin(), keys.end());
+        for (int64_t i = 0; i < k; ++i) j->h_src[i] = (int32_t)(uint32_t)keys[(size_t)i].lo;
+      }
     }
   }
   BC_TRY(pool_alloc(ctx, &j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));
@@ -1269,7 +1334,7 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
     st = BC_ERR_SIGMA_OVERFLOW;
   }
   ws_release(ctx, std::move(j->ws));
-  job_free_buffers(j);
+  job_free_buffers(ctx, j);
   return st;
 }
 
@@ -1296,12 +1361,12 @@ bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool
         j.ws->dirty = true;
         ws_release(ctx, std::move(j.ws));
       }
-      job_free_buffers(&j);
+      job_free_buffers(ctx, &j);
       return s;
     }
     cudaError_t e = cudaEventSynchronize(j.evdone);
     if (e != cudaSuccess) {
-      job_free_buffers(&j);
+      job_free_buffers(ctx, &j);
       return cuda_status(e);
     }
     s = job_finish(ctx, &j);
@@ -1353,7 +1418,7 @@ void scheduler_loop(bc_ctx *ctx) {
           j->ws->dirty = true;
           ws_release(ctx, std::move(j->ws));
         }
-        job_free_buffers(j);
+        job_free_buffers(ctx, j);
         lk.lock();
         j->status = s;
         j->done = true;
@@ -1382,7 +1447,7 @@ void scheduler_loop(bc_ctx *ctx) {
             j->ws->dirty = true;
             ws_release(ctx, std::move(j->ws));
           }
-          job_free_buffers(j);
+          job_free_buffers(ctx, j);
         }
         lk.lock();
         j->status = s;
@@ -1499,6 +1564,8 @@ bc_status bc_shutdown(bc_ctx *ctx) {
   ctx->graphs.clear();
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->stage) cudaFreeHost(ctx->stage);
+  for (auto &kv : ctx->pin_free) cudaFreeHost(kv.second);
+  ctx->pin_free.clear();
   for (int i = 0; i < kMaxSlots; ++i)
     if (ctx->slot_stream[i]) cudaStreamDestroy(ctx->slot_stream[i]);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1838,12 +1905,11 @@ bc_status bc_submit(bc_ctx *ctx, bc_graph h, const int32_t *src, int32_t k, cons
   const int sched = resolve_schedule(o, j->g->dev);
   j->footprint = job_footprint(*j->g, sched, o, j->k);
   if (j->footprint > ctx->budget) return BC_ERR_ADMISSION;
-  if (cudaMallocHost(&j->h_out, sizeof(double) * (size_t)std::max<int32_t>(j->g->dev.n, 1)) !=
-      cudaSuccess)
+  if (pin_get(ctx, &j->h_out, sizeof(double) * (size_t)std::max<int64_t>(j->n, 1)) != cudaSuccess)
     return BC_ERR_OOM;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->stop) {
-    cudaFreeHost(j->h_out);
+    pin_put(ctx, j->h_out, sizeof(double) * (size_t)std::max<int64_t>(j->n, 1));
     return BC_ERR_ARG;
   }
   j->handle = ctx->next_job++;
@@ -1862,7 +1928,7 @@ static bc_status take_result(bc_ctx *ctx, std::map<int64_t, std::unique_ptr<JobR
   if (bc_out && j->n) std::memcpy(bc_out, j->h_out, sizeof(double) * (size_t)j->n);
   if (stats) *stats = j->stats;
   bc_status s = j->status;
-  cudaFreeHost(j->h_out);
+  pin_put(ctx, j->h_out, sizeof(double) * (size_t)std::max<int64_t>(j->n, 1));
   ctx->jobs.erase(it);
   return s;
 }
