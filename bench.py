@@ -27,6 +27,7 @@ import multiprocessing as mp
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -162,7 +163,9 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{device}.csv")
+        # raw samples: BENCH_CLOCKS_DIR if set (to keep them), else a temporary file
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"bench_clocks_dev{device}_{os.getpid()}.csv")
 
     def start(self):
         try:
