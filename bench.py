@@ -163,7 +163,8 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        # raw samples: BENCH_CLOCKS_DIR if set (to keep them), else a temporary file
+        # raw samples: kept in BENCH_CLOCKS_DIR if set, else a temporary file
+        self.keep = bool(os.environ.get("BENCH_CLOCKS_DIR"))
         out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
         self.path = os.path.join(out_dir, f"bench_clocks_dev{device}_{os.getpid()}.csv")
 
@@ -202,6 +203,11 @@ class ClockSampler:
                 for nm, val in zip(names, parts[5:9]):
                     if val.lower().startswith("active"):
                         reasons.add(nm)
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
