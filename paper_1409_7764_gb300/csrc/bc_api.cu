@@ -83,7 +83,7 @@ struct GraphRec {
   // a batch wider than 64 sources overran its frontier queue or heavy list
   // (sized for 64 distinct depths per vertex): later jobs use 64 sources
   std::atomic<bool> narrow{false};
-  // batch composition (see batch_key_less): host copies of the out-CSR
+  // batch composition (see order_key): host copies of the out-CSR
   // offsets and of the two-hop walk counts; every vertex in batch order, made
   // on first need (kept on the host and in d_order)
   std::vector<int32_t> row_ptr;
@@ -100,18 +100,9 @@ struct GraphRec {
 // without out-edges (a traversal of one vertex) last, the others by the
 // number of two-hop walks leaving them (a proxy for how fast the traversal
 // fans out into the graph's core), descending; ties by out-degree, then
-// vertex id.
-inline bool batch_key_less(const GraphRec &g, int32_t a, int32_t b) {
-  const int32_t da = g.row_ptr[(size_t)a + 1] - g.row_ptr[(size_t)a];
-  const int32_t db = g.row_ptr[(size_t)b + 1] - g.row_ptr[(size_t)b];
-  if ((da == 0) != (db == 0)) return db == 0;
-  if (g.two[(size_t)a] != g.two[(size_t)b]) return g.two[(size_t)a] > g.two[(size_t)b];
-  if (da != db) return da > db;
-  return a < b;
-}
-
-// The same order as two words compared in turn (smaller first): dead flag
-// and descending two-hop count, then descending out-degree and the id.
+// vertex id.  Packed as two words compared in turn (smaller first): the
+// no-out-edge flag and the descending two-hop count, then the descending
+// out-degree and the id.
 struct OrderKey {
   uint64_t hi, lo;
   bool operator<(const OrderKey &o) const { return hi != o.hi ? hi < o.hi : lo < o.lo; }
@@ -124,7 +115,7 @@ inline OrderKey order_key(const std::vector<int32_t> &row_ptr, const std::vector
           ((uint64_t)(uint32_t)(INT32_MAX - d) << 32) | (uint32_t)v};
 }
 
-// Every vertex in batch order (batch_key_less): packed keys sorted in
+// Every vertex in batch order (order_key): packed keys sorted in
 // chunks on up to eight threads, then merged pairwise.
 std::vector<int32_t> batch_order(const std::vector<int32_t> &row_ptr,
                                  const std::vector<int64_t> &two, int32_t n) {
