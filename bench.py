@@ -50,6 +50,10 @@ WORKLOADS = {
                                src_seed=1, batch_k=0, schedule="batch"),
     "rmat20-sampled1024": dict(kind="rmat", scale=20, ef=16, seed=1, sources=1024,
                                src_seed=1, batch_k=0, schedule="batch"),
+    # a smaller R-MAT case of the same recipe for detailed profiles (scale 18,
+    # 1024 sources, four batches of 256; about 1.5 GB on the device)
+    "rmat18-sampled1024": dict(kind="rmat", scale=18, ef=16, seed=1, sources=1024,
+                               src_seed=1, batch_k=0, schedule="batch"),
     # directed preferential attachment n = 2^20, 8 out-edges, 4096 sources
     "ba20-sampled4096": dict(kind="ba", n=1 << 20, out=8, seed=1, sources=4096, src_seed=1,
                              batch_k=0, schedule="batch"),
@@ -86,22 +90,18 @@ def describe(name, w, g, nsrc):
 # ---- bytes model --------------------------------------------------------------
 
 def bytes_model(stats, delta_bytes):
-    """Algorithmic bytes of the BC kernels for the counters of one job
-    (element granularity, each element the design must touch counted once;
-    b = bytes of one dependency value).
+    """Design bytes model: algorithmic bytes of the BC kernels as this design
+    lays out its data, for the counters of one job (element granularity, each
+    element the design must touch counted once; b = bytes of one dependency
+    value, W = 64-bit words per source mask).
 
-    dense batch kernel (kernel_kind 3): 24 B per vertex and level (the level's
-           masks scanned forward and backward, then cleared), 72 B per
-           frontier entry (CSR offsets, visited read/write/reset, next-level
-           mask, BC read-modify-write), 12 B per scanned in-edge (column + the
-           predecessor's mask), 16 B per scanned out-edge (column + one or two
-           masks), (8 + b) B per (source, DAG edge) (predecessor path count,
+    queue batch kernel (kernel_kind 2): 124 B per frontier entry (queue
+           id/mask, CSR offsets, dense mask read/write/clear, visited, BC),
+           4 + 8W B per scanned edge (the neighbour id and its W-word mask),
+           (8 + b) B per (source, DAG edge) (predecessor path count,
            successor coefficient), (16 + b) B per (source, reached vertex)
-           (path count write and read; coefficient write; counts need no
+           (path count write and read, coefficient write; counts need no
            reset, since a count is only read where its batch wrote it).
-    queue batch kernel (2): 124 B per entry (queue id/mask, CSR offsets, dense
-           mask read/write/clear, visited, BC), 12 B per scanned edge, same
-           per-pair terms.
     plain kernel (1): (84 + b) B per entry, 8 B per scanned edge (column +
            int32 depth), (8 + b) B per DAG edge.
     """
@@ -109,21 +109,44 @@ def bytes_model(stats, delta_bytes):
     I, O = stats["scanned_in_edges"], stats["scanned_out_edges"]
     D, R = stats["dag_pairs"], stats["reached_pairs"]
     b = delta_bytes
-    kind = stats.get("kernel_kind", 2)
-    if kind == 3:
-        return (24 * stats["n"] * stats["levels_sum"] + 72 * E + 12 * I + 16 * O +
-                (8 + b) * D + (16 + b) * R)
-    if kind == 2:
-        return 124 * E + 12 * (I + O) + (8 + b) * D + (16 + b) * R
+    if stats.get("kernel_kind", 2) == 2:
+        W = max(int(stats.get("mask_words") or 1), 1)
+        return 124 * E + (4 + 8 * W) * (I + O) + (8 + b) * D + (16 + b) * R
     return (84 + b) * E + 8 * (I + O) + (8 + b) * D
 
 
-KERNEL_NAMES = {1: "plain_kernel", 2: "batch_kernel", 3: "dense_kernel"}
+def method_bytes_model(stats, delta_bytes):
+    """The method's bytes model, independent of this design's layout, per
+    job: every element the batched sweeps must touch, at the width the method
+    states it.  Batched, k sources per batch: the CSR once per batch and level (8 B of
+    offsets per frontier entry, 4 B per scanned edge), k/8 B of source
+    bitset per scanned edge endpoint, per (source, DAG edge) a 16-byte path
+    count read-modify-write and a b-byte coefficient read, per (source,
+    reached vertex) 16 + b bytes of count, dependency and BC terms:
+        8 E + 4 (I + O) + (k/8)(I + O) + (16 + b) D + (16 + b) R.
+    One source per launch (plain): 8 B per scanned edge (column + depth
+    test), (24 + b) B per DAG edge, (72 + 2b) B per reached vertex:
+        8 (I + O) + (24 + b) D + (72 + 2b) E."""
+    E = stats["frontier_entries"]
+    I, O = stats["scanned_in_edges"], stats["scanned_out_edges"]
+    D, R = stats["dag_pairs"], stats["reached_pairs"]
+    b = delta_bytes
+    if stats.get("kernel_kind", 2) == 2:
+        k = 64 * max(int(stats.get("mask_words") or 1), 1)
+        return 8 * E + 4 * (I + O) + (k // 8) * (I + O) + (16 + b) * D + (16 + b) * R
+    return 8 * (I + O) + (24 + b) * D + (72 + 2 * b) * E
+
+
+KERNEL_NAMES = {1: "plain_kernel", 2: "batch_kernel"}
+METHOD_MODEL_TEXT = {2: "8E + 4(I+O) + (k/8)(I+O) + (16+b)D + (16+b)R, k = 64 x mask_words",
+                     1: "8(I+O) + (24+b)D + (72+2b)E"}
+DESIGN_MODEL_TEXT = {2: "124E + (4+8W)(I+O) + (8+b)D + (16+b)R, W = mask_words",
+                     1: "(84+b)E + 8(I+O) + (8+b)D"}
 
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ["bc_kernels.cu", "bc_dense.cu", "bc_device.cuh", "bc_internal.cuh"]:
+    for f in ["bc_kernels.cu", "bc_device.cuh", "bc_internal.cuh"]:
         with open(os.path.join(ROOT, "paper_1409_7764_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,10 +400,12 @@ def run_ours(args, w, name):
     # kernel-level roofline of the batch (or plain) kernel on this rank
     st = stats[-1]
     delta_bytes = 8 if fp64 else 4
-    algo_bytes = bytes_model(st, delta_bytes)
+    algo_bytes = method_bytes_model(st, delta_bytes)
+    design_bytes = bytes_model(st, delta_bytes)
     launches = max(st["batches"], 1)
     my_ms = sum(step_ms) / args.steps
     achieved = algo_bytes / (my_ms / 1e3) / 1e9
+    design_achieved = design_bytes / (my_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = ncu_traffic(name)
 
@@ -467,8 +492,13 @@ def run_ours(args, w, name):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "kernel": KERNEL_NAMES.get(st.get("kernel_kind"), "?"),
+                         "model": METHOD_MODEL_TEXT.get(st.get("kernel_kind"), "?"),
                          "algo_bytes_per_launch": algo_bytes / launches,
-                         "launch_ms": my_ms / launches},
+                         "launch_ms": my_ms / launches,
+                         "design_model": {
+                             "formula": DESIGN_MODEL_TEXT.get(st.get("kernel_kind"), "?"),
+                             "bytes_per_launch": design_bytes / launches,
+                             "achieved": design_achieved, "frac": design_achieved / peak}},
             "cpu_baseline": cpu,
             "precision": precision,
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
@@ -677,7 +707,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat16-exact",
+    ap.add_argument("--workload", default="rmat20-sampled4096",
                     choices=sorted(WORKLOADS) + ["rmat-many10k", "serving"])
     ap.add_argument("--fp64", action="store_true", help="FP64 dependencies")
     ap.add_argument("--plain-sample", type=int, default=256)
@@ -685,7 +715,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the plain / precision extras")
     ap.add_argument("--schedule", default=None,
-                    choices=["plain", "batch", "batch_queue", "batch_dense"],
+                    choices=["plain", "batch", "batch_queue"],
                     help="override the workload's schedule")
     ap.add_argument("--max-sources", type=int, default=0,
                     help="use only the first N sources of the workload (profiling runs)")

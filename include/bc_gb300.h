@@ -66,11 +66,9 @@ typedef enum {
 enum {
   BC_SCHED_AUTO = 0,
   BC_SCHED_PLAIN = 1,       /* one source per kernel launch, whole GPU, level-synchronous */
-  BC_SCHED_BATCH = 2,       /* up to 256 sources per launch, bitset frontiers, [n][k] state;
-                               the library picks the frontier representation */
-  BC_SCHED_BATCH_QUEUE = 3, /* BATCH with per-level frontier queues */
-  BC_SCHED_BATCH_DENSE = 4  /* BATCH with per-level dense frontier masks (falls back to the
-                               queue form for graphs deeper than its mask array) */
+  BC_SCHED_BATCH = 2,       /* up to 256 sources per launch, bitset frontiers, per-level
+                               frontier queues, [n][k] state */
+  BC_SCHED_BATCH_QUEUE = 3  /* the same as BATCH */
 };
 
 typedef struct {
@@ -78,8 +76,7 @@ typedef struct {
   int32_t batch_k;       /* sources per batch of the batched schedules: 0 = the library picks
                             64, 128 or 256 (the widest that still gives the job eight batches;
                             64 for debug exports; per graph in bc_exact_many); else 1..256 for
-                            BC_SCHED_AUTO / BATCH / BATCH_QUEUE, 1..64 for BATCH_DENSE and
-                            bc_exact_many.  Bit j of a batch's source masks is its j-th
+                            BC_SCHED_AUTO / BATCH / BATCH_QUEUE, 1..64 for bc_exact_many.  Bit j of a batch's source masks is its j-th
                             source; masks are 1, 2 or 4 64-bit words.  Wider batches size
                             their frontier queue for 64 distinct depths per vertex; a job
                             that overruns it reruns with 64 sources per batch, and so do
@@ -113,8 +110,7 @@ typedef struct {
   int64_t dag_pairs;         /* sum over sources of shortest-path DAG edges */
   int64_t reached_pairs;     /* sum over sources of reached vertices (incl. source) */
   int64_t heavy_chunks;      /* edge chunks of high-degree vertices split across warps */
-  int32_t kernel_kind;       /* kernel of the last launch: 1 plain, 2 batch (frontier queue),
-                                3 batch (per-level dense masks) */
+  int32_t kernel_kind;       /* kernel of the last launch: 1 plain, 2 batch (frontier queue) */
   int32_t levels_sum;        /* BFS level counts summed over all batches */
   int32_t chunk_edges;       /* edges per chunk of a high-degree vertex in the last launch */
   int32_t grab;              /* work items a warp fetched at a time in the last launch */
@@ -312,7 +308,12 @@ bc_status bc_debug_inject_barrier_skip(bc_ctx *ctx, int32_t block, int32_t timeo
  * warps, so hubs run slower than through bc_sources.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) and the
  * kernel's grid size with that device current; make that first call before
- * any stream capture. */
+ * any stream capture.  Only a successful look-up is kept: if it fails (also
+ * when a CUDA error from earlier, unrelated work is still pending on the
+ * calling thread, which this call reports as BC_ERR_CUDA and does not clear)
+ * the next call tries again.  If fewer thread blocks can run at once than at
+ * that first call (the GPU shared differently, e.g. under MPS), the launch
+ * is retried with half the grid until it fits. */
 bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *in_ptr,
                              const int32_t *in_idx, int32_t n, int64_t m, const int32_t *src,
                              int32_t k, int32_t delta_fp64, double *bc_out, void *cuda_stream);

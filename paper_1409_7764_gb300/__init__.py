@@ -29,7 +29,7 @@ __all__ = [
 ]
 
 _SCHED = {"auto": BC_SCHED_AUTO, "plain": BC_SCHED_PLAIN, "batch": BC_SCHED_BATCH,
-          "batch_queue": capi.BC_SCHED_BATCH_QUEUE, "batch_dense": capi.BC_SCHED_BATCH_DENSE}
+          "batch_queue": capi.BC_SCHED_BATCH_QUEUE}
 
 
 def load():

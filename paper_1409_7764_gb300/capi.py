@@ -26,7 +26,6 @@ BC_SCHED_AUTO = 0
 BC_SCHED_PLAIN = 1
 BC_SCHED_BATCH = 2
 BC_SCHED_BATCH_QUEUE = 3
-BC_SCHED_BATCH_DENSE = 4
 
 # every symbol include/bc_gb300.h declares
 EXPORTED = [

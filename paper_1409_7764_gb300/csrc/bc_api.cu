@@ -73,7 +73,6 @@ struct GraphRec {
   void *mem = nullptr;
   size_t bytes = 0;
   int active_jobs = 0;
-  std::atomic<bool> deep{false}; // more BFS levels than the dense kernel's masks hold
   // chunk counts of the high-degree vertices for each candidate chunk size
   const int32_t *nch_variant[kChunkVariants] = {};
   int64_t heavy_v[kChunkVariants] = {}, heavy_c[kChunkVariants] = {};
@@ -167,14 +166,13 @@ static_assert(grabs_fit(), "a fetch larger than the kernels' header rounds hold"
 constexpr int kNumTune = 4;
 constexpr int kTuneRounds = 2; // trial batches per candidate
 
-enum WsKind { WS_PLAIN = 0, WS_QUEUE = 1, WS_DENSE = 2 };
+enum WsKind { WS_PLAIN = 0, WS_QUEUE = 1 };
 
 struct WsRec {
   bool batch = true;
   int kind = WS_QUEUE;
   int words = 1; // 64-bit words per source mask (queue kernel: 1, 2 or 4)
   int32_t n = 0;
-  int32_t dmax = 0;
   int64_t cap = 0, hcap = 0, chunk_cap = 0;
   Work w;
   void *mem = nullptr;
@@ -186,18 +184,14 @@ struct WsNeed {
   int kind;
   int words;
   int32_t n;
-  int32_t dmax;
   int64_t cap, hcap, chunk_cap;
   bool fits(const WsRec &r) const {
     if (r.kind != kind || r.words != words || r.n < n || r.hcap < hcap ||
         r.chunk_cap < chunk_cap)
       return false;
-    return kind == WS_DENSE ? r.dmax >= dmax : r.cap >= cap;
+    return r.cap >= cap;
   }
 };
-
-// Levels the dense kernel's per-level masks hold for an n-vertex graph.
-int32_t dense_levels(int32_t n) { return n <= (1 << 22) ? kDenseLevels : kDenseLevels / 2; }
 
 // Sources per batch and mask words of a job.  Explicit batch_k: that many
 // sources, in as many words as they need.  Automatic: the queue kernel takes
@@ -224,11 +218,10 @@ WsNeed ws_need(const GraphDev &g, int kind, int kb, int words) {
   nd.kind = kind;
   nd.words = kind == WS_QUEUE ? words : 1;
   nd.n = g.n;
-  nd.dmax = kind == WS_DENSE ? dense_levels(g.n) : 0;
   // a vertex is queued at most once per distinct depth among the batch's
   // sources; wider batches are sized for 64 depths (overruns are detected)
   const int64_t kk = kind == WS_PLAIN ? 1 : std::min<int64_t>(kb, kK);
-  nd.cap = kind == WS_DENSE ? 1 : std::max<int64_t>(1, (int64_t)g.n * kk);
+  nd.cap = std::max<int64_t>(1, (int64_t)g.n * kk);
   nd.hcap = std::max<int64_t>(1, g.heavy_vertices * kk);
   nd.chunk_cap = std::max<int64_t>(1, g.heavy_chunks);
   return nd;
@@ -247,24 +240,6 @@ size_t ws_layout(WsRec &r, char *mem) {
   w.k_max = (int32_t)kk;
   w.words = (int32_t)words;
   w.ctl = c.take<Ctl>(1);
-  if (r.kind == WS_DENSE) {
-    w.vis = c.take<uint64_t>(n);
-    w.lm = c.take<uint64_t>((size_t)r.dmax * n);
-    w.dmax = r.dmax;
-    w.lvl_flag = c.take<unsigned>((size_t)r.dmax + 2);
-    w.hpack = c.take<unsigned long long>((size_t)r.dmax + 3);
-    w.hoff = c.take<int64_t>((size_t)r.dmax + 3);
-    w.hq_e = c.take<int64_t>((size_t)r.hcap);
-    w.hq_c = c.take<int64_t>((size_t)r.hcap);
-    w.harrive = c.take<unsigned>((size_t)r.hcap);
-    w.hcap = r.hcap;
-    w.partial = c.take<uint64_t>((size_t)r.chunk_cap * kk);
-    w.partial_ovf = c.take<uint64_t>((size_t)r.chunk_cap);
-    w.chunk_cap = r.chunk_cap;
-    w.sigma = c.take<uint64_t>(n * kk);
-    w.cdep = c.take<double>(n * kk);
-    return align_up(c.off, 256);
-  }
   if (r.batch) {
     w.vis = c.take<uint64_t>(n * words);
     w.fr = c.take<uint64_t>(4 * n * words);
@@ -314,7 +289,6 @@ struct bc_ctx {
   std::atomic<size_t> used{0};
   int sm_count = 0;
   int grid_batch[3][2] = {}; // [mask words 1/2/4][fp64]
-  int grid_dense[2] = {0, 0};
   int grid_many[2] = {0, 0};
   int grid_plain[2] = {0, 0};
   // Stream-ordered allocations of this context (graphs, job buffers, prep
@@ -449,7 +423,7 @@ struct JobRec {
   bool done = false;
 };
 
-// internal: the job must be launched again (dense kernel ran out of levels)
+// internal: the job must be launched again (a wide batch overran its queue)
 constexpr bc_status kStatusRetry = static_cast<bc_status>(100);
 
 bc_status cuda_status(cudaError_t e) {
@@ -475,7 +449,7 @@ bool opts_valid(const bc_opts &o) {
          o.batch_k <= kK * kMaxWords &&
          (o.batch_k <= kK || o.schedule == BC_SCHED_AUTO || o.schedule == BC_SCHED_BATCH ||
           o.schedule == BC_SCHED_BATCH_QUEUE) &&
-         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_DENSE &&
+         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_QUEUE &&
          (o.normalize == 0 || o.normalize == 1) &&
          (o.scale_sampled == 0 || o.scale_sampled == 1) &&
          (o.out_device == 0 || o.out_device == 1) &&
@@ -488,17 +462,11 @@ int resolve_schedule(const bc_opts &o, const GraphDev &) {
 }
 
 
-// Frontier representation for BC_SCHED_BATCH: the queue form measured faster
-// than the dense-level form on every workload tried (R-MAT scales 16 and 20,
-// directed preferential attachment n = 2^20), so it is the default.
-int pick_batch_kind(const GraphDev &) { return WS_QUEUE; }
-
 // Grid of a persistent launch: the co-resident maximum for large graphs, a
 // smaller share of the GPU for small ones so that concurrent jobs overlap.
 int pick_grid(const bc_ctx *ctx, const GraphDev &g, int kind, bool fp64, int words) {
-  const int gmax = kind == WS_DENSE   ? ctx->grid_dense[fp64]
-                   : kind == WS_QUEUE ? ctx->grid_batch[word_index(words)][fp64]
-                                      : ctx->grid_plain[fp64];
+  const int gmax =
+      kind == WS_QUEUE ? ctx->grid_batch[word_index(words)][fp64] : ctx->grid_plain[fp64];
   if (const char *env = std::getenv("BC_GRID")) {
     int v = std::atoi(env);
     if (v > 0) return std::min(v, gmax);
@@ -957,7 +925,6 @@ bc_status ws_acquire(bc_ctx *ctx, const WsNeed &nd, cudaStream_t st, std::unique
   r->kind = nd.kind;
   r->words = nd.words;
   r->batch = nd.kind != WS_PLAIN;
-  r->dmax = nd.dmax;
   r->n = nd.n;
   r->cap = nd.cap;
   r->hcap = nd.hcap;
@@ -1002,15 +969,12 @@ void ws_release(bc_ctx *ctx, std::unique_ptr<WsRec> ws) {
 size_t job_footprint(const GraphRec &gr, int sched, const bc_opts &o, int64_t k) {
   const GraphDev &g = gr.dev;
   WsRec r;
-  const int kind = sched == BC_SCHED_PLAIN         ? WS_PLAIN
-                   : sched == BC_SCHED_BATCH_DENSE ? WS_DENSE
-                                                   : WS_QUEUE;
+  const int kind = sched == BC_SCHED_PLAIN ? WS_PLAIN : WS_QUEUE;
   const BatchShape bs = batch_shape(o, kind, k, gr.narrow, false);
   WsNeed nd = ws_need(g, kind, bs.kb, bs.words);
   r.kind = nd.kind;
   r.words = nd.words;
   r.batch = nd.kind != WS_PLAIN;
-  r.dmax = nd.dmax;
   r.n = nd.n;
   r.cap = nd.cap;
   r.hcap = nd.hcap;
@@ -1062,12 +1026,7 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   const bool fp64 = j->opts.delta_fp64 != 0;
   const int64_t n = g.n, k = j->k;
   cudaStream_t st = j->st;
-  // batches run on the dense-level kernel unless the graph is known to be
-  // deeper than its per-level masks; then on the queue kernel
-  const int kind = !batch                             ? WS_PLAIN
-                   : sched == BC_SCHED_BATCH_QUEUE || j->g->deep ? WS_QUEUE
-                   : sched == BC_SCHED_BATCH_DENSE               ? WS_DENSE
-                                                                 : pick_batch_kind(j->g->dev);
+  const int kind = batch ? WS_QUEUE : WS_PLAIN;
   j->kind = kind;
   const BatchShape bs = batch_shape(j->opts, kind, k, j->g->narrow, dbg != nullptr);
   // wider than one mask word: the queue kernel only
@@ -1218,9 +1177,8 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
         }
       }
     }
-    BC_TRY(kind == WS_DENSE   ? launch_dense(p, fp64, grid, st)
-           : kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words)
-                              : launch_plain(p, fp64, grid, st));
+    BC_TRY(kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words)
+                            : launch_plain(p, fp64, grid, st));
     ++j->batches;
     ++j->launches;
   }
@@ -1273,7 +1231,7 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.reached_pairs = (int64_t)j->h_cnt[CNT_REACHED];
   s.heavy_chunks = (int64_t)j->h_cnt[CNT_HEAVY];
   s.max_levels = (int32_t)j->h_cnt[CNT_MAXLEV];
-  s.kernel_kind = j->kind == WS_DENSE ? 3 : j->kind == WS_QUEUE ? 2 : 1;
+  s.kernel_kind = j->kind == WS_QUEUE ? 2 : 1;
   s.levels_sum = (int32_t)j->h_cnt[CNT_LEVELS];
   s.chunk_edges = kChunkCandidates[kTuneCandidates[j->cand].variant];
   s.batch_sources = j->kb;
@@ -1306,13 +1264,7 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.overflow_sources = novf;
   bc_status st = BC_OK;
   const int kerr = *j->h_err;
-  if (kerr == KERR_LEVELS) {
-    // deeper than the dense kernel's masks: no BC was written; rerun the job
-    // on the queue kernel
-    j->g->deep = true;
-    st = kStatusRetry;
-    j->ws->dirty = true;
-  } else if ((kerr == KERR_QUEUE || kerr == KERR_HEAVY) && j->words > 1) {
+  if ((kerr == KERR_QUEUE || kerr == KERR_HEAVY) && j->words > 1) {
     // a wide batch queued vertices at more distinct depths than its queue
     // holds: rerun the job with 64 sources per batch
     j->g->narrow = true;
@@ -1520,10 +1472,9 @@ bc_status bc_init(int device, void *cuda_stream, size_t hbm_budget_bytes, bc_ctx
       ctx->grid_batch[wi][f] = max_grid_batch(f != 0, device, 1 << wi);
       if (ctx->grid_batch[wi][f] <= 0) return BC_ERR_CUDA;
     }
-    ctx->grid_dense[f] = max_grid_dense(f != 0, device);
     ctx->grid_many[f] = max_grid_many(f != 0, device);
     ctx->grid_plain[f] = max_grid_plain(f != 0, device);
-    if (ctx->grid_plain[f] <= 0 || ctx->grid_dense[f] <= 0)
+    if (ctx->grid_plain[f] <= 0 || ctx->grid_many[f] <= 0)
       return BC_ERR_CUDA;
   }
   for (int i = 0; i < kMaxSlots; ++i)

@@ -139,50 +139,6 @@ template <typename DT> __device__ __forceinline__ DT warp_sum(DT v) {
   return v;
 }
 
-// Up to four set bits of a mask, lowest first (-1 when exhausted); clears them.
-struct Bits4 {
-  int j[4];
-  __device__ __forceinline__ explicit Bits4(uint64_t &m) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      j[k] = m ? __ffsll((long long)m) - 1 : -1;
-      m &= m - 1;
-    }
-  }
-};
-
-// Adds row[j] into acc[j] for every bit j of P (shared-memory atomics, up to
-// four loads in flight per lane); carries out of 64 bits are recorded in ovf.
-__device__ __forceinline__ void gather_counts(const uint64_t *row, uint64_t P,
-                                              unsigned long long *acc, uint64_t &ovf) {
-  while (P) {
-    const Bits4 q(P);
-    uint64_t x[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = q.j[k] >= 0 ? ldcg(row + q.j[k]) : 0ull;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (q.j[k] >= 0) {
-        const unsigned long long old = atomicAdd(acc + q.j[k], (unsigned long long)x[k]);
-        if (old + x[k] < old) ovf |= 1ull << q.j[k];
-      }
-  }
-}
-
-// Adds row[j] into acc[j] for every bit j of S (floating-point shared atomics).
-template <typename DT>
-__device__ __forceinline__ void gather_coeffs(const DT *row, uint64_t S, DT *acc) {
-  while (S) {
-    const Bits4 q(S);
-    DT y[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) y[k] = q.j[k] >= 0 ? ldcg(row + q.j[k]) : DT(0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (q.j[k] >= 0) atomicAdd(acc + q.j[k], y[k]);
-  }
-}
-
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
@@ -204,79 +160,6 @@ template <int U> struct LanesU {
     }
   }
 };
-
-// Full-width gathers: per step up to U of the round's shortest-path edges
-// (lanes with a non-empty mask, in lane order), lane j loading sources j and
-// 32+j of each edge's row when the mask has them; loads of the U edges are in
-// flight together and are added in edge order.
-
-// Path counts, 64-bit sums with the carry recorded (a carry means the true
-// count reached 2^64).
-template <int U>
-__device__ __forceinline__ void gather_counts_full(const uint64_t *base, int u, uint64_t P,
-                                                   int lane, uint64_t &s0, uint64_t &s1,
-                                                   bool &c0, bool &c1) {
-  unsigned bal = __ballot_sync(kFull, P != 0);
-  while (bal) {
-    const LanesU<U> q(bal);
-    uint64_t x0[U], x1[U];
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-      const int uu = shfl_or_zero(u, q.l[i]);
-      const uint64_t PP = shfl_or_zero(P, q.l[i]);
-      const uint64_t *row = base + (size_t)uu * kK;
-      x0[i] = ((PP >> lane) & 1ull) ? ldcg(row + lane) : 0ull;
-      x1[i] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 32 + lane) : 0ull;
-    }
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-      s0 += x0[i];
-      c0 |= s0 < x0[i];
-      s1 += x1[i];
-      c1 |= s1 < x1[i];
-    }
-  }
-}
-
-// Dense kernel, heavy chunks: path-count pull over in-edges [eb, ee) of
-// entry w (mask F) from the level l-1 dense mask Pm.  Lane j owns sources j
-// and j+32; per round the warp gathers the predecessor rows of
-// BC_GATHER_UNROLL shortest-path edges and adds them in edge order.  Counts
-// saturate at 2^64-1 on carry.
-__device__ __forceinline__ void batch_pull_sigma(const KParams &p, uint64_t F, int64_t eb,
-                                                 int64_t ee, const uint64_t *Pm, int lane,
-                                                 unsigned long long *wacc, uint64_t &s0,
-                                                 uint64_t &s1, bool &o0, bool &o1,
-                                                 unsigned long long &dag) {
-  (void)wacc;
-  constexpr int U = BC_GATHER_UNROLL;
-  unsigned long long nd = 0;
-  for (int64_t base = eb; base < ee; base += kWarp) {
-    const int64_t e = base + lane;
-    int u = 0;
-    uint64_t P = 0;
-    if (e < ee) {
-      u = __ldg(p.g.in_idx + e);
-      P = ldcg(Pm + u) & F;
-    }
-    nd += __popcll(P);
-    gather_counts_full<U>(p.w.sigma, u, P, lane, s0, s1, o0, o1);
-  }
-  nd = warp_sum_u64(nd);
-  if (lane == 0) dag += nd;
-}
-
-// Batch: writes the path counts of entry w (mask F) and records overflow.
-__device__ __forceinline__ void batch_store_sigma(const KParams &p, int w, uint64_t F,
-                                                  uint64_t s0, uint64_t s1, bool o0, bool o1,
-                                                  int lane) {
-  uint64_t *row = p.w.sigma + (size_t)w * kK;
-  if ((F >> lane) & 1ull) row[lane] = o0 ? ~0ull : s0;
-  if ((F >> (lane + 32)) & 1ull) row[32 + lane] = o1 ? ~0ull : s1;
-  const uint64_t ob =
-      ((uint64_t)__ballot_sync(kFull, o0) | ((uint64_t)__ballot_sync(kFull, o1) << 32)) & F;
-  if (ob && lane == 0) atomicOr(&p.w.ctl->ovf[0], (unsigned long long)ob);
-}
 
 // ---------------------------------------------------------------------------
 // Source masks of W 64-bit words (64*W sources per batch).  Lane j owns the
@@ -368,15 +251,34 @@ template <int W> struct GatherUnroll {
   static constexpr int value = W == 1 ? BC_GATHER_UNROLL : (W == 2 ? 2 : 1);
 };
 
+#ifndef BC_GATHER_FORM
+#define BC_GATHER_FORM 1 // 1: carry-counting adds, 32-bit lane tests, 4-byte rows twice as deep
+#endif
+
+// Edges per round of the dependency-coefficient gather: as many as keep 8
+// 8-byte (16 4-byte) values per lane in flight.
+template <int W, typename DT> struct CoeffUnroll {
+  static constexpr int value =
+      (BC_GATHER_FORM >= 1 && sizeof(DT) == 4) ? 2 * GatherUnroll<W>::value : GatherUnroll<W>::value;
+};
+
+// s += x, with the carry out of bit 63 added to c (c counts carries).
+__device__ __forceinline__ void add_count_carry(uint64_t &s, uint64_t x, unsigned &c) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(s), "+r"(c) : "l"(x));
+}
+
 // Path counts over the round's shortest-path edges (lanes whose mask P is not
 // empty, in lane order): lane j adds row[32*i + j] of each edge's row for
-// every slot i whose bit is set; 64-bit sums, carry of slot i recorded in
-// bit i of cbits (a carry means the true count reached 2^64).
-template <int W>
+// every slot i whose bit is set, in edge order.  kExact: the carry of slot
+// i is recorded in bit i of cbits (a carry means the true count reached
+// 2^64).  Otherwise cbits only counts carries: any carry sends the caller to
+// the exact form, which is rare (counts near 2^64) and gives the same sums.
+template <int W, bool kExact = true>
 __device__ __forceinline__ void gather_counts_w(const uint64_t *base, int u, const Mask<W> &P,
                                                 int lane, uint64_t (&s)[2 * W],
                                                 unsigned &cbits) {
   constexpr int U = GatherUnroll<W>::value;
+  const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, P.any());
   while (bal) {
     const LanesU<U> q(bal);
@@ -384,30 +286,36 @@ __device__ __forceinline__ void gather_counts_w(const uint64_t *base, int u, con
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const int uu = shfl_or_zero(u, q.l[i]);
-      const uint64_t *row = base + (size_t)uu * (kK * W);
+      const uint64_t *row = base + (size_t)uu * (kK * W) + lane;
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
         const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
-        x[i][2 * wi] = ((PP >> lane) & 1ull) ? ldcg(row + 64 * wi + lane) : 0ull;
-        x[i][2 * wi + 1] = ((PP >> (lane + 32)) & 1ull) ? ldcg(row + 64 * wi + 32 + lane) : 0ull;
+        const unsigned lo = (unsigned)PP, hi = (unsigned)(PP >> 32);
+        x[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : 0ull;
+        x[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : 0ull;
       }
     }
 #pragma unroll
     for (int i = 0; i < U; ++i)
 #pragma unroll
       for (int t = 0; t < 2 * W; ++t) {
-        s[t] += x[i][t];
-        cbits |= (s[t] < x[i][t] ? 1u : 0u) << t;
+        if (kExact || BC_GATHER_FORM == 0) {
+          s[t] += x[i][t];
+          cbits |= (s[t] < x[i][t] ? 1u : 0u) << t;
+        } else {
+          add_count_carry(s[t], x[i][t], cbits);
+        }
       }
   }
 }
 
 // Dependency coefficients over the round's successor edges, added in edge
-// order.
+// order (a missing edge adds +0, which changes no sum of non-negative terms).
 template <int W, typename DT>
 __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mask<W> &S,
                                                 int lane, DT (&a)[2 * W]) {
-  constexpr int U = GatherUnroll<W>::value;
+  constexpr int U = CoeffUnroll<W, DT>::value;
+  const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, S.any());
   while (bal) {
     const LanesU<U> q(bal);
@@ -415,20 +323,19 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const int xx = shfl_or_zero(x, q.l[i]);
-      const DT *row = base + (size_t)xx * (kK * W);
+      const DT *row = base + (size_t)xx * (kK * W) + lane;
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
         const uint64_t SS = shfl_or_zero(S.w[wi], q.l[i]);
-        y[i][2 * wi] = ((SS >> lane) & 1ull) ? ldcg(row + 64 * wi + lane) : DT(0);
-        y[i][2 * wi + 1] = ((SS >> (lane + 32)) & 1ull) ? ldcg(row + 64 * wi + 32 + lane) : DT(0);
+        const unsigned lo = (unsigned)SS, hi = (unsigned)(SS >> 32);
+        y[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : DT(0);
+        y[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : DT(0);
       }
     }
 #pragma unroll
     for (int i = 0; i < U; ++i)
-      if (q.l[i] >= 0) {
 #pragma unroll
-        for (int t = 0; t < 2 * W; ++t) a[t] += y[i][t];
-      }
+      for (int t = 0; t < 2 * W; ++t) a[t] += y[i][t];
   }
 }
 

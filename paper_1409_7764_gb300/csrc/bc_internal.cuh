@@ -51,7 +51,6 @@ enum : int {
   KERR_QUEUE = 2,    // frontier queue capacity exceeded
   KERR_HEAVY = 3,    // heavy-entry list capacity exceeded
   KERR_CHUNKS = 4,   // heavy chunk scratch exceeded
-  KERR_LEVELS = 5,   // dense kernel: more levels than the per-level masks hold
   KERR_GRAB = 6,     // more work items per fetch than a header round holds (host bug)
 };
 
@@ -70,8 +69,6 @@ enum : int {
   CNT_N = 10
 };
 
-constexpr int kGroup = 8;      // dense kernel: vertices per light work group
-constexpr int kDenseLevels = 64; // dense kernel: default level cap
 
 // Per-workspace control block; the host zeroes it once per job.
 struct Ctl {
@@ -115,7 +112,7 @@ struct Work {
   int64_t *qoff = nullptr;    // [n+3] start of each level in qv
   unsigned long long *hpack = nullptr; // [n+3] per level: (heavy count << 32) | chunk total
   int64_t *hoff = nullptr;    // [n+3] start of each level's heavy list
-  int64_t *hq_e = nullptr;    // [hcap] queue position (queue kernel) or vertex id (dense kernel)
+  int64_t *hq_e = nullptr;    // [hcap] queue position
                               // of each heavy entry
   int64_t *hq_c = nullptr;    // [hcap] first chunk of each heavy entry within its level
   unsigned *harrive = nullptr; // [hcap] chunk arrivals per heavy entry
@@ -125,9 +122,6 @@ struct Work {
   int64_t chunk_cap = 0;
   uint64_t *sigma = nullptr;  // [n][k_max] path counts
   void *cdep = nullptr;       // [n][k_max] (1 + delta) / sigma, float or double
-  uint64_t *lm = nullptr;     // dense kernel: [dmax][n] per-level frontier masks
-  int32_t dmax = 0;           // levels lm can hold
-  unsigned *lvl_flag = nullptr; // dense kernel: [dmax + 2] level non-empty flags
   Ctl *ctl = nullptr;
 };
 
@@ -173,8 +167,6 @@ cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t 
 int max_grid_many(bool fp64, int device);
 cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
-cudaError_t launch_dense(const KParams &p, bool fp64, int grid, cudaStream_t st);
-int max_grid_dense(bool fp64, int device);
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
 cudaError_t launch_estimate(const double *sum, const double *sumsq, int64_t n, int64_t k,
                             double factor, double *est, double *err, cudaStream_t st);

@@ -179,6 +179,38 @@ __device__ __forceinline__ void stage_new(const KParams &p, const LevelView &lv,
   nst += c;
 }
 
+// Path-count pull of an entry (mask F) over its in-edges [ib, ib + din)
+// from the level l-1 masks Pm, in edge order.
+template <int W, bool kExact>
+__device__ __forceinline__ void pull_counts(const KParams &p, const Mask<W> &F, int ib, int din,
+                                            const uint64_t *Pm, int lane, uint64_t (&s)[2 * W],
+                                            unsigned &cbits, unsigned long long &dag) {
+  for (int r = 0; r < din; r += kWarp) {
+    const int t = r + lane;
+    int u = 0;
+    Mask<W> P = Mask<W>::zero();
+    if (t < din) {
+      u = __ldg(p.g.in_idx + ib + t);
+      P = load_mask<W>(Pm, u) & F;
+    }
+    dag += P.popc(); // per lane; the warp's counters are summed at the flush
+    gather_counts_w<W, kExact>(p.w.sigma, u, P, lane, s, cbits);
+  }
+}
+
+// The same pull again with every slot's carry recorded, for an entry whose
+// fast pull saw a carry (some count reached 2^64): same sums, flags per slot.
+template <int W>
+__device__ __forceinline__ void exact_counts(const KParams &p, const Mask<W> &F, int ib, int din,
+                                          const uint64_t *Pm, int lane, uint64_t (&s)[2 * W],
+                                          unsigned &cbits) {
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i) s[i] = 0;
+  cbits = 0;
+  unsigned long long dag = 0; // counted by the fast pull already
+  pull_counts<W, true>(p, F, ib, din, Pm, lane, s, cbits, dag);
+}
+
 // Forward work of one frontier entry (mask F) at level l: the path-count
 // pull over in-edges [ib, ie) and the discovery push over out-edges
 // [ob, oe).  A vertex x gets the bits F & ~visited[x], OR-ed into its
@@ -198,21 +230,14 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
                                          unsigned &cbits, unsigned long long &dag) {
   const int din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
   const int claim_to = lv.lvl + 2;
+  constexpr bool kFast = BC_GATHER_FORM >= 1;
+  unsigned carries = 0; // fast form: carries out of bit 63 (any -> exact rerun)
   if constexpr (W >= 2) {
     // wide masks: the pull and the push run as two loops, so the registers
     // of the path-count gathers and of the discovery masks are not live
     // together
-    for (int r = 0; r < din; r += kWarp) {
-      const int t = r + lane;
-      int u = 0;
-      Mask<W> P = Mask<W>::zero();
-      if (t < din) {
-        u = __ldg(p.g.in_idx + ib + t);
-        P = load_mask<W>(Pm, u) & F;
-      }
-      dag += P.popc(); // per lane; the warp's counters are summed at the flush
-      gather_counts_w<W>(p.w.sigma, u, P, lane, s, cbits);
-    }
+    pull_counts<W, !kFast>(p, F, ib, din, Pm, lane, s, kFast ? carries : cbits, dag);
+    if (kFast && __any_sync(kFull, carries != 0)) exact_counts<W>(p, F, ib, din, Pm, lane, s, cbits);
     for (int r = 0; r < dout; r += kWarp) {
       const int t = r + lane;
       int x = 0;
@@ -253,9 +278,10 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
       dag += __popcll(P); // per lane; the warp's counters are summed at the flush
       Mask<1> PM;
       PM.w[0] = P;
-      gather_counts_w<1>(p.w.sigma, u, PM, lane, s, cbits);
+      gather_counts_w<1, !kFast>(p.w.sigma, u, PM, lane, s, kFast ? carries : cbits);
       stage_new(p, lv, nb != 0 && old == 0, x, stage, nst, lane);
     }
+    if (kFast && __any_sync(kFull, carries != 0)) exact_counts<1>(p, F, ib, din, Pm, lane, s, cbits);
   }
 }
 

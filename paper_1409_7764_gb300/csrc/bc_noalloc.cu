@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 using namespace bcgpu;
@@ -79,27 +80,41 @@ constexpr ScratchLayout kLay = make_layout();
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kLay.total];
 
 struct DeviceSetup {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
+  std::mutex mu;
+  std::atomic<bool> ready{false}; // set once, only after a successful set-up
   unsigned char *base = nullptr;
   int grid[2] = {0, 0};
 };
 
 DeviceSetup g_setup[kMaxDevices];
 
-// Per-device set-up, run by the first call on that device with the device
-// current: resolve the scratch array's device address and the co-resident
-// grid size of the batched kernel.  Neither allocates.
-void setup_device(int dev) {
+// Per-device set-up, run with the device current by the first call on that
+// device that finds it missing: resolve the scratch array's device address
+// and the co-resident grid size of the batched kernel.  Neither allocates.
+// Only success is remembered; a failed attempt is retried by the next call.
+// An error already pending on this thread (left by earlier, unrelated work)
+// is reported as it is and not cleared, so the lookup below is never blamed
+// for it and the caller still sees it.
+cudaError_t ensure_setup(int dev) {
   DeviceSetup &s = g_setup[dev];
+  if (s.ready.load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(s.mu);
+  if (s.ready.load(std::memory_order_relaxed)) return cudaSuccess;
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return e;
   void *ptr = nullptr;
-  s.err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-  if (s.err != cudaSuccess) return;
-  s.base = static_cast<unsigned char *>(ptr);
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  int grid[2];
   for (int f = 0; f < 2; ++f) {
-    s.grid[f] = max_grid_batch(f != 0, dev);
-    if (s.grid[f] <= 0) s.err = cudaErrorUnknown;
+    grid[f] = max_grid_batch(f != 0, dev);
+    if (grid[f] <= 0) return cudaErrorUnknown;
   }
+  s.base = static_cast<unsigned char *>(ptr);
+  s.grid[0] = grid[0];
+  s.grid[1] = grid[1];
+  s.ready.store(true, std::memory_order_release);
+  return cudaSuccess;
 }
 
 bc_status to_status(cudaError_t e) {
@@ -124,9 +139,8 @@ extern "C" bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *c
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BC_ERR_CUDA;
+  if (ensure_setup(dev) != cudaSuccess) return BC_ERR_CUDA;
   DeviceSetup &ds = g_setup[dev];
-  std::call_once(ds.once, setup_device, dev);
-  if (ds.err != cudaSuccess) return BC_ERR_CUDA;
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   unsigned char *b = ds.base;
@@ -186,7 +200,7 @@ extern "C" bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *c
   if (e != cudaSuccess) return to_status(e);
 
   const int64_t want = ((int64_t)n * 8 + kBlock - 1) / kBlock; // ~8 threads per vertex
-  const int grid = (int)std::min<int64_t>(ds.grid[fp64], std::max<int64_t>(2, want));
+  int grid = (int)std::min<int64_t>(ds.grid[fp64], std::max<int64_t>(2, want));
   for (int32_t b0 = 0; b0 < k; b0 += kK) {
     const int32_t kb = std::min<int32_t>(kK, k - b0);
     // stream-ordered after the previous batch's kernel, so the slot is free
@@ -195,6 +209,14 @@ extern "C" bc_status bc_sources_noalloc(const int32_t *row_ptr, const int32_t *c
     p.src = d_src;
     p.k = kb;
     e = launch_batch(p, fp64, grid, st);
+    while (e == cudaErrorCooperativeLaunchTooLarge && grid > 1) {
+      // fewer blocks fit at once than at set-up (e.g. the GPU is partitioned
+      // differently now): the launch was refused before running; clear that
+      // error and retry with half the grid (the kernel works with any grid)
+      (void)cudaGetLastError();
+      grid /= 2;
+      e = launch_batch(p, fp64, grid, st);
+    }
     if (e != cudaSuccess) return to_status(e);
   }
 
