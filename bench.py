@@ -475,6 +475,12 @@ def run_ours(args, w, name):
             ctx.sources(G, sample, out=out, **dict(opts, delta_fp64=f64, batch_k=kb))
             precision[name_] = rel_errors(out.cpu().numpy(), ref_bc)
 
+    if rank == 0 and not args.quick and args.line_serve_requests > 0:
+        # the serving loop at stated load, compactly: 2 seeds per scale in the
+        # graph pool, line_serve_requests requests per offered load
+        extra["serving"] = serving_experiment(ctx, args.line_serve_requests, [1, 2],
+                                              args.serve_seed)
+
     if rank == 0:
         line = {
             "metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS",
@@ -640,60 +646,91 @@ def run_many(args):
 
 # ---- serving ----------------------------------------------------------------------
 
-def run_serving(args):
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
-    import torch
-    import paper_1409_7764_gb300 as bc
+def serving_experiment(ctx, n_requests, seeds, serve_seed):
+    """Open-loop serving of BC requests on a pool of device-resident R-MAT
+    graphs (scales 8..20, edge factor 16, one per seed and scale): exact BC
+    up to scale 14, 1024 seeded sampled sources above.  Capacity comes from
+    solo service times; at offered loads rho = 0.5 and 0.8 of it, the same
+    Poisson request stream runs with FP32 and then FP64 dependencies, so the
+    FP32 results can be compared with the FP64 ones request by request."""
     from paper_1409_7764_gb300.serving import (Request, poisson_arrivals, run_open_loop,
                                                 solo_service_times, summarize)
     scales = list(range(8, 21))
-    seeds = [1, 2, 3, 4]
-    ctx = bc.Context(0)
     pool = {}
-    for s in scales:
+    for sc in scales:
         for sd in seeds:
-            g = bcgen.rmat(s, 16, seed=sd)
-            pool[(s, sd)] = ctx.create_graph(g.row_ptr, g.col_idx)
-    rs = np.random.default_rng(args.serve_seed)
+            g = bcgen.rmat(sc, 16, seed=sd)
+            pool[(sc, sd)] = ctx.create_graph(g.row_ptr, g.col_idx)
+    rs = np.random.default_rng(serve_seed)
 
-    def make_requests(count, fp64):
+    def make_requests(count):
         reqs = []
         for i in range(count):
-            s = int(rs.integers(8, 21))
-            G = pool[(s, seeds[int(rs.integers(0, 4))])]
-            srcs = None if s <= 14 else bcgen.sample_sources(G.n, 1024, seed=1000 + i)
-            reqs.append(Request(G, srcs, dict(delta_fp64=fp64)))
+            sc = int(rs.integers(8, 21))
+            G = pool[(sc, seeds[int(rs.integers(0, len(seeds)))])]
+            srcs = None if sc <= 14 else bcgen.sample_sources(G.n, 1024, seed=1000 + i)
+            reqs.append(Request(G, srcs, {}))
         return reqs
 
-    out = {}
+    def with_opts(reqs, fp64):
+        return [Request(r.graph, r.sources, dict(delta_fp64=fp64)) for r in reqs]
+
+    out = {"fp32": {}, "fp64": {}, "fp32_vs_fp64": {}}
+    taus = {}
     for fp64 in (False, True):
-        key = "fp64" if fp64 else "fp32"
-        # capacity from solo service times of one request per pool graph
-        probe = []
-        for s in scales:
-            G = pool[(s, 1)]
-            probe.append(Request(G, None if s <= 14 else bcgen.sample_sources(G.n, 1024, seed=7),
-                                 dict(delta_fp64=fp64)))
+        probe = [Request(pool[(sc, seeds[0])],
+                         None if sc <= 14 else bcgen.sample_sources(pool[(sc, seeds[0])].n, 1024,
+                                                                    seed=7),
+                         dict(delta_fp64=fp64)) for sc in scales]
         solo_service_times(ctx, probe[:3])  # warm-up
         tau = float(np.mean(solo_service_times(ctx, probe)))
-        res = {"mean_solo_ms": tau * 1e3, "capacity_rps": 1.0 / tau}
-        for rho in (0.5, 0.8):
-            reqs = make_requests(args.serve_requests, fp64)
-            arr = poisson_arrivals(len(reqs), rho / tau, seed=args.serve_seed + int(rho * 10))
-            recs = run_open_loop(ctx, reqs, arr)
-            res[f"rho{rho}"] = summarize(recs)
-        out[key] = res
+        taus[fp64] = tau
+        key = "fp64" if fp64 else "fp32"
+        out[key]["mean_solo_ms"] = tau * 1e3
+        out[key]["capacity_rps"] = 1.0 / tau
+    for rho in (0.5, 0.8):
+        reqs = make_requests(n_requests)
+        got = {}
+        for fp64 in (False, True):
+            arr = poisson_arrivals(len(reqs), rho / taus[fp64], seed=serve_seed + int(rho * 10))
+            results = {}
+            recs = run_open_loop(ctx, with_opts(reqs, fp64), arr, results=results)
+            out["fp64" if fp64 else "fp32"][f"rho{rho}"] = summarize(recs)
+            got[fp64] = results
+        # each request's FP32 result against its FP64 result
+        worst = []
+        for i, r64 in got[True].items():
+            r32 = got[False].get(i)
+            if r32 is None or r64 is None:
+                continue
+            nz = r64 != 0
+            worst.append(float(np.max(np.abs(r32[nz] - r64[nz]) / np.abs(r64[nz])))
+                         if nz.any() else 0.0)
+        out["fp32_vs_fp64"][f"rho{rho}"] = {
+            "requests": len(worst), "max_rel": max(worst) if worst else None,
+            "p99_rel": float(np.percentile(worst, 99)) if worst else None}
+    for G in pool.values():
+        ctx.destroy_graph(G)
+    out["pool"] = f"R-MAT scales 8..20 x {len(seeds)} seeds, edge factor 16"
+    out["request_mix"] = "scale uniform 8..20; exact for scale <= 14, 1024 seeded sources above"
+    out["arrivals"] = "Poisson at rho x capacity (capacity from solo service times)"
+    return out
+
+
+def run_serving(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import paper_1409_7764_gb300 as bc
+    ctx = bc.Context(0)
+    out = serving_experiment(ctx, args.serve_requests, [1, 2, 3, 4], args.serve_seed)
     main = out["fp32"]["rho0.8"]
     line = {
         "metric": "BC GTEPS (sources*m/s)", "value": main["gteps"], "unit": "GTEPS", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
-        "config": {"workload": "serving", "pool": "R-MAT scales 8..20 x 4 seeds, edge factor 16",
-                   "requests": args.serve_requests,
-                   "request_mix": "scale uniform 8..20; exact for scale <= 14, "
-                                  "1024 seeded sources above",
-                   "arrivals": "Poisson at rho x capacity (capacity from solo service times)"},
+        "config": {"workload": "serving", "requests": args.serve_requests,
+                   "pool": out["pool"], "request_mix": out["request_mix"],
+                   "arrivals": out["arrivals"]},
         "serving": out,
         "gpu_launches": None,
     }
@@ -724,7 +761,10 @@ def main():
     ap.add_argument("--keep-source-order", action="store_true",
                     help="batches take the sources in the given order instead of the library's grouping")
     ap.add_argument("--many-count", type=int, default=10000)
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--line-serve-requests", type=int, default=500,
+                    help="requests per offered load of the serving record in the main line "
+                         "(0: none)")
     ap.add_argument("--serve-seed", type=int, default=1)
     args = ap.parse_args()
     if args.workload == "rmat-many10k" and args.impl == "ours":

@@ -62,13 +62,21 @@ typedef enum {
   BC_ERR_INTERNAL = -9        /* device-side capacity check failed (a bug) */
 } bc_status;
 
-/* Work schedules.  AUTO picks per graph. */
+/* Work schedules.  AUTO is BATCH. */
 enum {
   BC_SCHED_AUTO = 0,
-  BC_SCHED_PLAIN = 1,       /* one source per kernel launch, whole GPU, level-synchronous */
-  BC_SCHED_BATCH = 2,       /* up to 256 sources per launch, bitset frontiers, per-level
-                               frontier queues, [n][k] state */
-  BC_SCHED_BATCH_QUEUE = 3  /* the same as BATCH */
+  BC_SCHED_PLAIN = 1,        /* one source per kernel launch, level-synchronous: the whole GPU
+                                per source, or one thread block per source on small graphs */
+  BC_SCHED_BATCH = 2,        /* up to 256 sources per launch, bitset frontiers, per-level
+                                frontier queues, [n][k] state.  The first job on a graph with
+                                enough sources times trial batches and keeps, per graph, the
+                                fastest batch width (when batch_k = 0) and work split */
+  BC_SCHED_BATCH_QUEUE = 3,  /* the same as BATCH */
+  BC_SCHED_BATCH_VERTEX = 4, /* BATCH with a fixed vertex-centric split: one warp per frontier
+                                entry whatever its degree */
+  BC_SCHED_BATCH_WARP = 5,   /* BATCH, warp-centric: entries with more than 256 in- plus
+                                out-edges cut into 256-edge chunks, one warp each */
+  BC_SCHED_BATCH_EDGE = 6    /* BATCH, edge-centric leaning: 128-edge chunks */
 };
 
 typedef struct {
@@ -92,6 +100,14 @@ typedef struct {
                             edge scans are shared by more sources; 1 = batches take the
                             sources in the given order.  The result is the same sum over
                             the sources, up to floating-point summation order. */
+  int32_t direction;     /* path-count step of each forward level l >= 1 of the batched
+                            schedules: 0 (default) = per level, pull over the in-edges of
+                            level l unless pushing from level l-1 along its out-edges scans
+                            several times fewer edges; 1 = always pull; 2 = always push.
+                            Pulling adds in a fixed order, pushing with 64-bit integer
+                            atomics; both give the same exact counts.  A pushed count of
+                            2^32 or more makes the job rerun pulling (and later jobs on
+                            that graph pull) */
 } bc_opts;
 
 /* Per-call statistics.  Counters feed the bytes model of the roofline. */
@@ -116,6 +132,7 @@ typedef struct {
   int32_t grab;              /* work items a warp fetched at a time in the last launch */
   int32_t batch_sources;     /* sources per batch in the last launch */
   int32_t mask_words;        /* 64-bit words per source mask in the last launch (1, 2 or 4) */
+  int32_t push_levels;       /* forward levels whose path counts were pushed, over all batches */
 } bc_stats;
 
 /* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t

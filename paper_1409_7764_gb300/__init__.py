@@ -29,7 +29,11 @@ __all__ = [
 ]
 
 _SCHED = {"auto": BC_SCHED_AUTO, "plain": BC_SCHED_PLAIN, "batch": BC_SCHED_BATCH,
-          "batch_queue": capi.BC_SCHED_BATCH_QUEUE}
+          "batch_queue": capi.BC_SCHED_BATCH_QUEUE, "batch_vertex": capi.BC_SCHED_BATCH_VERTEX,
+          "batch_warp": capi.BC_SCHED_BATCH_WARP, "batch_edge": capi.BC_SCHED_BATCH_EDGE}
+
+
+_DIRECTION = {"auto": 0, "pull": 1, "push": 2}
 
 
 def load():
@@ -54,7 +58,8 @@ def _check(rc: int, what: str):
 
 def make_opts(delta_fp64: bool = False, batch_k: int = 0, schedule="auto",
               normalize: bool = False, scale_sampled: bool = False,
-              out_device: bool = False, keep_source_order: bool = False) -> bc_opts:
+              out_device: bool = False, keep_source_order: bool = False,
+              direction="auto") -> bc_opts:
     o = bc_opts()
     o.delta_fp64 = int(bool(delta_fp64))
     o.batch_k = int(batch_k)
@@ -63,6 +68,7 @@ def make_opts(delta_fp64: bool = False, batch_k: int = 0, schedule="auto",
     o.scale_sampled = int(bool(scale_sampled))
     o.out_device = int(bool(out_device))
     o.source_order = int(bool(keep_source_order))
+    o.direction = _DIRECTION[direction] if isinstance(direction, str) else int(direction)
     return o
 
 

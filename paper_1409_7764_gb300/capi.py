@@ -26,6 +26,9 @@ BC_SCHED_AUTO = 0
 BC_SCHED_PLAIN = 1
 BC_SCHED_BATCH = 2
 BC_SCHED_BATCH_QUEUE = 3
+BC_SCHED_BATCH_VERTEX = 4
+BC_SCHED_BATCH_WARP = 5
+BC_SCHED_BATCH_EDGE = 6
 
 # every symbol include/bc_gb300.h declares
 EXPORTED = [
@@ -42,7 +45,7 @@ class bc_opts(ctypes.Structure):
     _fields_ = [("delta_fp64", ctypes.c_int32), ("batch_k", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("normalize", ctypes.c_int32),
                 ("scale_sampled", ctypes.c_int32), ("out_device", ctypes.c_int32),
-                ("source_order", ctypes.c_int32)]
+                ("source_order", ctypes.c_int32), ("direction", ctypes.c_int32)]
 
 
 class bc_stats(ctypes.Structure):
@@ -55,7 +58,8 @@ class bc_stats(ctypes.Structure):
                 ("heavy_chunks", ctypes.c_int64), ("kernel_kind", ctypes.c_int32),
                 ("levels_sum", ctypes.c_int32),
                 ("chunk_edges", ctypes.c_int32), ("grab", ctypes.c_int32),
-                ("batch_sources", ctypes.c_int32), ("mask_words", ctypes.c_int32)]
+                ("batch_sources", ctypes.c_int32), ("mask_words", ctypes.c_int32),
+                ("push_levels", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

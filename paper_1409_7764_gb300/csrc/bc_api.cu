@@ -79,9 +79,13 @@ struct GraphRec {
   // per-graph tuning of the batched kernel, per batch width (1, 2, 4 mask
   // words): chunk variant and grab size (-1: not tuned yet)
   std::atomic<int> tuned[3] = {-1, -1, -1};
+  // mask words the width trial found fastest per source (0: not tried yet)
+  std::atomic<int> tuned_words{0};
   // a batch wider than 64 sources overran its frontier queue or heavy list
   // (sized for 64 distinct depths per vertex): later jobs use 64 sources
   std::atomic<bool> narrow{false};
+  // a pushed path count was 2^32 or more: later jobs pull every level
+  std::atomic<bool> no_push{false};
   // batch composition (see order_key): host copies of the out-CSR
   // offsets and of the two-hop walk counts; every vertex in batch order, made
   // on first need (kept on the host and in d_order)
@@ -151,20 +155,27 @@ std::vector<int32_t> batch_order(const std::vector<int32_t> &row_ptr,
 // Graphs up to this many vertices get their batch order at creation.
 constexpr int32_t kEagerOrderN = 1 << 16;
 
-// Launch configurations the tuner compares: (chunk variant, items per fetch).
+// Launch configurations the tuner compares: (work split, items per fetch).
+// The splits are kChunkCandidates: warp-centric with 256-edge chunks of hubs
+// (the default), edge-centric leaning 128-edge chunks, coarser 512-edge
+// chunks, vertex-centric (no split); the fourth candidate takes one item per
+// counter fetch instead of two.
 struct TuneCandidate {
   int variant;
   int grab;
 };
-constexpr TuneCandidate kTuneCandidates[] = {{0, 2}, {1, 2}, {2, 2}, {0, 1}};
+constexpr TuneCandidate kTuneCandidates[] = {
+    {kSplitWarp, 2}, {kSplitEdge, 2}, {kSplitWarp512, 2}, {kSplitWarp, 1}, {kSplitVertex, 2}};
 constexpr bool grabs_fit() {
   for (const TuneCandidate &c : kTuneCandidates)
     if (c.grab < 1 || c.grab > kGrabMax) return false;
   return kGrabDefault <= kGrabMax;
 }
 static_assert(grabs_fit(), "a fetch larger than the kernels' header rounds hold");
-constexpr int kNumTune = 4;
+constexpr int kNumTune = 5;
 constexpr int kTuneRounds = 2; // trial batches per candidate
+// Batch widths (mask words) the width trial compares, widest first.
+constexpr int kWidthTrial[3] = {4, 2, 1};
 
 enum WsKind { WS_PLAIN = 0, WS_QUEUE = 1 };
 
@@ -172,9 +183,12 @@ struct WsRec {
   bool batch = true;
   int kind = WS_QUEUE;
   int words = 1; // 64-bit words per source mask (queue kernel: 1, 2 or 4)
+  int slots = 1; // plain, one block per source: copies for concurrent launches
   int32_t n = 0;
   int64_t cap = 0, hcap = 0, chunk_cap = 0;
-  Work w;
+  Work w;                   // the workspace (slot 0)
+  size_t slot_bytes = 0;    // stride between slot copies
+  double *parts = nullptr;  // slots > 1: [slots][n] BC partial sums, one per slot
   void *mem = nullptr;
   size_t bytes = 0;
   bool dirty = false;
@@ -183,10 +197,11 @@ struct WsRec {
 struct WsNeed {
   int kind;
   int words;
+  int slots;
   int32_t n;
   int64_t cap, hcap, chunk_cap;
   bool fits(const WsRec &r) const {
-    if (r.kind != kind || r.words != words || r.n < n || r.hcap < hcap ||
+    if (r.kind != kind || r.words != words || r.slots < slots || r.n < n || r.hcap < hcap ||
         r.chunk_cap < chunk_cap)
       return false;
     return r.cap >= cap;
@@ -213,10 +228,11 @@ BatchShape batch_shape(const bc_opts &o, int kind, int64_t k, bool narrow, bool 
 
 int word_index(int words) { return words == 1 ? 0 : words == 2 ? 1 : 2; }
 
-WsNeed ws_need(const GraphDev &g, int kind, int kb, int words) {
+WsNeed ws_need(const GraphDev &g, int kind, int kb, int words, int slots = 1) {
   WsNeed nd;
   nd.kind = kind;
   nd.words = kind == WS_QUEUE ? words : 1;
+  nd.slots = kind == WS_PLAIN ? slots : 1;
   nd.n = g.n;
   // a vertex is queued at most once per distinct depth among the batch's
   // sources; wider batches are sized for 64 depths (overruns are detected)
@@ -227,8 +243,8 @@ WsNeed ws_need(const GraphDev &g, int kind, int kb, int words) {
   return nd;
 }
 
-// Lays out (mem == nullptr: only sizes) the arrays of a workspace.
-size_t ws_layout(WsRec &r, char *mem) {
+// Lays out (mem == nullptr: only sizes) the arrays of one workspace copy.
+size_t ws_layout_one(WsRec &r, char *mem) {
   Carver c;
   c.base = mem;
   const size_t n = (size_t)r.n;
@@ -245,6 +261,7 @@ size_t ws_layout(WsRec &r, char *mem) {
     w.fr = c.take<uint64_t>(4 * n * words);
     w.qm = c.take<uint64_t>((size_t)r.cap * words);
     w.claim = words > 1 ? c.take<int32_t>(n) : nullptr;
+    w.lsum = c.take<unsigned long long>(2 * (n + 3));
     w.d = nullptr;
   } else {
     w.d = c.take<int32_t>(n);
@@ -269,11 +286,34 @@ size_t ws_layout(WsRec &r, char *mem) {
   return align_up(c.off, 256);
 }
 
+// Lays out a workspace: one copy, or for the one-block plain form `slots`
+// copies back to back and then one BC partial vector per copy.
+size_t ws_layout(WsRec &r, char *mem) {
+  const size_t one = ws_layout_one(r, mem);
+  if (r.slots <= 1) {
+    r.slot_bytes = one;
+    r.parts = nullptr;
+    return one;
+  }
+  r.slot_bytes = one;
+  r.parts = mem ? reinterpret_cast<double *>(mem + one * (size_t)r.slots) : nullptr;
+  return align_up(one * (size_t)r.slots + sizeof(double) * (size_t)r.n * (size_t)r.slots, 256);
+}
+
+// The workspace copy of slot i (plain, one block per source).
+Work slot_work(const WsRec &r, int i) {
+  WsRec t = r;
+  t.slots = 1;
+  ws_layout_one(t, static_cast<char *>(r.mem) + r.slot_bytes * (size_t)i);
+  return t.w;
+}
+
 // Brings a workspace to its resting state: all masks, counts and arrival
 // counters zero, depths -1.
 cudaError_t ws_clear(WsRec &r, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(r.mem, 0, r.bytes, st);
-  if (e == cudaSuccess && !r.batch) e = cudaMemsetAsync(r.w.d, 0xff, sizeof(int32_t) * r.n, st);
+  for (int i = 0; i < r.slots && e == cudaSuccess && !r.batch; ++i)
+    e = cudaMemsetAsync(slot_work(r, i).d, 0xff, sizeof(int32_t) * r.n, st);
   return e;
 }
 
@@ -314,6 +354,10 @@ struct bc_ctx {
 
   bc_stats last{};
   std::vector<int32_t> last_ovf; // sources whose path count reached 2^64 in the last call
+  // streams (and their events) of the one-block plain launches, made on first use
+  std::mutex aux_mu;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> aux_ev;
   int32_t inject_block = -1;
   int32_t inject_timeout_ms = 0;
 
@@ -447,13 +491,13 @@ bc_opts default_opts() {
 bool opts_valid(const bc_opts &o) {
   return (o.delta_fp64 == 0 || o.delta_fp64 == 1) && o.batch_k >= 0 &&
          o.batch_k <= kK * kMaxWords &&
-         (o.batch_k <= kK || o.schedule == BC_SCHED_AUTO || o.schedule == BC_SCHED_BATCH ||
-          o.schedule == BC_SCHED_BATCH_QUEUE) &&
-         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_QUEUE &&
+         (o.batch_k <= kK || o.schedule != BC_SCHED_PLAIN) &&
+         o.schedule >= BC_SCHED_AUTO && o.schedule <= BC_SCHED_BATCH_EDGE &&
          (o.normalize == 0 || o.normalize == 1) &&
          (o.scale_sampled == 0 || o.scale_sampled == 1) &&
          (o.out_device == 0 || o.out_device == 1) &&
-         (o.source_order == 0 || o.source_order == 1);
+         (o.source_order == 0 || o.source_order == 1) &&
+         (o.direction >= 0 && o.direction <= 2);
 }
 
 int resolve_schedule(const bc_opts &o, const GraphDev &) {
@@ -461,6 +505,26 @@ int resolve_schedule(const bc_opts &o, const GraphDev &) {
   return BC_SCHED_BATCH;
 }
 
+// Work split a batched schedule fixes (-1: tuned per graph).
+int fixed_split(int sched) {
+  return sched == BC_SCHED_BATCH_VERTEX ? kSplitVertex
+         : sched == BC_SCHED_BATCH_WARP ? kSplitWarp
+         : sched == BC_SCHED_BATCH_EDGE ? kSplitEdge
+                                        : -1;
+}
+
+
+// Direction rule of the forward path-count step (KParams::push_ratio): by
+// default a level pushes from the previous level when that scans at least
+// kPushRatio times fewer edges than pulling (BC_PUSH_RATIO overrides it for
+// experiments); bc_opts.direction forces either form.
+constexpr int kPushRatio = 8;
+int push_ratio(const bc_opts &o, const GraphRec &g) {
+  if (o.direction == 1 || g.no_push) return 0;
+  if (o.direction == 2) return -1;
+  if (const char *env = std::getenv("BC_PUSH_RATIO")) return std::atoi(env);
+  return kPushRatio;
+}
 
 // Grid of a persistent launch: the co-resident maximum for large graphs, a
 // smaller share of the GPU for small ones so that concurrent jobs overlap.
@@ -924,6 +988,7 @@ bc_status ws_acquire(bc_ctx *ctx, const WsNeed &nd, cudaStream_t st, std::unique
   auto r = std::make_unique<WsRec>();
   r->kind = nd.kind;
   r->words = nd.words;
+  r->slots = nd.slots;
   r->batch = nd.kind != WS_PLAIN;
   r->n = nd.n;
   r->cap = nd.cap;
@@ -966,14 +1031,28 @@ void ws_release(bc_ctx *ctx, std::unique_ptr<WsRec> ws) {
 
 // ---- jobs -------------------------------------------------------------------
 
+// The one-source-per-launch schedule on small graphs: each source is a
+// one-block launch (block barriers between levels) instead of a launch over
+// the whole GPU, whose grid barriers dominate when a level holds a few
+// hundred vertices; launches go round-robin to this many streams, so that
+// many sources run at once, each stream adding into its own BC partial
+// vector (summed in stream order at the end).
+constexpr int32_t kPlainBlockMaxN = 1 << 16;
+constexpr int kPlainStreams = 64;
+int plain_slots(const GraphDev &g, int64_t k) {
+  if (g.n > kPlainBlockMaxN || k < 2) return 1;
+  return (int)std::min<int64_t>(kPlainStreams, k);
+}
+
 size_t job_footprint(const GraphRec &gr, int sched, const bc_opts &o, int64_t k) {
   const GraphDev &g = gr.dev;
   WsRec r;
   const int kind = sched == BC_SCHED_PLAIN ? WS_PLAIN : WS_QUEUE;
   const BatchShape bs = batch_shape(o, kind, k, gr.narrow, false);
-  WsNeed nd = ws_need(g, kind, bs.kb, bs.words);
+  WsNeed nd = ws_need(g, kind, bs.kb, bs.words, plain_slots(g, k));
   r.kind = nd.kind;
   r.words = nd.words;
+  r.slots = nd.slots;
   r.batch = nd.kind != WS_PLAIN;
   r.n = nd.n;
   r.cap = nd.cap;
@@ -1016,6 +1095,242 @@ struct DebugOut {
   double *delta = nullptr;
 };
 
+// Tuning candidate of a fixed work split (items per fetch at the default).
+int cand_of_split(int variant) {
+  for (int c = 0; c < kNumTune; ++c)
+    if (kTuneCandidates[c].variant == variant && kTuneCandidates[c].grab == kGrabDefault) return c;
+  return 0;
+}
+
+// Times the batches launched between consecutive events of `ev` (all of them
+// enqueued already) and returns, per slot of `slot_of`, the summed time per
+// source; the events are destroyed.
+bc_status trial_times(std::vector<cudaEvent_t> &ev, const std::vector<int> &slot_of,
+                      const std::vector<int64_t> &sources, std::vector<double> &per_slot) {
+  bc_status s = BC_OK;
+  if (cudaEventSynchronize(ev.back()) != cudaSuccess) s = BC_ERR_CUDA;
+  for (size_t t = 0; t + 1 < ev.size() && s == BC_OK; ++t) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[t], ev[t + 1]) != cudaSuccess) s = BC_ERR_CUDA;
+    per_slot[(size_t)slot_of[t]] += (double)ms / (double)std::max<int64_t>(sources[t], 1);
+  }
+  for (cudaEvent_t &e : ev)
+    if (e) cudaEventDestroy(e);
+  ev.clear();
+  return s;
+}
+
+// The one-block plain form: source i of the job runs as its own one-block
+// launch on stream i mod S (S = the workspace's slots), with that slot's
+// workspace copy and BC partial vector; the job's stream waits for all of
+// them, sums the partial vectors in slot order and collects the first
+// device error of any slot.
+bc_status run_plain_blocks(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg,
+                           int trace_cap) {
+  WsRec *ws = j->ws.get();
+  const int64_t n = j->g->dev.n, k = j->k;
+  const bool fp64 = j->opts.delta_fp64 != 0;
+  const int S = (int)std::min<int64_t>(ws->slots, k);
+  cudaStream_t st = j->st;
+  {
+    std::lock_guard<std::mutex> lk(ctx->aux_mu);
+    while ((int)ctx->aux.size() < S) {
+      cudaStream_t a = nullptr;
+      cudaEvent_t e = nullptr;
+      BC_TRY(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+      BC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ctx->aux.push_back(a);
+      ctx->aux_ev.push_back(e);
+    }
+  }
+  // one job at a time uses the extra streams (jobs of other threads wait)
+  std::lock_guard<std::mutex> lk(ctx->aux_mu);
+  BC_TRY(cudaMemsetAsync(ws->parts, 0, sizeof(double) * (size_t)n * (size_t)S, st));
+  cudaEvent_t start = ctx->aux_ev[0];
+  BC_TRY(cudaEventRecord(start, st));
+  for (int i = 0; i < S; ++i) BC_TRY(cudaStreamWaitEvent(ctx->aux[(size_t)i], start, 0));
+  p.g.nchunks = j->g->nch_variant[kSplitWarp];
+  p.grab = kGrabDefault;
+  p.k = 1;
+  for (int64_t b = 0; b < k; ++b) {
+    const int slot = (int)(b % S);
+    p.w = slot_work(*ws, slot);
+    p.bc = ws->parts + (size_t)slot * (size_t)n;
+    p.src = j->d_src + b;
+    p.src_base = b;
+    p.trace = (j->d_trace && b == j->trace_batch) ? j->d_trace : nullptr;
+    p.trace_cap = p.trace ? trace_cap : 0;
+    if (dbg) {
+      p.dbg_d = dbg->d + b * n;
+      p.dbg_sigma = dbg->sigma + b * n;
+      p.dbg_delta = dbg->delta + b * n;
+    }
+    BC_TRY(launch_plain_block(p, fp64, ctx->aux[(size_t)slot]));
+    ++j->batches;
+    ++j->launches;
+  }
+  for (int i = 0; i < S; ++i) {
+    BC_TRY(cudaEventRecord(ctx->aux_ev[(size_t)i], ctx->aux[(size_t)i]));
+    BC_TRY(cudaStreamWaitEvent(st, ctx->aux_ev[(size_t)i], 0));
+  }
+  BC_TRY(launch_sum_parts(ws->parts, S, n, j->d_bc, st));
+  BC_TRY(launch_gather_err(ws->w.ctl, ws->slot_bytes, S, st));
+  j->launches += 2;
+  j->cand = cand_of_split(kSplitWarp);
+  return BC_OK;
+}
+
+// Launches a job's batches on j->st in source order.  A graph's first job
+// with enough sources also tunes, on its own batches (every configuration
+// computes the same sums; only the work layout differs):
+//   - with the automatic width, the width trial: two rounds of one batch at
+//     each width from the automatic one down to 64 sources (rounds in
+//     opposite orders, so a trend in cost along the grouped source order
+//     weighs every width alike); the fastest per source is kept for the
+//     graph.  A width runs in the same workspace in its own layout, which is
+//     cleared (all but the control block, which keeps errors) when the width
+//     changes;
+//   - then, unless the schedule fixes it, the work-split trial at the chosen
+//     width: kTuneRounds batches per candidate, fastest kept per graph and
+//     width.
+bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bool wtrial,
+                      int trace_cap) {
+  const GraphDev &g = j->g->dev;
+  const bool fp64 = j->opts.delta_fp64 != 0;
+  const int64_t n = g.n, k = j->k;
+  cudaStream_t st = j->st;
+  const int kind = j->kind;
+  const int fixed = fixed_split(resolve_schedule(j->opts, g));
+  const bool notune = dbg || kind != WS_QUEUE || std::getenv("BC_NO_TUNE");
+  WsRec *ws = j->ws.get();
+  if (kind == WS_PLAIN && ws->slots > 1) return run_plain_blocks(ctx, j, p, dbg, trace_cap);
+  const size_t ctl_bytes = align_up(sizeof(Ctl), 256);
+  int cur_words = j->words; // layout the workspace holds
+  int64_t bi = 0, b0 = 0;
+
+  auto launch = [&](int kb, int words, int cand) -> bc_status {
+    if (words != cur_words) {
+      WsRec r = *ws;
+      r.words = words;
+      ws_layout(r, static_cast<char *>(ws->mem));
+      p.w = r.w;
+      BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->bytes - ctl_bytes,
+                             st));
+      cur_words = words;
+    }
+    p.g.nchunks = j->g->nch_variant[kTuneCandidates[cand].variant];
+    p.grab = kTuneCandidates[cand].grab;
+    p.src = j->d_src + b0;
+    p.k = (int32_t)std::min<int64_t>(kb, k - b0);
+    p.src_base = b0;
+    p.trace = (j->d_trace && bi == j->trace_batch) ? j->d_trace : nullptr;
+    p.trace_cap = p.trace ? trace_cap : 0;
+    if (dbg) {
+      p.dbg_d = dbg->d + b0 * n;
+      p.dbg_sigma = dbg->sigma + b0 * n;
+      p.dbg_delta = dbg->delta + b0 * n;
+    }
+    const int grid = pick_grid(ctx, g, kind, fp64, words);
+    if (grid <= 0) return BC_ERR_CUDA;
+    BC_TRY(kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words)
+                            : launch_plain(p, fp64, grid, st));
+    b0 += p.k;
+    ++bi;
+    ++j->batches;
+    ++j->launches;
+    j->cand = cand;
+    return BC_OK;
+  };
+  auto record = [&](std::vector<cudaEvent_t> &ev) -> bc_status {
+    cudaEvent_t e = nullptr;
+    BC_TRY(cudaEventCreate(&e));
+    ev.push_back(e);
+    BC_TRY(cudaEventRecord(e, st));
+    return BC_OK;
+  };
+
+  int words = j->words;
+  int kb = j->kb;
+  const int split_cand = fixed >= 0 ? cand_of_split(fixed) : 0;
+  // ---- width trial ----
+  if (wtrial && !notune) {
+    std::vector<int> widths;
+    for (int w : kWidthTrial)
+      if (w <= words) widths.push_back(w);
+    int64_t need = 0;
+    for (int w : widths) need += 2 * (int64_t)kK * w;
+    if (widths.size() > 1 && k - need >= 2 * (int64_t)kK * words) {
+      std::vector<cudaEvent_t> ev;
+      std::vector<int> slot_of;
+      std::vector<int64_t> srcs;
+      const int nw = (int)widths.size();
+      for (int t = 0; t < 2 * nw; ++t) {
+        const int i = t < nw ? t : 2 * nw - 1 - t;
+        const int w = widths[(size_t)i];
+        bc_status s = record(ev);
+        if (s != BC_OK) return s;
+        slot_of.push_back(i);
+        srcs.push_back(std::min<int64_t>((int64_t)kK * w, k - b0));
+        s = launch(kK * w, w, split_cand);
+        if (s != BC_OK) return s;
+      }
+      bc_status s = record(ev);
+      if (s != BC_OK) return s;
+      std::vector<double> per((size_t)nw, 0.0);
+      s = trial_times(ev, slot_of, srcs, per);
+      if (s != BC_OK) return s;
+      int best = 0;
+      for (int i = 1; i < nw; ++i)
+        if (per[(size_t)i] < per[(size_t)best]) best = i;
+      words = widths[(size_t)best];
+      kb = kK * words;
+      j->g->tuned_words = words;
+    }
+  }
+  j->words = words;
+  j->kb = kb;
+  // ---- work-split trial ----
+  std::atomic<int> &tuned_slot = j->g->tuned[word_index(words)];
+  int cand = fixed >= 0 ? split_cand : std::max(tuned_slot.load(), 0);
+  if (kind != WS_QUEUE) cand = 0;
+  const int64_t left = (k - b0 + kb - 1) / kb;
+  if (!notune && fixed < 0 && tuned_slot.load() < 0 && left >= kNumTune * kTuneRounds + 4) {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> slot_of;
+    std::vector<int64_t> srcs;
+    for (int t = 0; t < kNumTune * kTuneRounds; ++t) {
+      // rounds alternate direction (c0 c1 .. c4 c4 .. c0), so a trend in
+      // batch cost along the source order weighs every candidate alike
+      const int r = t / kNumTune, c = t % kNumTune;
+      const int cc = r % 2 == 0 ? c : kNumTune - 1 - c;
+      bc_status s = record(ev);
+      if (s != BC_OK) return s;
+      slot_of.push_back(cc);
+      srcs.push_back(std::min<int64_t>(kb, k - b0));
+      s = launch(kb, words, cc);
+      if (s != BC_OK) return s;
+    }
+    bc_status s = record(ev);
+    if (s != BC_OK) return s;
+    std::vector<double> per((size_t)kNumTune, 0.0);
+    s = trial_times(ev, slot_of, srcs, per);
+    if (s != BC_OK) return s;
+    int best = 0;
+    for (int c = 1; c < kNumTune; ++c)
+      if (per[(size_t)c] < per[(size_t)best]) best = c;
+    tuned_slot = best;
+    cand = best;
+  }
+  // ---- the rest of the job ----
+  while (b0 < k) {
+    const bc_status s = launch(kb, words, cand);
+    if (s != BC_OK) return s;
+  }
+  if (cur_words != ws->words) // back to the workspace's own layout, clean
+    BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->bytes - ctl_bytes, st));
+  return BC_OK;
+}
+
 // Enqueues a whole job on j->st: inputs, one launch per batch, scaling, copy
 // of the result to `out` (device or host pointer per opts.out_device; an
 // async job passes its pinned buffer) and of the job counters.
@@ -1028,14 +1343,22 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   cudaStream_t st = j->st;
   const int kind = batch ? WS_QUEUE : WS_PLAIN;
   j->kind = kind;
-  const BatchShape bs = batch_shape(j->opts, kind, k, j->g->narrow, dbg != nullptr);
+  BatchShape bs = batch_shape(j->opts, kind, k, j->g->narrow, dbg != nullptr);
   // wider than one mask word: the queue kernel only
   if (bs.words > 1 && kind != WS_QUEUE) return BC_ERR_ARG;
+  // automatic width: the graph's width trial, once run, caps it
+  const bool auto_width = batch && j->opts.batch_k == 0 && !j->g->narrow && !dbg;
+  const int tw = j->g->tuned_words.load();
+  if (auto_width && tw > 0 && tw < bs.words) bs = {kK * tw, tw};
+  // the width trial runs on the first job of a graph whose automatic width
+  // has narrower alternatives and enough sources to try each twice
+  const bool wtrial = auto_width && tw == 0 && bs.words > 1 && !std::getenv("BC_NO_TUNE");
   const int kb = bs.kb, words = bs.words;
   j->kb = kb;
   j->words = words;
 
-  bc_status s = ws_acquire(ctx, ws_need(g, kind, kb, words), st, j->ws);
+  bc_status s =
+      ws_acquire(ctx, ws_need(g, kind, kb, words, batch ? 1 : plain_slots(g, k)), st, j->ws);
   if (s != BC_OK) return s;
   BC_TRY(pin_get(ctx, &j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
   BC_TRY(pin_get(ctx, &j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
@@ -1099,13 +1422,13 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   p.bc2 = j->d_bc2;
   p.ovf_flags = j->d_ovf;
   p.job_cnt = j->d_cnt;
+  p.push_ratio = push_ratio(j->opts, *j->g);
   if (ctx->inject_block >= 0 && batch) {
     p.skip_block = ctx->inject_block;
     p.timeout_ns = (long long)ctx->inject_timeout_ms * 1000000LL;
     ctx->inject_block = -1;
   }
-  const int grid = pick_grid(ctx, g, kind, fp64, words);
-  if (grid <= 0) return BC_ERR_CUDA;
+  if (pick_grid(ctx, g, kind, fp64, words) <= 0) return BC_ERR_CUDA;
   constexpr int kTraceCap = 8192;
   if (const char *tr = std::getenv("BC_TRACE")) {
     // per-step timing of one batch (index BC_TRACE, -1 = last) to stderr
@@ -1118,72 +1441,8 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   BC_TRY(cudaEventRecord(j->ev0, st));
   j->batches = 0;
   j->launches = 0;
-  // Per-graph tuning of the queue kernel: the first job on a graph with
-  // enough batches runs kTuneRounds trial batches with each candidate
-  // (chunk size, items per fetch), times them with events, and keeps the
-  // fastest for the rest of the job and for later jobs on the graph.  Every
-  // candidate computes the same result; only the work split differs.
-  const int64_t nbatch = (k + kb - 1) / kb;
-  std::atomic<int> &tuned_slot = j->g->tuned[word_index(words)];
-  const int tuned = tuned_slot.load();
-  const bool tune = kind == WS_QUEUE && tuned < 0 && !dbg && !std::getenv("BC_NO_TUNE") &&
-                    nbatch >= kNumTune * kTuneRounds + 8;
-  auto apply = [&](int cand) {
-    p.g.nchunks = j->g->nch_variant[kTuneCandidates[cand].variant];
-    p.grab = kTuneCandidates[cand].grab;
-    j->cand = cand;
-  };
-  apply(kind == WS_QUEUE && tuned >= 0 ? tuned : 0);
-  cudaEvent_t tev[kNumTune * kTuneRounds + 1] = {};
-  int64_t bi = 0;
-  for (int64_t b0 = 0; b0 < k; b0 += kb, ++bi) {
-    p.src = j->d_src + b0;
-    p.k = (int32_t)std::min<int64_t>(kb, k - b0);
-    p.src_base = b0;
-    p.trace = (j->d_trace && b0 / kb == j->trace_batch) ? j->d_trace : nullptr;
-    p.trace_cap = p.trace ? kTraceCap : 0;
-    if (dbg) {
-      p.dbg_d = dbg->d + b0 * n;
-      p.dbg_sigma = dbg->sigma + b0 * n;
-      p.dbg_delta = dbg->delta + b0 * n;
-    }
-    if (tune && bi <= kNumTune * kTuneRounds) {
-      if (!tev[bi]) BC_TRY(cudaEventCreate(&tev[bi]));
-      BC_TRY(cudaEventRecord(tev[bi], st));
-      if (bi < kNumTune * kTuneRounds) {
-        // rounds alternate direction (c0 c1 c2 c3 c3 c2 c1 c0 ...), so a
-        // trend in batch cost along the source order weighs every candidate
-        // alike
-        const int64_t r = bi / kNumTune, c = bi % kNumTune;
-        apply((int)(r % 2 == 0 ? c : kNumTune - 1 - c));
-      } else {
-        // all trial batches are enqueued: pick the fastest candidate
-        BC_TRY(cudaEventSynchronize(tev[bi]));
-        float sum[kNumTune] = {};
-        for (int64_t t = 0; t < kNumTune * kTuneRounds; ++t) {
-          float ms = 0.f;
-          BC_TRY(cudaEventElapsedTime(&ms, tev[t], tev[t + 1]));
-          const int64_t r = t / kNumTune, c = t % kNumTune;
-          sum[r % 2 == 0 ? c : kNumTune - 1 - c] += ms;
-        }
-        int best = 0;
-        for (int c = 1; c < kNumTune; ++c)
-          if (sum[c] < sum[best]) best = c;
-        tuned_slot = best;
-        apply(best);
-        for (auto &ev : tev) {
-          cudaEventDestroy(ev);
-          ev = nullptr;
-        }
-      }
-    }
-    BC_TRY(kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words)
-                            : launch_plain(p, fp64, grid, st));
-    ++j->batches;
-    ++j->launches;
-  }
-  for (auto &ev : tev)
-    if (ev) cudaEventDestroy(ev);
+  s = run_batches(ctx, j, p, dbg, wtrial, kTraceCap);
+  if (s != BC_OK) return s;
   BC_TRY(cudaEventRecord(j->ev1, st));
   double factor = 1.0;
   if (j->opts.normalize && n > 2) factor /= (double)(n - 1) * (double)(n - 2);
@@ -1233,10 +1492,13 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.max_levels = (int32_t)j->h_cnt[CNT_MAXLEV];
   s.kernel_kind = j->kind == WS_QUEUE ? 2 : 1;
   s.levels_sum = (int32_t)j->h_cnt[CNT_LEVELS];
-  s.chunk_edges = kChunkCandidates[kTuneCandidates[j->cand].variant];
+  s.chunk_edges = kTuneCandidates[j->cand].variant == kSplitVertex
+                      ? 0
+                      : kChunkCandidates[kTuneCandidates[j->cand].variant];
   s.batch_sources = j->kb;
   s.mask_words = j->words;
   s.grab = kTuneCandidates[j->cand].grab;
+  s.push_levels = (int32_t)j->h_cnt[CNT_PUSH];
   int32_t novf = 0;
   j->ovf_sources.clear();
   for (int64_t i = 0; i < j->k; ++i)
@@ -1264,7 +1526,13 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.overflow_sources = novf;
   bc_status st = BC_OK;
   const int kerr = *j->h_err;
-  if ((kerr == KERR_QUEUE || kerr == KERR_HEAVY) && j->words > 1) {
+  if (kerr == KERR_PUSH) {
+    // a pushed path count reached 2^32, so a pushed sum could have carried:
+    // rerun the job pulling every level (and keep pulling on this graph)
+    j->g->no_push = true;
+    st = kStatusRetry;
+    j->ws->dirty = true;
+  } else if ((kerr == KERR_QUEUE || kerr == KERR_HEAVY) && j->words > 1) {
     // a wide batch queued vertices at more distinct depths than its queue
     // holds: rerun the job with 64 sources per batch
     j->g->narrow = true;
@@ -1510,6 +1778,8 @@ bc_status bc_shutdown(bc_ctx *ctx) {
   ctx->pin_free.clear();
   for (int i = 0; i < kMaxSlots; ++i)
     if (ctx->slot_stream[i]) cudaStreamDestroy(ctx->slot_stream[i]);
+  for (cudaStream_t a : ctx->aux) cudaStreamDestroy(a);
+  for (cudaEvent_t e : ctx->aux_ev) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return BC_OK;
@@ -2105,6 +2375,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     mp.next = d_next;
     mp.kb = kb;
     mp.max_words = ws_words;
+    total.mask_words = std::max(total.mask_words, ws_words);
     mp.grouped = o.source_order == 0 ? 1 : 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -2152,6 +2423,8 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
       total.reached_pairs += ctx->last.reached_pairs;
       total.heavy_chunks += ctx->last.heavy_chunks;
       total.levels_sum += ctx->last.levels_sum;
+      total.push_levels += ctx->last.push_levels;
+      total.mask_words = std::max(total.mask_words, ctx->last.mask_words);
     }
   }
   // per-graph normalisation, result copy, counters of the persistent launch

@@ -73,7 +73,11 @@ __device__ bool grid_sync(Ctl *ctl, long long timeout_ns, int64_t *snap_dst = nu
 // ---------------------------------------------------------------------------
 
 template <typename DT> __device__ __forceinline__ DT u64_to(uint64_t x);
-template <> __device__ __forceinline__ float u64_to<float>(uint64_t x) { return __ull2float_rn(x); }
+template <> __device__ __forceinline__ float u64_to<float>(uint64_t x) {
+  // counts below 2^32 (all but pathological graphs) take the 32-bit
+  // conversion; both round to nearest, so the value is the same
+  return (x >> 32) == 0 ? __uint2float_rn((unsigned)x) : __ull2float_rn(x);
+}
 template <> __device__ __forceinline__ double u64_to<double>(uint64_t x) { return __ull2double_rn(x); }
 
 // saturating add: on carry the sum pins at 2^64-1 and the flag is raised

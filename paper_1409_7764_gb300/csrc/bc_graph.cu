@@ -139,8 +139,9 @@ __global__ void graph_keys_kernel(const int32_t *__restrict__ row_ptr,
     if (lane == 0) {
       two[v] = t;
       const int64_t cost = (int64_t)(e - b) + (in_ptr[v + 1] - in_ptr[v]);
+      static_assert(kChunkVariants == 4, "one size per work-split variant");
       constexpr int64_t kSizes[kChunkVariants] = {kChunkCandidates[0], kChunkCandidates[1],
-                                                   kChunkCandidates[2]};
+                                                   kChunkCandidates[2], kChunkCandidates[3]};
 #pragma unroll
       for (int c = 0; c < kChunkVariants; ++c) {
         const int64_t ch = kSizes[c];

@@ -29,10 +29,15 @@ __host__ __device__ constexpr int auto_words(int64_t k, int max_words) {
          : max_words >= 2 && k >= (int64_t)kWideMinBatches * kK * 2 ? 2
                                                                     : 1;
 }
-// Edges per work chunk of a high-degree vertex: candidates the per-graph
-// tuner picks from (the first is the default before tuning).
-constexpr int kChunkCandidates[3] = {256, 128, 512};
-constexpr int kChunkVariants = 3;
+// Work split of a level's entries among warps (the per-graph tuner picks
+// one; the first is the default before tuning): an entry with more in- plus
+// out-edges than the chunk size is cut into chunks of about that many edges,
+// each taken by its own warp; smaller entries take one warp each.  128 edges
+// leans towards edge-centric balance, 256 and 512 are warp-centric, and 2^30
+// never splits (vertex-centric: one warp per entry, whatever its degree).
+constexpr int kChunkCandidates[4] = {256, 128, 512, 1 << 30};
+constexpr int kChunkVariants = 4;
+constexpr int kSplitWarp = 0, kSplitEdge = 1, kSplitWarp512 = 2, kSplitVertex = 3;
 constexpr int kChunk = kChunkCandidates[0];    // chunk size of the plain and no-alloc paths
 #ifndef BC_PREFETCH_GROUPS
 #define BC_PREFETCH_GROUPS 0 // 1: fetch the next item group before processing the current one
@@ -52,6 +57,7 @@ enum : int {
   KERR_HEAVY = 3,    // heavy-entry list capacity exceeded
   KERR_CHUNKS = 4,   // heavy chunk scratch exceeded
   KERR_GRAB = 6,     // more work items per fetch than a header round holds (host bug)
+  KERR_PUSH = 7,     // a pushed path count was 2^32 or more: the job reruns pulling counts
 };
 
 // Job-level counters (uint64 each), accumulated by the kernels.
@@ -66,7 +72,8 @@ enum : int {
   CNT_LEVELS = 7,    // level counts summed over batches
   CNT_BUSY = 8,      // phase-clock builds: warp cycles spent on step items
   CNT_IDLE = 9,      // phase-clock builds: warp cycles from a warp's last item to the step's end
-  CNT_N = 10
+  CNT_PUSH = 10,     // forward levels whose path counts were pushed (summed over batches)
+  CNT_N = 11
 };
 
 
@@ -120,6 +127,8 @@ struct Work {
   void *partial = nullptr;    // [chunk_cap][k_max] chunk partial sums (u64 or float type)
   uint64_t *partial_ovf = nullptr; // [chunk_cap][words] overflow bits of forward partials
   int64_t chunk_cap = 0;
+  unsigned long long *lsum = nullptr; // batch: [n+3][2] per level: summed in- and out-degree of
+                              // its vertices (the scan lengths of pulling and pushing counts)
   uint64_t *sigma = nullptr;  // [n][k_max] path counts
   void *cdep = nullptr;       // [n][k_max] (1 + delta) / sigma, float or double
   Ctl *ctl = nullptr;
@@ -143,6 +152,11 @@ struct KParams {
   unsigned long long *trace = nullptr; // optional [trace_cap][4] per-step records
   int32_t trace_cap = 0;
   int32_t grab = kGrabDefault;  // work items per counter fetch
+  // Direction of the path-count step of forward level l >= 1: 0 = always
+  // pull over the in-edges of level l; r > 0 = push from level l-1 along its
+  // out-edges when r x (their out-degree sum) < (level l's in-degree sum);
+  // -1 = push at every level >= 1.  Needs Work::lsum.
+  int32_t push_ratio = 0;
 };
 
 // Parameters of the many-small-graphs launch: one thread block per graph at a
@@ -167,6 +181,10 @@ cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t 
 int max_grid_many(bool fp64, int device);
 cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_plain_block(const KParams &p, bool fp64, cudaStream_t st);
+cudaError_t launch_sum_parts(const double *parts, int nparts, int64_t n, double *out,
+                             cudaStream_t st);
+cudaError_t launch_gather_err(Ctl *first, size_t stride_bytes, int count, cudaStream_t st);
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
 cudaError_t launch_estimate(const double *sum, const double *sumsq, int64_t n, int64_t k,
                             double factor, double *est, double *err, cudaStream_t st);

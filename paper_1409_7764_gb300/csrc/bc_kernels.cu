@@ -125,6 +125,20 @@ __device__ __forceinline__ void zero_ring_ahead(Ctl *ctl, int step, int64_t gtid
 
 constexpr int kStage = 64; // per-warp staging of newly discovered vertices
 
+// Adds the in- and out-degrees of a level's new vertices (summed over the
+// warp) to that level's totals, which choose the direction of the level's
+// path-count step.
+__device__ __forceinline__ void add_level_degrees(const KParams &p, int lvl,
+                                                  unsigned long long din,
+                                                  unsigned long long dout, int lane) {
+  din = warp_sum_u64(din);
+  dout = warp_sum_u64(dout);
+  if (lane == 0 && (din | dout)) {
+    atomicAdd(p.w.lsum + 2 * lvl, din);
+    atomicAdd(p.w.lsum + 2 * lvl + 1, dout);
+  }
+}
+
 // Appends a warp's staged vertices to the next level's queue with one tail
 // atomic; high-degree ones also get their chunk range in the level's list.
 __device__ __forceinline__ void stage_flush(const KParams &p, const LevelView &lv, const int *buf,
@@ -133,6 +147,8 @@ __device__ __forceinline__ void stage_flush(const KParams &p, const LevelView &l
   unsigned long long base = 0;
   if (lane == 0) base = atomicAdd(&p.w.ctl->tail, (unsigned long long)nst);
   base = __shfl_sync(kFull, base, 0);
+  unsigned long long din = 0, dout = 0;
+  const bool sums = p.push_ratio != 0;
   for (int i = lane; i < nst; i += kWarp) {
     const long long pos = (long long)base + i;
     if (pos >= p.w.cap) {
@@ -141,6 +157,10 @@ __device__ __forceinline__ void stage_flush(const KParams &p, const LevelView &l
     }
     const int x = buf[i];
     p.w.qv[pos] = x;
+    if (sums) {
+      din += (unsigned long long)(__ldg(p.g.in_ptr + x + 1) - __ldg(p.g.in_ptr + x));
+      dout += (unsigned long long)(__ldg(p.g.row_ptr + x + 1) - __ldg(p.g.row_ptr + x));
+    }
     const int nch = __ldg(p.g.nchunks + x);
     if (nch > 0) {
       const unsigned long long h =
@@ -159,6 +179,7 @@ __device__ __forceinline__ void stage_flush(const KParams &p, const LevelView &l
       p.w.hq_c[hidx] = cpre;
     }
   }
+  if (sums) add_level_degrees(p, lv.lvl + 1, din, dout, lane);
 }
 
 // Stages the vertices this round discovered first (isnew lanes) in the
@@ -209,6 +230,60 @@ __device__ __forceinline__ void exact_counts(const KParams &p, const Mask<W> &F,
   cbits = 0;
   unsigned long long dag = 0; // counted by the fast pull already
   pull_counts<W, true>(p, F, ib, din, Pm, lane, s, cbits, dag);
+}
+
+// Pushed path counts (the other direction of the forward step at level l):
+// entry u of level l-1 (mask F, its sources at level l-1) adds its counts
+// along its out-edges [ob, oe) to every vertex x whose level-l mask A[x]
+// shares a source: sigma[x][j] += sigma[u][j] for j in F & A[x].  The masks
+// of level l are complete when the step starts, so exactly the
+// shortest-path DAG edges into level l receive counts; the adds are 64-bit
+// integer atomics, whose order does not change the sums.  The target counts
+// start at zero (every batch resets the counts it wrote).  Overflow is ruled
+// out before adding: the step refuses (KERR_PUSH, and the job reruns
+// pulling counts) as soon as a pushed count is 2^32 or more, so every sum
+// of fewer than 2^31 pushed terms stays below 2^63.
+template <int W>
+__device__ __forceinline__ void push_counts(const KParams &p, int u, const Mask<W> &F, int ob,
+                                            int oe, const uint64_t *A, int lane,
+                                            unsigned long long &dag) {
+  uint64_t own[2 * W];
+  const uint64_t *srow = p.w.sigma + (size_t)u * (kK * W) + lane;
+  unsigned big = 0;
+#pragma unroll
+  for (int i = 0; i < 2 * W; ++i) {
+    own[i] = F.has(i, lane) ? ldcg(srow + 32 * i) : 0ull;
+    big |= (unsigned)(own[i] >> 32);
+  }
+  if (__any_sync(kFull, big != 0)) {
+    set_err(p.w.ctl, KERR_PUSH);
+    return;
+  }
+  const unsigned mybit = 1u << lane;
+  for (int r = ob; r < oe; r += kWarp) {
+    const int t = r + lane;
+    int x = 0;
+    Mask<W> P = Mask<W>::zero();
+    if (t < oe) {
+      x = __ldg(p.g.col_idx + t);
+      P = load_mask<W>(A, x) & F;
+    }
+    dag += P.popc(); // per lane; the warp's counters are summed at the flush
+    unsigned bal = __ballot_sync(kFull, P.any());
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int xx = __shfl_sync(kFull, x, src);
+      unsigned long long *row =
+          reinterpret_cast<unsigned long long *>(p.w.sigma) + (size_t)xx * (kK * W) + lane;
+#pragma unroll
+      for (int wi = 0; wi < W; ++wi) {
+        const uint64_t PP = __shfl_sync(kFull, P.w[wi], src);
+        if ((unsigned)PP & mybit) atomicAdd(row + 64 * wi, own[2 * wi]);
+        if ((unsigned)(PP >> 32) & mybit) atomicAdd(row + 64 * wi + 32, own[2 * wi + 1]);
+      }
+    }
+  }
 }
 
 // Forward work of one frontier entry (mask F) at level l: the path-count
@@ -285,18 +360,71 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
   }
 }
 
+#ifndef BC_CONTRIB_FORM
+#define BC_CONTRIB_FORM 1 // FP32 dependencies: 1 = compensated FP32 pair per entry, 0 = FP64
+#endif
+
+// Knuth's error-free sum of two floats: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// Sum of the lane's per-source dependencies of one entry over the warp,
+// returned to lane 0 as a double.  FP64 dependencies add in FP64.  FP32
+// dependencies add as a compensated pair of floats (a two-sum running value
+// and its accumulated error, about 46 significant bits for these sums of
+// positive terms) and widen once at the end: GB300's FP64 pipe is a small
+// fraction of its FP32 one, and an FP64 add per source and entry measured a
+// visible share of the kernel.
+template <typename DT, int W> struct EntrySum {
+  double d = 0.0;
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(DT x) {
+    if constexpr (sizeof(DT) == 8 || BC_CONTRIB_FORM == 0) {
+      d += (double)x;
+    } else {
+      float e;
+      two_sum(hi, (float)x, hi, e);
+      lo += e;
+    }
+  }
+  __device__ __forceinline__ double warp_total() {
+    if constexpr (sizeof(DT) == 8 || BC_CONTRIB_FORM == 0) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(kFull, d, off);
+      return d;
+    } else {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ohi = __shfl_down_sync(kFull, hi, off);
+        const float olo = __shfl_down_sync(kFull, lo, off);
+        float e;
+        two_sum(hi, ohi, hi, e);
+        lo += olo + e;
+      }
+      return (double)hi + (double)lo;
+    }
+  }
+};
+
 // Batch: closes entry v (mask F) at level l of the backward sweep given the
 // lane's successor sums a, its path counts sg and (lane 0) the current BC
 // value bcv, all loaded by the caller ahead of the successor scan:
-// dependencies, coefficients, BC, resets.  (Path counts need no reset: a
-// count is only read where the same batch wrote it, for a source whose mask
-// bit marks the vertex reached.)
+// dependencies, coefficients, BC, resets.  The entry's path counts are
+// reset to zero here, so every batch starts on zeroed counts (the pushed
+// form of the forward step adds into them).  At level 0 every source bit of
+// the entry is the vertex itself, whose own dependency is never added to its
+// BC; at deeper levels no source of the entry is the vertex.
 template <typename DT, int W, bool SQ>
 __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, const Mask<W> &F,
                                              const DT (&a)[2 * W], const uint64_t (&sg)[2 * W],
                                              double bcv, uint64_t *Wn, int lane) {
   DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * (kK * W);
-  double contrib = 0.0, contrib2 = 0.0;
+  uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
+  EntrySum<DT, W> sum;
+  double contrib2 = 0.0;
   const int n = p.g.n;
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i)
@@ -305,8 +433,9 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
       const DT sf = u64_to<DT>(sg[i]);
       const DT dl = sf * a[i];
       crow[j] = (DT(1) + dl) / sf;
-      if (__ldg(p.src + j) != v) {
-        contrib += (double)dl;
+      srow[j] = 0;
+      if (lvl > 0) {
+        sum.add(dl);
         if (SQ) contrib2 += (double)dl * (double)dl;
       }
       if (p.dbg_d) {
@@ -316,8 +445,7 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
         p.dbg_delta[o] = (double)dl;
       }
     }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(kFull, contrib, off);
+  const double contrib = sum.warp_total();
   if (SQ) {
     // squared per-source terms for the sampled-source estimator's variance
 #pragma unroll
@@ -549,6 +677,8 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
       p.w.hpack[1] = 0;
       p.w.qoff[0] = 0;
       p.w.hoff[0] = 0;
+      if (p.push_ratio != 0)
+        for (int i = 0; i < 4; ++i) p.w.lsum[i] = 0;
     }
     __syncthreads();
     if (threadIdx.x < p.k) {
@@ -562,6 +692,12 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
       if (first) {
         const unsigned long long pos = atomicAdd(&ctl->tail, 1ull);
         p.w.qv[pos] = s;
+        if (p.push_ratio != 0) {
+          atomicAdd(p.w.lsum, (unsigned long long)(__ldg(p.g.in_ptr + s + 1) -
+                                                   __ldg(p.g.in_ptr + s)));
+          atomicAdd(p.w.lsum + 1, (unsigned long long)(__ldg(p.g.row_ptr + s + 1) -
+                                                       __ldg(p.g.row_ptr + s)));
+        }
         const int nch = __ldg(p.g.nchunks + s);
         if (nch > 0) {
           const unsigned long long h =
@@ -595,18 +731,50 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
     lv.nheavy = (int64_t)(hp >> 32);
     lv.nhc = (int64_t)(hp & 0xffffffffull);
     lv.hoff_next = lv.hoff + lv.nheavy;
+    // direction of this level's path-count step, the same in every block:
+    // the degree sums of levels l-1 and l are complete since the last barrier
+    bool push = false;
+    if (p.push_ratio != 0 && l >= 1)
+      push = p.push_ratio < 0 ||
+             (unsigned long long)p.push_ratio * ldcg(p.w.lsum + 2 * (l - 1) + 1) <
+                 ldcg(p.w.lsum + 2 * l);
     if (gtid == 0) {
       p.w.hoff[l] = lv.hoff;
       p.w.hpack[l + 2] = 0;
+      if (p.push_ratio != 0) {
+        p.w.lsum[2 * (l + 2)] = 0;
+        p.w.lsum[2 * (l + 2) + 1] = 0;
+      }
+      if (push) atomicAdd(p.job_cnt + CNT_PUSH, 1ull);
     }
     zero_ring_ahead(ctl, step, gtid);
     if (l >= 2)
       for (int64_t i = lo_m2 + gtid; i < lo_m1; i += nthr) zero_mask<W>(Z, ldcg(p.w.qv + i));
 
+    // push form: the step's first items are the entries of level l-1 (chunks
+    // of its heavy entries, then its light entries), pushing their counts
+    // along their out-edges; level l's own items then only discover level
+    // l+1 and write no counts
+    LevelView pv;
+    pv.lvl = l - 1;
+    pv.lo = lo_m1;
+    pv.hi = lv.lo;
+    pv.hoff = 0;
+    pv.nheavy = 0;
+    pv.nhc = 0;
+    pv.hoff_next = 0;
+    if (push) {
+      const unsigned long long hpp = ldcg(p.w.hpack + l - 1);
+      pv.hoff = ldcg(p.w.hoff + l - 1);
+      pv.nheavy = (int64_t)(hpp >> 32);
+      pv.nhc = (int64_t)(hpp & 0xffffffffull);
+    }
+    const int64_t poff = push ? pv.nhc + (pv.hi - pv.lo) : 0;
+
     unsigned long long *ctr = &ctl->work[step & 3];
-    const int64_t total = lv.nhc + (lv.hi - lv.lo);
+    const int64_t total = poff + lv.nhc + (lv.hi - lv.lo);
     trace_step(p, step, l, total, lv.nhc, gtid);
-    HeavyCursor hc;
+    HeavyCursor hc, hcp;
     int nst = 0; // staged new vertices of this warp
     const int grab = p.grab;
     const int64_t stat = nwarps * grab;
@@ -615,7 +783,30 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
     while (base < total) {
       const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
       const int64_t end = base + grab < total ? base + grab : total;
-      for (int64_t item = base; item < end && item < lv.nhc; ++item) {
+      for (int64_t item = base; item < end && item < poff; ++item) {
+        // push form: one entry (or one chunk of a heavy entry) of level l-1
+        int u, ob, oe;
+        if (item < pv.nhc) {
+          hcp.seek(p, pv, item, lane);
+          u = ldcg(p.w.qv + ldcg(p.w.hq_e + hcp.h));
+          const int nch = __ldg(p.g.nchunks + u);
+          const int64_t c = item - hcp.first;
+          const int rs = __ldg(p.g.row_ptr + u), od = __ldg(p.g.row_ptr + u + 1) - rs;
+          ob = rs + (int)(c * od / nch);
+          oe = rs + (int)((c + 1) * od / nch);
+        } else {
+          u = ldcg(p.w.qv + pv.lo + (item - pv.nhc));
+          if (__ldg(p.g.nchunks + u) != 0) continue; // heavy: handled as chunks
+          ob = __ldg(p.g.row_ptr + u);
+          oe = __ldg(p.g.row_ptr + u + 1);
+        }
+        push_counts<W>(p, u, load_mask<W>(Pm, u), ob, oe, A, lane, dag);
+        if (lane == 0) cnt.out_e += (uint64_t)(oe - ob);
+      }
+      // level l's own items, numbered from 0
+      const int64_t lbase = base > poff ? base - poff : 0;
+      const int64_t lend = end > poff ? end - poff : 0;
+      for (int64_t item = lbase; item < lend && item < lv.nhc; ++item) {
         // one chunk of a heavy entry
         hc.seek(p, lv, item, lane);
         const int64_t h = hc.h;
@@ -626,6 +817,25 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         const int64_t c = item - hc.first;
         const int is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
         const int rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
+        if (push) {
+          // discovery only, over this chunk's share of the out-edges; the
+          // first chunk records the entry
+          const int od = re - rs;
+          const int a = (int)(c * od / nch), b = (int)((c + 1) * od / nch);
+          uint64_t s[2 * W] = {};
+          unsigned cb = 0;
+          fwd_scan<W>(p, lv, F, 0, 0, rs + a, rs + b, A, Pm, Bn, stage, nst, lane, s, cb, dag);
+          if (lane == 0) {
+            cnt.out_e += (uint64_t)(b - a);
+            cnt.heavy++;
+            if (c == 0) {
+              store_mask<W>(p.w.qm, e, F);
+              cnt.entries++;
+              cnt.reached += F.popc();
+            }
+          }
+          continue;
+        }
         const int indeg = ie - is, tot = indeg + (re - rs);
         const int a = (int)(c * tot / nch), b = (int)((c + 1) * tot / nch);
         uint64_t s[2 * W] = {};
@@ -677,11 +887,11 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           }
         }
       }
-      if (end > lv.nhc) {
+      if (lend > lv.nhc) {
         using FF = FwdField<W>;
-        const int64_t first = base > lv.nhc ? base : lv.nhc;
+        const int64_t first = lbase > lv.nhc ? lbase : lv.nhc;
         const int64_t e0 = lv.lo + (first - lv.nhc);
-        const auto hd = fwd_headers<W>(p, A, e0, (int)(end - first), lane);
+        const auto hd = fwd_headers<W>(p, A, e0, (int)(lend - first), lane);
         for (int i = 0; i < hd.cnt; ++i) {
           if (hd.field(FF::kNch, i) != 0) continue; // heavy: handled as chunks
           const Mask<W> F = hd.mask(i);
@@ -690,15 +900,16 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           const int w = (int)hd.field(FF::kId, i);
           uint64_t s[2 * W] = {};
           unsigned cb = 0;
-          fwd_scan<W>(p, lv, F, l > 0 ? is : 0, l > 0 ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
+          const bool pull = l > 0 && !push;
+          fwd_scan<W>(p, lv, F, pull ? is : 0, pull ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
                       lane, s, cb, dag);
           if (l == 0) unit_counts<W>(s);
-          batch_store_sigma_w<W>(p, w, F, s, cb, lane);
+          if (!push) batch_store_sigma_w<W>(p, w, F, s, cb, lane);
           if (lane == 0) {
             store_mask<W>(p.w.qm, e0 + i, F);
             cnt.entries++;
             cnt.reached += F.popc();
-            cnt.in_e += (uint64_t)(l > 0 ? ie - is : 0);
+            cnt.in_e += (uint64_t)(pull ? ie - is : 0);
             cnt.out_e += (uint64_t)(re - rs);
           }
         }
@@ -1005,19 +1216,22 @@ __device__ __forceinline__ void plain_finish(const KParams &p, int lvl, int v, D
   }
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
+// One source through both sweeps in the given scope: the whole grid of a
+// cooperative launch (grid barriers between levels), or one thread block
+// (block barriers; small graphs, where many such launches run at once).
+template <typename DT, typename Scope>
+__device__ __forceinline__ void plain_body(const KParams &p, const Scope sc) {
   const int lane = threadIdx.x & 31;
-  const int64_t gwarp = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-  const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const int64_t nthr = (int64_t)gridDim.x * kBlock;
+  const int64_t gwarp = (int64_t)sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)sc.size() * kWarpsPerBlock;
+  const int64_t gtid = (int64_t)sc.rank() * kBlock + threadIdx.x;
+  const int64_t nthr = (int64_t)sc.size() * kBlock;
   Ctl *ctl = p.w.ctl;
   Counters cnt;
   if (read_err(ctl)) return;
   const int s = __ldg(p.src);
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sc.rank() == 0 && threadIdx.x == 0) {
     ctl->tail = 1;
     ctl->ovf[0] = 0;
     for (int i = 0; i < 4; ++i) ctl->work[i] = 0;
@@ -1034,8 +1248,8 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
       p.w.hq_c[0] = 0;
     }
   }
-  if (p.skip_block == (int)blockIdx.x) return;
-  if (!grid_sync(ctl, p.timeout_ns)) return;
+  if (Scope::kGrid && p.skip_block == sc.rank()) return; // failure-injection hook
+  if (!sc.sync(ctl, p.timeout_ns)) return;
 
   LevelView lv;
   lv.lvl = 0;
@@ -1135,7 +1349,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
       }
       base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
-    if (!grid_sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
+    if (!sc.sync(ctl, p.timeout_ns, p.w.qoff + l + 2)) return;
     ++step;
     const int64_t nh = ldcg(p.w.qoff + l + 2);
     if (nh == lv.hi) {
@@ -1225,7 +1439,7 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
       }
       base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
     }
-    if (!grid_sync(ctl, p.timeout_ns)) return;
+    if (!sc.sync(ctl, p.timeout_ns)) return;
     ++step;
   }
   trace_step(p, step, 1 << 20, 0, 0, gtid); // end marker
@@ -1234,6 +1448,44 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
     for (int64_t i = gtid; i < q2; i += nthr) p.w.d[ldcg(p.w.qv + i)] = -1;
   }
   flush_counters(p.job_cnt, cnt, lane);
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
+  plain_body<DT>(p, GridScope());
+}
+
+// One source in one thread block: the small-graph form of the one-source
+// launch; the host issues such launches on several streams at once, each
+// stream adding into its own BC partial vector.
+template <typename DT>
+__global__ void __launch_bounds__(kBlock) plain_block_kernel(const KParams p) {
+  plain_body<DT>(p, CtaScope());
+}
+
+// out[v] = sum over parts of parts[part][v], parts in order (deterministic).
+__global__ void sum_parts_kernel(const double *__restrict__ parts, int nparts, int64_t n,
+                                 double *__restrict__ out) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int i = 0; i < nparts; ++i) t += parts[(size_t)i * n + v];
+    out[v] = t;
+  }
+}
+
+// The first device error of any of the control blocks, into the first one.
+__global__ void gather_err_kernel(Ctl *first, size_t stride_bytes, int count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (first->err) return;
+  for (int i = 1; i < count; ++i) {
+    const Ctl *c = reinterpret_cast<const Ctl *>(reinterpret_cast<const char *>(first) +
+                                                 stride_bytes * (size_t)i);
+    if (c->err) {
+      first->err = c->err;
+      return;
+    }
+  }
 }
 
 __global__ void scale_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t n,
@@ -1346,6 +1598,26 @@ cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st,
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st) {
   return fp64 ? coop_launch(plain_kernel<double>, p, grid, st)
               : coop_launch(plain_kernel<float>, p, grid, st);
+}
+
+cudaError_t launch_plain_block(const KParams &p, bool fp64, cudaStream_t st) {
+  if (fp64) plain_block_kernel<double><<<1, kBlock, 0, st>>>(p);
+  else plain_block_kernel<float><<<1, kBlock, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_parts(const double *parts, int nparts, int64_t n, double *out,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  sum_parts_kernel<<<grid, 256, 0, st>>>(parts, nparts, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_err(Ctl *first, size_t stride_bytes, int count, cudaStream_t st) {
+  gather_err_kernel<<<1, 32, 0, st>>>(first, stride_bytes, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor,

@@ -5,6 +5,7 @@ check that it builds, loads, exports every function include/bc_gb300.h
 declares, and that the product path shares no code with the oracle.
 """
 import ctypes
+import subprocess
 import os
 import re
 
@@ -63,8 +64,25 @@ def test_product_path_never_touches_the_oracle():
                 assert "bcgen" not in text, f"{f} imports the input generators"
 
 
-def test_options_struct_matches_header():
+def test_options_struct_matches_header(tmp_path):
+    """The ctypes mirrors have the C structs' sizes and field offsets, as a C
+    compiler lays them out from include/bc_gb300.h."""
     from paper_1409_7764_gb300 import capi
-    assert ctypes.sizeof(capi.bc_opts) == 7 * 4
-    # int64 x5, int32 x2, double, int64 x6, int32 x6
-    assert ctypes.sizeof(capi.bc_stats) == 5 * 8 + 2 * 4 + 8 + 6 * 8 + 6 * 4
+    fields = {"bc_opts": capi.bc_opts, "bc_stats": capi.bc_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bc_gb300.h"',
+             "int main(void) {"]
+    for name, cls in fields.items():
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = []
+    for cls in fields.values():
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, fname).offset for fname, _ in cls._fields_]
+    assert got == want

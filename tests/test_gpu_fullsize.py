@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configurations bench.py
-times (the library's automatic batch width: 256 sources per batch for R-MAT
-scale 16 exact and for 4096 sampled sources, 128 for 1024), on outputs the
+times (the batch width the library keeps for the graph after its width
+trial, at most 256 sources per batch for R-MAT scale 16 exact and for 4096
+sampled sources, at most 128 for 1024), on outputs the
 oracle can compute: BC over source subsets run in the same configuration,
 depths and path counts of single sources bit for bit, and properties of the
 full runs.  Graphs and source samples are the benchmark's own (same seeds).
@@ -32,9 +33,9 @@ def close(got, ref, tol):
         assert rel.max() <= tol, f"max rel err {rel.max():.3e}"
 
 
-def bit_exact(ctx, G, g, srcs, kb):
+def bit_exact(ctx, G, g, srcs, kb, direction="auto"):
     d, sig, _ = ctx.debug_sources(G, np.asarray(srcs, dtype=np.int32), batch_k=kb,
-                                  delta_fp64=True)
+                                  delta_fp64=True, direction=direction)
     for i, s in enumerate(srcs):
         od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, int(s))
         np.testing.assert_array_equal(d[i], od)
@@ -44,20 +45,22 @@ def bit_exact(ctx, G, g, srcs, kb):
 def test_rmat16_exact_full_size(ctx):
     g = bcgen.rmat(16, 16, seed=1)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ctx.exact(G)                                     # first job: width and split trials
     full = ctx.exact(G).copy()                       # the benchmark's call (FP32 dependencies)
     st = ctx.last_stats()
-    assert st["sources"] == g.n and st["batch_sources"] == 256
+    kb = st["batch_sources"]
+    assert st["sources"] == g.n and kb in (64, 128, 256)
     # the exact result is the sum over any partition of the sources
     parts = np.array_split(np.arange(g.n, dtype=np.int32), 4)
-    summed = sum(ctx.sources(G, p_, batch_k=256).copy() for p_ in parts)
+    summed = sum(ctx.sources(G, p_, batch_k=kb).copy() for p_ in parts)
     close(full, summed, 1e-4)
     assert np.all(full >= 0)
     # 256 sources in the same configuration, element by element against the oracle
     src = bcgen.sample_sources(g.n, 256, seed=7)
     ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, src)
     for fp64 in (False, True):
-        close(ctx.sources(G, src, batch_k=256, delta_fp64=fp64), ref, TOL[fp64])
-    bit_exact(ctx, G, g, src[:6], 256)
+        close(ctx.sources(G, src, batch_k=kb, delta_fp64=fp64), ref, TOL[fp64])
+    bit_exact(ctx, G, g, src[:6], kb)
     ctx.destroy_graph(G)
 
 
@@ -70,11 +73,16 @@ def test_rmat20_sampled_full_size(ctx):
     for kb in (128, 256):                              # the 1024- and 4096-source widths
         for fp64 in (False, True):
             close(ctx.sources(G, sub, batch_k=kb, delta_fp64=fp64), ref, TOL[fp64])
+    # path counts pushed at every level (64-bit integer atomics) or pulled
+    for direction in ("push", "pull"):
+        close(ctx.sources(G, sub, batch_k=256, direction=direction), ref, TOL[False])
     bit_exact(ctx, G, g, sub[:3], 128)
+    bit_exact(ctx, G, g, sub[3:5], 128, direction="push")
     # the full 1024-source job as timed: width 128, and the sum over its batches
     full = ctx.sources(G, src1024).copy()
-    assert ctx.last_stats()["batch_sources"] == 128
-    halves = ctx.sources(G, src1024[:512], batch_k=128) + ctx.sources(G, src1024[512:], batch_k=128)
+    kb = ctx.last_stats()["batch_sources"]
+    assert kb in (64, 128)
+    halves = ctx.sources(G, src1024[:512], batch_k=kb) + ctx.sources(G, src1024[512:], batch_k=kb)
     close(full, halves, 1e-4)
     ctx.destroy_graph(G)
 
@@ -86,7 +94,14 @@ def test_ba20_sampled_full_size(ctx):
     ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, src)
     for fp64 in (False, True):
         close(ctx.sources(G, src, batch_k=256, delta_fp64=fp64), ref, TOL[fp64])
+        # the benchmark's direction rule pushes counts on this DAG
+        assert ctx.last_stats()["push_levels"] > 0
+    for direction in ("push", "pull"):
+        close(ctx.sources(G, src, batch_k=256, direction=direction), ref, TOL[False])
+        st = ctx.last_stats()
+        assert (st["push_levels"] > 0) == (direction == "push")
     bit_exact(ctx, G, g, src[:3], 256)
+    bit_exact(ctx, G, g, src[3:5], 256, direction="pull")
     ctx.destroy_graph(G)
 
 
@@ -109,14 +124,16 @@ def test_ba_undirected_30k_d60_full_size(ctx):
     subset in the same configuration and on properties of the full run."""
     g = bcgen.ba_undirected(30000, 30, seed=1)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
+    ctx.exact(G)                                     # first job: width and split trials
     full = ctx.exact(G).copy()
     st = ctx.last_stats()
-    assert st["sources"] == g.n and st["batch_sources"] == 256
+    kb = st["batch_sources"]
+    assert st["sources"] == g.n and kb in (64, 128, 256)
     assert np.all(full >= 0)
     # every source reaches every vertex (the graph is connected)
     assert st["reached_pairs"] == g.n * g.n
     src = np.concatenate([np.arange(8), bcgen.sample_sources(g.n, 248, seed=9)]).astype(np.int32)
     ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, src)
     for fp64 in (False, True):
-        close(ctx.sources(G, src, batch_k=256, delta_fp64=fp64), ref, TOL[fp64])
-    bit_exact(ctx, G, g, src[:4], 256)
+        close(ctx.sources(G, src, batch_k=kb, delta_fp64=fp64), ref, TOL[fp64])
+    bit_exact(ctx, G, g, src[:4], kb)
