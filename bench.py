@@ -355,8 +355,8 @@ def run_ours(args, w, name):
     ctx = bc.Context(local, stream=stream)
     fp64 = bool(w.get("fp64", False)) or args.fp64
     opts = dict(schedule=args.schedule or w["schedule"], batch_k=w["batch_k"],
-                delta_fp64=fp64,
-                keep_source_order=args.keep_source_order)
+                delta_fp64=fp64, keep_source_order=args.keep_source_order,
+                count_bits=args.count_bits, direction=args.direction)
     G = ctx.create_graph(g.row_ptr, g.col_idx)
     out = torch.zeros(g.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -486,7 +486,9 @@ def run_ours(args, w, name):
             "metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong",
-            "vs_baseline": None, "dtype": "u64+f64" if fp64 else "u64+f32",
+            "vs_baseline": None,
+            "dtype": ("u64" if (args.count_bits == 64 or opts["schedule"] == "plain") else "u32")
+                     + ("+f64" if fp64 else "+f32"),
             "data": "synthetic",
             "config": dict(describe(name, w, g, len(srcs)),
                            batch_k=int(st.get("batch_sources") or w["batch_k"]),
@@ -515,7 +517,7 @@ def run_ours(args, w, name):
                                             "scanned_out_edges", "dag_pairs", "reached_pairs",
                                             "heavy_chunks", "max_levels", "levels_sum",
                                             "batches", "kernel_kind", "chunk_edges", "grab",
-                                            "batch_sources", "mask_words")},
+                                            "batch_sources", "mask_words", "push_levels")},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -760,6 +762,10 @@ def main():
                     help="sources per batch (0: the library picks; default: the workload's)")
     ap.add_argument("--keep-source-order", action="store_true",
                     help="batches take the sources in the given order instead of the library's grouping")
+    ap.add_argument("--count-bits", type=int, default=0, choices=[0, 32, 64],
+                    help="path-count storage (0: the library's default, 32 bits with promotion)")
+    ap.add_argument("--direction", default="auto", choices=["auto", "pull", "push"],
+                    help="path-count step direction of the batched forward levels")
     ap.add_argument("--many-count", type=int, default=10000)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--line-serve-requests", type=int, default=500,

@@ -108,6 +108,11 @@ typedef struct {
                             atomics; both give the same exact counts.  A pushed count of
                             2^32 or more makes the job rerun pulling (and later jobs on
                             that graph pull) */
+  int32_t count_bits;    /* storage of the batched schedules' path counts: 0 (default) = 32
+                            bits, and a job in which a count reaches 2^32 reruns with 64 bits
+                            (so do later jobs on that graph); 64 = always 64 bits.  Sums and
+                            results are the same; 32-bit rows halve the bytes each
+                            shortest-path edge moves.  Estimator calls use 64 bits */
 } bc_opts;
 
 /* Per-call statistics.  Counters feed the bytes model of the roofline. */

@@ -59,7 +59,7 @@ def _check(rc: int, what: str):
 def make_opts(delta_fp64: bool = False, batch_k: int = 0, schedule="auto",
               normalize: bool = False, scale_sampled: bool = False,
               out_device: bool = False, keep_source_order: bool = False,
-              direction="auto") -> bc_opts:
+              direction="auto", count_bits: int = 0) -> bc_opts:
     o = bc_opts()
     o.delta_fp64 = int(bool(delta_fp64))
     o.batch_k = int(batch_k)
@@ -69,6 +69,7 @@ def make_opts(delta_fp64: bool = False, batch_k: int = 0, schedule="auto",
     o.out_device = int(bool(out_device))
     o.source_order = int(bool(keep_source_order))
     o.direction = _DIRECTION[direction] if isinstance(direction, str) else int(direction)
+    o.count_bits = int(count_bits)
     return o
 
 

@@ -45,7 +45,8 @@ class bc_opts(ctypes.Structure):
     _fields_ = [("delta_fp64", ctypes.c_int32), ("batch_k", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("normalize", ctypes.c_int32),
                 ("scale_sampled", ctypes.c_int32), ("out_device", ctypes.c_int32),
-                ("source_order", ctypes.c_int32), ("direction", ctypes.c_int32)]
+                ("source_order", ctypes.c_int32), ("direction", ctypes.c_int32),
+                ("count_bits", ctypes.c_int32)]
 
 
 class bc_stats(ctypes.Structure):

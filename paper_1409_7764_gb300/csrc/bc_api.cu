@@ -86,6 +86,8 @@ struct GraphRec {
   std::atomic<bool> narrow{false};
   // a pushed path count was 2^32 or more: later jobs pull every level
   std::atomic<bool> no_push{false};
+  // a path count reached 2^32: later jobs store counts in 64 bits
+  std::atomic<bool> wide_counts{false};
   // batch composition (see order_key): host copies of the out-CSR
   // offsets and of the two-hop walk counts; every vertex in batch order, made
   // on first need (kept on the host and in d_order)
@@ -189,6 +191,14 @@ struct WsRec {
   Work w;                   // the workspace (slot 0)
   size_t slot_bytes = 0;    // stride between slot copies
   double *parts = nullptr;  // slots > 1: [slots][n] BC partial sums, one per slot
+  KParams *slot_params = nullptr; // slots > 1: [slots] launch parameters, rewritten per job
+  // slots > 1: the one-block launches of a job of plain_k sources on plain_s
+  // streams, captured once as a CUDA graph (the launches read everything that
+  // changes between jobs from slot_params)
+  cudaGraphExec_t plain_exec = nullptr;
+  int64_t plain_k = 0;
+  int plain_s = 0;
+  bool plain_fp64 = false;
   void *mem = nullptr;
   size_t bytes = 0;
   bool dirty = false;
@@ -296,8 +306,19 @@ size_t ws_layout(WsRec &r, char *mem) {
     return one;
   }
   r.slot_bytes = one;
-  r.parts = mem ? reinterpret_cast<double *>(mem + one * (size_t)r.slots) : nullptr;
-  return align_up(one * (size_t)r.slots + sizeof(double) * (size_t)r.n * (size_t)r.slots, 256);
+  const size_t parts_at = one * (size_t)r.slots;
+  const size_t params_at = align_up(parts_at + sizeof(double) * (size_t)r.n * (size_t)r.slots, 256);
+  r.parts = mem ? reinterpret_cast<double *>(mem + parts_at) : nullptr;
+  r.slot_params = mem ? reinterpret_cast<KParams *>(mem + params_at) : nullptr;
+  return align_up(params_at + sizeof(KParams) * (size_t)r.slots, 256);
+}
+
+// Releases a workspace's device memory and captured launches.
+void ws_free(WsRec &r) {
+  if (r.plain_exec) cudaGraphExecDestroy(r.plain_exec);
+  r.plain_exec = nullptr;
+  cudaFree(r.mem);
+  r.mem = nullptr;
 }
 
 // The workspace copy of slot i (plain, one block per source).
@@ -358,6 +379,7 @@ struct bc_ctx {
   std::mutex aux_mu;
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> aux_ev;
+  cudaStream_t aux_root = nullptr; // stream the launches are captured on
   int32_t inject_block = -1;
   int32_t inject_timeout_ms = 0;
 
@@ -445,6 +467,7 @@ struct JobRec {
   double *acc_sum = nullptr, *acc_sumsq = nullptr; // estimator jobs: running sums to add into
   int8_t *d_ovf = nullptr;
   unsigned long long *d_cnt = nullptr;
+  KParams *h_slots = nullptr; // one-block plain form: pinned staging of the launch parameters
   int32_t *h_src = nullptr;   // pinned staging
   double *h_out = nullptr;    // pinned result (async jobs)
   unsigned long long *h_cnt = nullptr; // pinned: counters + err + ovf count
@@ -461,13 +484,15 @@ struct JobRec {
   int kb = 0;                // sources per batch of the last launch
   int words = 1;             // mask words of the last launch
   int cand = 0;              // tuning candidate of the last launch
+  int ws_slots = 0;          // one-block plain form: streams (entries of h_slots)
   size_t footprint = 0;
   bc_status status = BC_PENDING;
   bc_stats stats{};
   bool done = false;
 };
 
-// internal: the job must be launched again (a wide batch overran its queue)
+// internal: the job must be launched again (a wide batch overran its queue,
+// a count needed 64 bits or a pushed count was too large to push)
 constexpr bc_status kStatusRetry = static_cast<bc_status>(100);
 
 bc_status cuda_status(cudaError_t e) {
@@ -497,7 +522,8 @@ bool opts_valid(const bc_opts &o) {
          (o.scale_sampled == 0 || o.scale_sampled == 1) &&
          (o.out_device == 0 || o.out_device == 1) &&
          (o.source_order == 0 || o.source_order == 1) &&
-         (o.direction >= 0 && o.direction <= 2);
+         (o.direction >= 0 && o.direction <= 2) &&
+         (o.count_bits == 0 || o.count_bits == 32 || o.count_bits == 64);
 }
 
 int resolve_schedule(const bc_opts &o, const GraphDev &) {
@@ -1004,7 +1030,7 @@ bc_status ws_acquire(bc_ctx *ctx, const WsNeed &nd, cudaStream_t st, std::unique
       victim = std::move(ctx->free_ws.back());
       ctx->free_ws.pop_back();
     }
-    cudaFree(victim->mem);
+    ws_free(*victim);
     ctx->used -= victim->bytes;
   }
   if (ctx->used + r->bytes > ctx->budget) return BC_ERR_ADMISSION;
@@ -1068,6 +1094,8 @@ void job_free_buffers(bc_ctx *ctx, JobRec *j) {
   j->d_bc2 = nullptr;
   if (j->d_ovf) cudaFreeAsync(j->d_ovf, j->st);
   if (j->d_cnt) cudaFreeAsync(j->d_cnt, j->st);
+  if (j->h_slots) pin_put(ctx, j->h_slots, sizeof(KParams) * (size_t)std::max(j->ws_slots, 1));
+  j->h_slots = nullptr;
   j->d_src = nullptr;
   j->d_bc = nullptr;
   j->d_ovf = nullptr;
@@ -1125,54 +1153,76 @@ bc_status trial_times(std::vector<cudaEvent_t> &ev, const std::vector<int> &slot
 // workspace copy and BC partial vector; the job's stream waits for all of
 // them, sums the partial vectors in slot order and collects the first
 // device error of any slot.
-bc_status run_plain_blocks(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg,
-                           int trace_cap) {
+bc_status run_plain_blocks(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg) {
   WsRec *ws = j->ws.get();
   const int64_t n = j->g->dev.n, k = j->k;
   const bool fp64 = j->opts.delta_fp64 != 0;
   const int S = (int)std::min<int64_t>(ws->slots, k);
   cudaStream_t st = j->st;
-  {
-    std::lock_guard<std::mutex> lk(ctx->aux_mu);
-    while ((int)ctx->aux.size() < S) {
-      cudaStream_t a = nullptr;
-      cudaEvent_t e = nullptr;
-      BC_TRY(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
-      BC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      ctx->aux.push_back(a);
-      ctx->aux_ev.push_back(e);
-    }
-  }
   // one job at a time uses the extra streams (jobs of other threads wait)
   std::lock_guard<std::mutex> lk(ctx->aux_mu);
-  BC_TRY(cudaMemsetAsync(ws->parts, 0, sizeof(double) * (size_t)n * (size_t)S, st));
-  cudaEvent_t start = ctx->aux_ev[0];
-  BC_TRY(cudaEventRecord(start, st));
-  for (int i = 0; i < S; ++i) BC_TRY(cudaStreamWaitEvent(ctx->aux[(size_t)i], start, 0));
+  while ((int)ctx->aux.size() < S) {
+    cudaStream_t a = nullptr;
+    cudaEvent_t e = nullptr;
+    BC_TRY(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    BC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->aux.push_back(a);
+    ctx->aux_ev.push_back(e);
+  }
+  if (!ctx->aux_root) BC_TRY(cudaStreamCreateWithFlags(&ctx->aux_root, cudaStreamNonBlocking));
+  // each slot's parameters (a launch adds its source's position b),
+  // staged in pinned memory and copied in stream order
   p.g.nchunks = j->g->nch_variant[kSplitWarp];
   p.grab = kGrabDefault;
   p.k = 1;
-  for (int64_t b = 0; b < k; ++b) {
-    const int slot = (int)(b % S);
-    p.w = slot_work(*ws, slot);
-    p.bc = ws->parts + (size_t)slot * (size_t)n;
-    p.src = j->d_src + b;
-    p.src_base = b;
-    p.trace = (j->d_trace && b == j->trace_batch) ? j->d_trace : nullptr;
-    p.trace_cap = p.trace ? trace_cap : 0;
-    if (dbg) {
-      p.dbg_d = dbg->d + b * n;
-      p.dbg_sigma = dbg->sigma + b * n;
-      p.dbg_delta = dbg->delta + b * n;
-    }
-    BC_TRY(launch_plain_block(p, fp64, ctx->aux[(size_t)slot]));
-    ++j->batches;
-    ++j->launches;
+  p.src = j->d_src;
+  p.src_base = 0;
+  p.trace = nullptr;
+  p.trace_cap = 0;
+  if (dbg) {
+    p.dbg_d = dbg->d;
+    p.dbg_sigma = dbg->sigma;
+    p.dbg_delta = dbg->delta;
   }
+  j->ws_slots = S;
+  BC_TRY(pin_get(ctx, &j->h_slots, sizeof(KParams) * (size_t)S));
   for (int i = 0; i < S; ++i) {
-    BC_TRY(cudaEventRecord(ctx->aux_ev[(size_t)i], ctx->aux[(size_t)i]));
-    BC_TRY(cudaStreamWaitEvent(st, ctx->aux_ev[(size_t)i], 0));
+    j->h_slots[i] = p;
+    j->h_slots[i].w = slot_work(*ws, i);
+    j->h_slots[i].bc = ws->parts + (size_t)i * (size_t)n;
   }
+  BC_TRY(cudaMemcpyAsync(ws->slot_params, j->h_slots, sizeof(KParams) * (size_t)S,
+                         cudaMemcpyHostToDevice, st));
+  BC_TRY(cudaMemsetAsync(ws->parts, 0, sizeof(double) * (size_t)n * (size_t)S, st));
+  // the k launches over S streams, captured once per (k, S, precision) and
+  // replayed: one graph launch costs the host far less than k launches
+  if (!ws->plain_exec || ws->plain_k != k || ws->plain_s != S || ws->plain_fp64 != fp64) {
+    if (ws->plain_exec) cudaGraphExecDestroy(ws->plain_exec);
+    ws->plain_exec = nullptr;
+    cudaStream_t cs = ctx->aux_root;
+    BC_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = cudaEventRecord(ctx->aux_ev[0], cs);
+    for (int i = 0; i < S && e == cudaSuccess; ++i)
+      e = cudaStreamWaitEvent(ctx->aux[(size_t)i], ctx->aux_ev[0], 0);
+    for (int64_t b = 0; b < k && e == cudaSuccess; ++b)
+      e = launch_plain_block(ws->slot_params, (int)(b % S), b, fp64, ctx->aux[(size_t)(b % S)]);
+    for (int i = 0; i < S && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(ctx->aux_ev[(size_t)i], ctx->aux[(size_t)i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->aux_ev[(size_t)i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ws->plain_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    BC_TRY(e);
+    ws->plain_k = k;
+    ws->plain_s = S;
+    ws->plain_fp64 = fp64;
+  }
+  BC_TRY(cudaGraphLaunch(ws->plain_exec, st));
+  j->batches += k;
+  j->launches += k;
   BC_TRY(launch_sum_parts(ws->parts, S, n, j->d_bc, st));
   BC_TRY(launch_gather_err(ws->w.ctl, ws->slot_bytes, S, st));
   j->launches += 2;
@@ -1202,8 +1252,10 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
   const int kind = j->kind;
   const int fixed = fixed_split(resolve_schedule(j->opts, g));
   const bool notune = dbg || kind != WS_QUEUE || std::getenv("BC_NO_TUNE");
+  // 32-bit path-count rows unless asked for 64 bits or this graph needed them
+  const bool c32 = j->opts.count_bits != 64 && !j->g->wide_counts && !j->acc_sum;
   WsRec *ws = j->ws.get();
-  if (kind == WS_PLAIN && ws->slots > 1) return run_plain_blocks(ctx, j, p, dbg, trace_cap);
+  if (kind == WS_PLAIN && ws->slots > 1) return run_plain_blocks(ctx, j, p, dbg);
   const size_t ctl_bytes = align_up(sizeof(Ctl), 256);
   int cur_words = j->words; // layout the workspace holds
   int64_t bi = 0, b0 = 0;
@@ -1232,7 +1284,7 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
     }
     const int grid = pick_grid(ctx, g, kind, fp64, words);
     if (grid <= 0) return BC_ERR_CUDA;
-    BC_TRY(kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words)
+    BC_TRY(kind == WS_QUEUE ? launch_batch(p, fp64, grid, st, words, c32)
                             : launch_plain(p, fp64, grid, st));
     b0 += p.k;
     ++bi;
@@ -1526,7 +1578,13 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.overflow_sources = novf;
   bc_status st = BC_OK;
   const int kerr = *j->h_err;
-  if (kerr == KERR_PUSH) {
+  if (kerr == KERR_WIDE) {
+    // a path count reached 2^32: rerun the job with 64-bit counts (and keep
+    // them for this graph)
+    j->g->wide_counts = true;
+    st = kStatusRetry;
+    j->ws->dirty = true;
+  } else if (kerr == KERR_PUSH) {
     // a pushed path count reached 2^32, so a pushed sum could have carried:
     // rerun the job pulling every level (and keep pulling on this graph)
     j->g->no_push = true;
@@ -1564,7 +1622,7 @@ bc_status run_sync(bc_ctx *ctx, GraphRec *g, const int32_t *src, int64_t k, bool
   j.acc_sum = acc_sum;
   j.acc_sumsq = acc_sumsq;
   bc_status s = kStatusRetry;
-  for (int attempt = 0; attempt < 3 && s == kStatusRetry; ++attempt) {
+  for (int attempt = 0; attempt < 5 && s == kStatusRetry; ++attempt) {
     s = job_launch(ctx, &j, out, dbg);
     if (s != BC_OK) {
       cudaStreamSynchronize(j.st);
@@ -1767,7 +1825,7 @@ bc_status bc_shutdown(bc_ctx *ctx) {
     if (kv.second->h_out) cudaFreeHost(kv.second->h_out);
   }
   ctx->jobs.clear();
-  for (auto &w : ctx->free_ws) cudaFree(w->mem);
+  for (auto &w : ctx->free_ws) ws_free(*w);
   ctx->free_ws.clear();
   for (auto &kv : ctx->graphs) cudaFreeAsync(kv.second->mem, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
@@ -1779,6 +1837,7 @@ bc_status bc_shutdown(bc_ctx *ctx) {
   for (int i = 0; i < kMaxSlots; ++i)
     if (ctx->slot_stream[i]) cudaStreamDestroy(ctx->slot_stream[i]);
   for (cudaStream_t a : ctx->aux) cudaStreamDestroy(a);
+  if (ctx->aux_root) cudaStreamDestroy(ctx->aux_root);
   for (cudaEvent_t e : ctx->aux_ev) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

@@ -266,44 +266,53 @@ template <int W, typename DT> struct CoeffUnroll {
       (BC_GATHER_FORM >= 1 && sizeof(DT) == 4) ? 2 * GatherUnroll<W>::value : GatherUnroll<W>::value;
 };
 
-// s += x, with the carry out of bit 63 added to c (c counts carries).
+// s += x, with the carry out of the top bit added to c (c counts carries).
 __device__ __forceinline__ void add_count_carry(uint64_t &s, uint64_t x, unsigned &c) {
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(s), "+r"(c) : "l"(x));
 }
+__device__ __forceinline__ void add_count_carry(uint32_t &s, uint32_t x, unsigned &c) {
+  asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(s), "+r"(c) : "r"(x));
+}
+
+// Edges per round of the path-count gather: 4-byte counts (the 32-bit
+// storage form) keep twice as many edges in flight in the same registers.
+template <int W, typename CT> struct CountUnroll {
+  static constexpr int value = sizeof(CT) == 4 ? 2 * GatherUnroll<W>::value : GatherUnroll<W>::value;
+};
 
 // Path counts over the round's shortest-path edges (lanes whose mask P is not
 // empty, in lane order): lane j adds row[32*i + j] of each edge's row for
-// every slot i whose bit is set, in edge order.  kExact: the carry of slot
-// i is recorded in bit i of cbits (a carry means the true count reached
-// 2^64).  Otherwise cbits only counts carries: any carry sends the caller to
-// the exact form, which is rare (counts near 2^64) and gives the same sums.
-template <int W, bool kExact = true>
-__device__ __forceinline__ void gather_counts_w(const uint64_t *base, int u, const Mask<W> &P,
-                                                int lane, uint64_t (&s)[2 * W],
-                                                unsigned &cbits) {
-  constexpr int U = GatherUnroll<W>::value;
+// every slot i whose bit is set, in edge order.  kExact (64-bit counts): the
+// carry of slot i is recorded in bit i of cbits (a carry means the true
+// count reached 2^64).  Otherwise cbits only counts carries out of the
+// count's width: the caller then takes the exact form (64-bit counts, rare:
+// counts near 2^64) or promotes the job to 64-bit counts (32-bit storage).
+template <int W, bool kExact = true, typename CT = uint64_t>
+__device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mask<W> &P,
+                                                int lane, CT (&s)[2 * W], unsigned &cbits) {
+  constexpr int U = CountUnroll<W, CT>::value;
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, P.any());
   while (bal) {
     const LanesU<U> q(bal);
-    uint64_t x[U][2 * W];
+    CT x[U][2 * W];
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const int uu = shfl_or_zero(u, q.l[i]);
-      const uint64_t *row = base + (size_t)uu * (kK * W) + lane;
+      const CT *row = base + (size_t)uu * (kK * W) + lane;
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
         const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
         const unsigned lo = (unsigned)PP, hi = (unsigned)(PP >> 32);
-        x[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : 0ull;
-        x[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : 0ull;
+        x[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : CT(0);
+        x[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : CT(0);
       }
     }
 #pragma unroll
     for (int i = 0; i < U; ++i)
 #pragma unroll
       for (int t = 0; t < 2 * W; ++t) {
-        if (kExact || BC_GATHER_FORM == 0) {
+        if ((kExact || BC_GATHER_FORM == 0) && sizeof(CT) == 8) {
           s[t] += x[i][t];
           cbits |= (s[t] < x[i][t] ? 1u : 0u) << t;
         } else {
@@ -365,14 +374,15 @@ __device__ __forceinline__ void batch_pull_delta_w(const KParams &p, const Mask<
 
 // Writes the path counts of entry w (mask F; counts saturated where the carry
 // bit is set) and records the overflowing sources in the control block.
-template <int W>
+// Counts are stored as CT (32-bit counts are below 2^32 here).
+template <int W, typename CT, typename AT>
 __device__ __forceinline__ void batch_store_sigma_w(const KParams &p, int w, const Mask<W> &F,
-                                                    const uint64_t (&s)[2 * W], unsigned cbits,
+                                                    const AT (&s)[2 * W], unsigned cbits,
                                                     int lane) {
-  uint64_t *row = p.w.sigma + (size_t)w * (kK * W);
+  CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)w * (kK * W);
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i)
-    if (F.has(i, lane)) row[32 * i + lane] = ((cbits >> i) & 1u) ? ~0ull : s[i];
+    if (F.has(i, lane)) row[32 * i + lane] = ((cbits >> i) & 1u) ? CT(~0ull) : CT(s[i]);
 #pragma unroll
   for (int wi = 0; wi < W; ++wi) {
     const uint64_t ob = ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi)) & 1u) |

@@ -58,6 +58,7 @@ enum : int {
   KERR_CHUNKS = 4,   // heavy chunk scratch exceeded
   KERR_GRAB = 6,     // more work items per fetch than a header round holds (host bug)
   KERR_PUSH = 7,     // a pushed path count was 2^32 or more: the job reruns pulling counts
+  KERR_WIDE = 8,     // a path count did not fit 32-bit storage: the job reruns with 64 bits
 };
 
 // Job-level counters (uint64 each), accumulated by the kernels.
@@ -179,9 +180,11 @@ struct ManyParams {
 // Host launchers (bc_kernels.cu).  Return a cudaError_t.
 cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st);
 int max_grid_many(bool fp64, int device);
-cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1);
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1,
+                         bool counts32 = false);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
-cudaError_t launch_plain_block(const KParams &p, bool fp64, cudaStream_t st);
+cudaError_t launch_plain_block(const KParams *slots, int slot, int64_t b, bool fp64,
+                               cudaStream_t st);
 cudaError_t launch_sum_parts(const double *parts, int nparts, int64_t n, double *out,
                              cudaStream_t st);
 cudaError_t launch_gather_err(Ctl *first, size_t stride_bytes, int count, cudaStream_t st);

@@ -202,9 +202,9 @@ __device__ __forceinline__ void stage_new(const KParams &p, const LevelView &lv,
 
 // Path-count pull of an entry (mask F) over its in-edges [ib, ib + din)
 // from the level l-1 masks Pm, in edge order.
-template <int W, bool kExact>
+template <int W, bool kExact, typename CT>
 __device__ __forceinline__ void pull_counts(const KParams &p, const Mask<W> &F, int ib, int din,
-                                            const uint64_t *Pm, int lane, uint64_t (&s)[2 * W],
+                                            const uint64_t *Pm, int lane, CT (&s)[2 * W],
                                             unsigned &cbits, unsigned long long &dag) {
   for (int r = 0; r < din; r += kWarp) {
     const int t = r + lane;
@@ -215,7 +215,8 @@ __device__ __forceinline__ void pull_counts(const KParams &p, const Mask<W> &F, 
       P = load_mask<W>(Pm, u) & F;
     }
     dag += P.popc(); // per lane; the warp's counters are summed at the flush
-    gather_counts_w<W, kExact>(p.w.sigma, u, P, lane, s, cbits);
+    gather_counts_w<W, kExact, CT>(reinterpret_cast<const CT *>(p.w.sigma), u, P, lane, s,
+                                   cbits);
   }
 }
 
@@ -229,7 +230,7 @@ __device__ __forceinline__ void exact_counts(const KParams &p, const Mask<W> &F,
   for (int i = 0; i < 2 * W; ++i) s[i] = 0;
   cbits = 0;
   unsigned long long dag = 0; // counted by the fast pull already
-  pull_counts<W, true>(p, F, ib, din, Pm, lane, s, cbits, dag);
+  pull_counts<W, true, uint64_t>(p, F, ib, din, Pm, lane, s, cbits, dag);
 }
 
 // Pushed path counts (the other direction of the forward step at level l):
@@ -239,23 +240,32 @@ __device__ __forceinline__ void exact_counts(const KParams &p, const Mask<W> &F,
 // of level l are complete when the step starts, so exactly the
 // shortest-path DAG edges into level l receive counts; the adds are 64-bit
 // integer atomics, whose order does not change the sums.  The target counts
-// start at zero (every batch resets the counts it wrote).  Overflow is ruled
-// out before adding: the step refuses (KERR_PUSH, and the job reruns
-// pulling counts) as soon as a pushed count is 2^32 or more, so every sum
-// of fewer than 2^31 pushed terms stays below 2^63.
-template <int W>
+// start at zero (every batch resets the counts it wrote).  64-bit counts:
+// overflow is ruled out before adding: the step refuses (KERR_PUSH, and the
+// job reruns pulling counts) as soon as a pushed count is 2^32 or more, so
+// every sum of fewer than 2^31 pushed terms stays below 2^63, and the adds
+// need no reply.  32-bit counts: each add returns the old value, and a sum
+// that wraps promotes the job to 64-bit counts (KERR_WIDE).
+__device__ __forceinline__ void push_add(uint64_t *a, uint64_t v, unsigned &) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
+}
+__device__ __forceinline__ void push_add(uint32_t *a, uint32_t v, unsigned &wrap) {
+  const unsigned old = atomicAdd(reinterpret_cast<unsigned *>(a), v);
+  wrap |= (old + v < old) ? 1u : 0u;
+}
+template <int W, typename CT>
 __device__ __forceinline__ void push_counts(const KParams &p, int u, const Mask<W> &F, int ob,
                                             int oe, const uint64_t *A, int lane,
                                             unsigned long long &dag) {
-  uint64_t own[2 * W];
-  const uint64_t *srow = p.w.sigma + (size_t)u * (kK * W) + lane;
-  unsigned big = 0;
+  CT own[2 * W];
+  const CT *srow = reinterpret_cast<const CT *>(p.w.sigma) + (size_t)u * (kK * W) + lane;
+  unsigned big = 0, wrap = 0;
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) {
-    own[i] = F.has(i, lane) ? ldcg(srow + 32 * i) : 0ull;
-    big |= (unsigned)(own[i] >> 32);
+    own[i] = F.has(i, lane) ? ldcg(srow + 32 * i) : CT(0);
+    if constexpr (sizeof(CT) == 8) big |= (unsigned)(own[i] >> 32);
   }
-  if (__any_sync(kFull, big != 0)) {
+  if (sizeof(CT) == 8 && __any_sync(kFull, big != 0)) {
     set_err(p.w.ctl, KERR_PUSH);
     return;
   }
@@ -274,16 +284,16 @@ __device__ __forceinline__ void push_counts(const KParams &p, int u, const Mask<
       const int src = __ffs(bal) - 1;
       bal &= bal - 1;
       const int xx = __shfl_sync(kFull, x, src);
-      unsigned long long *row =
-          reinterpret_cast<unsigned long long *>(p.w.sigma) + (size_t)xx * (kK * W) + lane;
+      CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)xx * (kK * W) + lane;
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
         const uint64_t PP = __shfl_sync(kFull, P.w[wi], src);
-        if ((unsigned)PP & mybit) atomicAdd(row + 64 * wi, own[2 * wi]);
-        if ((unsigned)(PP >> 32) & mybit) atomicAdd(row + 64 * wi + 32, own[2 * wi + 1]);
+        if ((unsigned)PP & mybit) push_add(row + 64 * wi, own[2 * wi], wrap);
+        if ((unsigned)(PP >> 32) & mybit) push_add(row + 64 * wi + 32, own[2 * wi + 1], wrap);
       }
     }
   }
+  if (sizeof(CT) == 4 && __any_sync(kFull, wrap != 0)) set_err(p.w.ctl, KERR_WIDE);
 }
 
 // Forward work of one frontier entry (mask F) at level l: the path-count
@@ -297,22 +307,35 @@ __device__ __forceinline__ void push_counts(const KParams &p, int u, const Mask<
 // toucher; it is read only after the round's path-count gathers.  With
 // several words no single atomic covers the mask: a claim on x decides
 // (claim[x] < l+2 before, raised to l+2).
-template <int W>
+// After a fast pull saw a carry: 64-bit counts pull again recording each
+// slot's carry (the counts saturate); 32-bit counts stop the batch, and the
+// job reruns with 64-bit counts.
+template <int W, typename CT>
+__device__ __forceinline__ void settle_carries(const KParams &p, const Mask<W> &F, int ib,
+                                               int din, const uint64_t *Pm, int lane,
+                                               CT (&s)[2 * W], unsigned &cbits,
+                                               unsigned carries) {
+  if (!__any_sync(kFull, carries != 0)) return;
+  if constexpr (sizeof(CT) == 4) set_err(p.w.ctl, KERR_WIDE);
+  else exact_counts<W>(p, F, ib, din, Pm, lane, s, cbits);
+}
+
+template <int W, typename CT>
 __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, const Mask<W> &F,
                                          int ib, int ie, int ob, int oe,
                                          const uint64_t *A, const uint64_t *Pm, uint64_t *Bn,
-                                         int *stage, int &nst, int lane, uint64_t (&s)[2 * W],
+                                         int *stage, int &nst, int lane, CT (&s)[2 * W],
                                          unsigned &cbits, unsigned long long &dag) {
   const int din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
   const int claim_to = lv.lvl + 2;
-  constexpr bool kFast = BC_GATHER_FORM >= 1;
-  unsigned carries = 0; // fast form: carries out of bit 63 (any -> exact rerun)
+  constexpr bool kFast = BC_GATHER_FORM >= 1 || sizeof(CT) == 4;
+  unsigned carries = 0; // fast form: carries out of the count's width
   if constexpr (W >= 2) {
     // wide masks: the pull and the push run as two loops, so the registers
     // of the path-count gathers and of the discovery masks are not live
     // together
-    pull_counts<W, !kFast>(p, F, ib, din, Pm, lane, s, kFast ? carries : cbits, dag);
-    if (kFast && __any_sync(kFull, carries != 0)) exact_counts<W>(p, F, ib, din, Pm, lane, s, cbits);
+    pull_counts<W, !kFast, CT>(p, F, ib, din, Pm, lane, s, kFast ? carries : cbits, dag);
+    if (kFast) settle_carries<W, CT>(p, F, ib, din, Pm, lane, s, cbits, carries);
     for (int r = 0; r < dout; r += kWarp) {
       const int t = r + lane;
       int x = 0;
@@ -353,10 +376,11 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
       dag += __popcll(P); // per lane; the warp's counters are summed at the flush
       Mask<1> PM;
       PM.w[0] = P;
-      gather_counts_w<1, !kFast>(p.w.sigma, u, PM, lane, s, kFast ? carries : cbits);
+      gather_counts_w<1, !kFast, CT>(reinterpret_cast<const CT *>(p.w.sigma), u, PM, lane, s,
+                                     kFast ? carries : cbits);
       stage_new(p, lv, nb != 0 && old == 0, x, stage, nst, lane);
     }
-    if (kFast && __any_sync(kFull, carries != 0)) exact_counts<1>(p, F, ib, din, Pm, lane, s, cbits);
+    if (kFast) settle_carries<1, CT>(p, F, ib, din, Pm, lane, s, cbits, carries);
   }
 }
 
@@ -417,12 +441,12 @@ template <typename DT, int W> struct EntrySum {
 // form of the forward step adds into them).  At level 0 every source bit of
 // the entry is the vertex itself, whose own dependency is never added to its
 // BC; at deeper levels no source of the entry is the vertex.
-template <typename DT, int W, bool SQ>
+template <typename DT, int W, bool SQ, typename CT>
 __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, const Mask<W> &F,
-                                             const DT (&a)[2 * W], const uint64_t (&sg)[2 * W],
+                                             const DT (&a)[2 * W], const CT (&sg)[2 * W],
                                              double bcv, uint64_t *Wn, int lane) {
   DT *crow = reinterpret_cast<DT *>(p.w.cdep) + (size_t)v * (kK * W);
-  uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
+  CT *srow = reinterpret_cast<CT *>(p.w.sigma) + (size_t)v * (kK * W);
   EntrySum<DT, W> sum;
   double contrib2 = 0.0;
   const int n = p.g.n;
@@ -430,7 +454,7 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
   for (int i = 0; i < 2 * W; ++i)
     if (F.has(i, lane)) {
       const int j = 32 * i + lane; // source index within the batch (j < k)
-      const DT sf = u64_to<DT>(sg[i]);
+      const DT sf = u64_to<DT>((uint64_t)sg[i]);
       const DT dl = sf * a[i];
       crow[j] = (DT(1) + dl) / sf;
       srow[j] = 0;
@@ -462,13 +486,13 @@ __device__ __forceinline__ void batch_finish(const KParams &p, int lvl, int v, c
 
 // Loads of an entry's own path counts and BC value, issued before its
 // successor scan so they overlap it.
-template <int W> struct EntryOwn {
-  uint64_t sg[2 * W];
+template <int W, typename CT> struct EntryOwn {
+  CT sg[2 * W];
   double bcv;
   __device__ __forceinline__ EntryOwn(const KParams &p, int v, const Mask<W> &F, int lane) {
-    const uint64_t *srow = p.w.sigma + (size_t)v * (kK * W);
+    const CT *srow = reinterpret_cast<const CT *>(p.w.sigma) + (size_t)v * (kK * W);
 #pragma unroll
-    for (int i = 0; i < 2 * W; ++i) sg[i] = F.has(i, lane) ? ldcg(srow + 32 * i + lane) : 0ull;
+    for (int i = 0; i < 2 * W; ++i) sg[i] = F.has(i, lane) ? ldcg(srow + 32 * i + lane) : CT(0);
     bcv = lane == 0 ? ldcg(p.bc + v) : 0.0;
   }
 };
@@ -642,7 +666,7 @@ __device__ __forceinline__ Counters to_counters(const WarpCounters &w, unsigned 
 
 // Sets the path counts of a level-0 entry (every source bit of it is the
 // vertex itself: one path) in the lane's slots.
-template <int W> __device__ __forceinline__ void unit_counts(uint64_t (&s)[2 * W]) {
+template <int W, typename T> __device__ __forceinline__ void unit_counts(T (&s)[2 * W]) {
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) s[i] = 1;
 }
@@ -650,7 +674,9 @@ template <int W> __device__ __forceinline__ void unit_counts(uint64_t (&s)[2 * W
 // One batch of up to 64*W sources through both sweeps, in the given scope.
 // Returns early (leaving the workspace dirty) when the job is in an error
 // state.  Warp counters accumulate into cnt (shared, lane 0) and dag (lane).
-template <typename DT, int W, bool SQ, typename Scope>
+// CT: storage type of the path counts (uint32_t with promotion of the job to
+// 64 bits on the first count that does not fit, or uint64_t).
+template <typename DT, int W, bool SQ, typename CT, typename Scope>
 __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int *stage,
                                            WarpCounters &cnt, unsigned long long &dag) {
   const int lane = threadIdx.x & 31;
@@ -800,7 +826,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           ob = __ldg(p.g.row_ptr + u);
           oe = __ldg(p.g.row_ptr + u + 1);
         }
-        push_counts<W>(p, u, load_mask<W>(Pm, u), ob, oe, A, lane, dag);
+        push_counts<W, CT>(p, u, load_mask<W>(Pm, u), ob, oe, A, lane, dag);
         if (lane == 0) cnt.out_e += (uint64_t)(oe - ob);
       }
       // level l's own items, numbered from 0
@@ -822,9 +848,10 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           // first chunk records the entry
           const int od = re - rs;
           const int a = (int)(c * od / nch), b = (int)((c + 1) * od / nch);
-          uint64_t s[2 * W] = {};
+          CT s[2 * W] = {};
           unsigned cb = 0;
-          fwd_scan<W>(p, lv, F, 0, 0, rs + a, rs + b, A, Pm, Bn, stage, nst, lane, s, cb, dag);
+          fwd_scan<W, CT>(p, lv, F, 0, 0, rs + a, rs + b, A, Pm, Bn, stage, nst, lane, s, cb,
+                          dag);
           if (lane == 0) {
             cnt.out_e += (uint64_t)(b - a);
             cnt.heavy++;
@@ -838,13 +865,13 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         }
         const int indeg = ie - is, tot = indeg + (re - rs);
         const int a = (int)(c * tot / nch), b = (int)((c + 1) * tot / nch);
-        uint64_t s[2 * W] = {};
+        CT s[2 * W] = {};
         unsigned cb = 0;
         const int ib = is + (a < indeg ? a : indeg), ie2 = is + (b < indeg ? b : indeg);
         const int obg = rs + (a > indeg ? a - indeg : 0);
         const int oen = rs + (b > indeg ? b - indeg : 0);
-        fwd_scan<W>(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage, nst,
-                    lane, s, cb, dag);
+        fwd_scan<W, CT>(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage,
+                        nst, lane, s, cb, dag);
         if (lane == 0) {
           cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
           cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
@@ -865,7 +892,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           uint64_t t[2 * W] = {};
           unsigned q = 0;
           if (l == 0) {
-            unit_counts<W>(t);
+            unit_counts<W, uint64_t>(t);
           } else {
             const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
             for (int64_t cc = c0; cc < c0 + nch; ++cc) {
@@ -878,7 +905,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
               }
             }
           }
-          batch_store_sigma_w<W>(p, w, F, t, q, lane);
+          if (sizeof(CT) == 4) {
+            // the chunks' sum must fit the 32-bit storage
+            bool big = false;
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) big |= F.has(i, lane) && (t[i] >> 32) != 0;
+            if (__any_sync(kFull, big)) set_err(ctl, KERR_WIDE);
+          }
+          batch_store_sigma_w<W, CT>(p, w, F, t, q, lane);
           if (lane == 0) {
             p.w.harrive[h] = 0;
             store_mask<W>(p.w.qm, e, F);
@@ -898,13 +932,13 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           const int is = (int)hd.field(FF::kIn0, i), ie = (int)hd.field(FF::kIn1, i);
           const int rs = (int)hd.field(FF::kOut0, i), re = (int)hd.field(FF::kOut1, i);
           const int w = (int)hd.field(FF::kId, i);
-          uint64_t s[2 * W] = {};
+          CT s[2 * W] = {};
           unsigned cb = 0;
           const bool pull = l > 0 && !push;
-          fwd_scan<W>(p, lv, F, pull ? is : 0, pull ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
-                      lane, s, cb, dag);
-          if (l == 0) unit_counts<W>(s);
-          if (!push) batch_store_sigma_w<W>(p, w, F, s, cb, lane);
+          fwd_scan<W, CT>(p, lv, F, pull ? is : 0, pull ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
+                          lane, s, cb, dag);
+          if (l == 0) unit_counts<W, CT>(s);
+          if (!push) batch_store_sigma_w<W, CT>(p, w, F, s, cb, lane);
           if (lane == 0) {
             store_mask<W>(p.w.qm, e0 + i, F);
             cnt.entries++;
@@ -1008,8 +1042,8 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           for (int64_t cc = c0; cc < c0 + nch; ++cc)
 #pragma unroll
             for (int i = 0; i < 2 * W; ++i) t[i] += ldcg(pp + (size_t)cc * kRow + 32 * i + lane);
-          const EntryOwn<W> own(p, v, F, lane);
-          batch_finish<DT, W, SQ>(p, l, v, F, t, own.sg, own.bcv, Wn, lane);
+          const EntryOwn<W, CT> own(p, v, F, lane);
+          batch_finish<DT, W, SQ, CT>(p, l, v, F, t, own.sg, own.bcv, Wn, lane);
           if (lane == 0) p.w.harrive[h] = 0;
         }
       }
@@ -1026,14 +1060,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           DT acc[2 * W] = {};
           if constexpr (W <= BC_OWN_EARLY_MAX_W) {
             // own counts loaded ahead of the successor scan (overlapping it)
-            const EntryOwn<W> own(p, v, F, lane);
+            const EntryOwn<W, CT> own(p, v, F, lane);
             if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
-            batch_finish<DT, W, SQ>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+            batch_finish<DT, W, SQ, CT>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           } else {
             // widest masks: loaded after it, which keeps 4W registers free
             if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
-            const EntryOwn<W> own(p, v, F, lane);
-            batch_finish<DT, W, SQ>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+            const EntryOwn<W, CT> own(p, v, F, lane);
+            batch_finish<DT, W, SQ, CT>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           }
           if (!deepest && lane == 0) cnt.out_e += (uint64_t)(re - rs);
         }
@@ -1060,7 +1094,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
   }
 }
 
-template <typename DT, int W, bool SQ>
+template <typename DT, int W, bool SQ, typename CT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KParams p) {
   __shared__ int s_stage[kWarpsPerBlock][kStage]; // warp-private new-vertex stage
   __shared__ WarpCounters s_cnt[kWarpsPerBlock];
@@ -1068,7 +1102,7 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
   WarpCounters &cnt = s_cnt[threadIdx.x >> 5];
   zero_counters(cnt, lane);
   unsigned long long dag = 0;
-  batch_body<DT, W, SQ>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+  batch_body<DT, W, SQ, CT>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt, dag);
   __syncwarp();
   flush_counters(p.job_cnt, to_counters(cnt, dag, lane), lane);
 }
@@ -1125,11 +1159,11 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
       p.k = p.g.n - b0 < kb ? p.g.n - b0 : kb;
       p.src_base = off + b0;
       if (words == 4)
-        batch_body<DT, 4, false>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+        batch_body<DT, 4, false, uint64_t>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       else if (words == 2)
-        batch_body<DT, 2, false>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+        batch_body<DT, 2, false, uint64_t>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       else
-        batch_body<DT, 1, false>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+        batch_body<DT, 1, false, uint64_t>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
       __syncthreads();
       const int e = read_err(p.w.ctl);
       if ((e == KERR_QUEUE || e == KERR_HEAVY) && words > 1) {
@@ -1457,10 +1491,31 @@ __global__ void __launch_bounds__(kBlock) plain_kernel(const KParams p) {
 
 // One source in one thread block: the small-graph form of the one-source
 // launch; the host issues such launches on several streams at once, each
-// stream adding into its own BC partial vector.
+// stream adding into its own BC partial vector.  The launch carries only the
+// stream slot's parameters (in device memory) and the source's position b
+// in the job, which keeps the host's cost per launch low: on small graphs
+// the rate of launches bounds this schedule.
 template <typename DT>
-__global__ void __launch_bounds__(kBlock) plain_block_kernel(const KParams p) {
-  plain_body<DT>(p, CtaScope());
+__global__ void __launch_bounds__(kBlock) plain_block_kernel(const KParams *__restrict__ slots,
+                                                             int slot, int64_t b) {
+  __shared__ KParams sp;
+  constexpr int kWords = (int)(sizeof(KParams) / sizeof(unsigned long long));
+  static_assert(sizeof(KParams) % sizeof(unsigned long long) == 0, "copied in 8-byte words");
+  const unsigned long long *from = reinterpret_cast<const unsigned long long *>(slots + slot);
+  unsigned long long *to = reinterpret_cast<unsigned long long *>(&sp);
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x) to[i] = from[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sp.src += b;
+    sp.src_base = b;
+    if (sp.dbg_d) {
+      sp.dbg_d += b * sp.g.n;
+      sp.dbg_sigma += b * sp.g.n;
+      sp.dbg_delta += b * sp.g.n;
+    }
+  }
+  __syncthreads();
+  plain_body<DT>(sp, CtaScope());
 }
 
 // out[v] = sum over parts of parts[part][v], parts in order (deterministic).
@@ -1569,18 +1624,18 @@ template <typename K> cudaError_t coop_launch(K kernel, const KParams &p, int gr
                                      dim3(kBlock), args, 0, st);
 }
 
-template <bool SQ>
+template <bool SQ, typename CT>
 cudaError_t launch_batch_sq(const KParams &p, bool fp64, int grid, cudaStream_t st, int words) {
   switch (words) {
     case 1:
-      return fp64 ? coop_launch(batch_kernel<double, 1, SQ>, p, grid, st)
-                  : coop_launch(batch_kernel<float, 1, SQ>, p, grid, st);
+      return fp64 ? coop_launch(batch_kernel<double, 1, SQ, CT>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 1, SQ, CT>, p, grid, st);
     case 2:
-      return fp64 ? coop_launch(batch_kernel<double, 2, SQ>, p, grid, st)
-                  : coop_launch(batch_kernel<float, 2, SQ>, p, grid, st);
+      return fp64 ? coop_launch(batch_kernel<double, 2, SQ, CT>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 2, SQ, CT>, p, grid, st);
     case 4:
-      return fp64 ? coop_launch(batch_kernel<double, 4, SQ>, p, grid, st)
-                  : coop_launch(batch_kernel<float, 4, SQ>, p, grid, st);
+      return fp64 ? coop_launch(batch_kernel<double, 4, SQ, CT>, p, grid, st)
+                  : coop_launch(batch_kernel<float, 4, SQ, CT>, p, grid, st);
     default:
       return cudaErrorInvalidValue;
   }
@@ -1590,9 +1645,12 @@ cudaError_t launch_batch_sq(const KParams &p, bool fp64, int grid, cudaStream_t 
 
 // The squared-term accumulation of the estimator is a separate
 // instantiation, so plain BC jobs carry none of its code.
-cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words) {
-  return p.bc2 ? launch_batch_sq<true>(p, fp64, grid, st, words)
-               : launch_batch_sq<false>(p, fp64, grid, st, words);
+// Estimator jobs keep 64-bit counts.
+cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words,
+                         bool counts32) {
+  if (p.bc2) return launch_batch_sq<true, uint64_t>(p, fp64, grid, st, words);
+  return counts32 ? launch_batch_sq<false, uint32_t>(p, fp64, grid, st, words)
+                  : launch_batch_sq<false, uint64_t>(p, fp64, grid, st, words);
 }
 
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st) {
@@ -1600,9 +1658,10 @@ cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st)
               : coop_launch(plain_kernel<float>, p, grid, st);
 }
 
-cudaError_t launch_plain_block(const KParams &p, bool fp64, cudaStream_t st) {
-  if (fp64) plain_block_kernel<double><<<1, kBlock, 0, st>>>(p);
-  else plain_block_kernel<float><<<1, kBlock, 0, st>>>(p);
+cudaError_t launch_plain_block(const KParams *slots, int slot, int64_t b, bool fp64,
+                               cudaStream_t st) {
+  if (fp64) plain_block_kernel<double><<<1, kBlock, 0, st>>>(slots, slot, b);
+  else plain_block_kernel<float><<<1, kBlock, 0, st>>>(slots, slot, b);
   return cudaGetLastError();
 }
 
@@ -1670,14 +1729,14 @@ int max_grid_many(bool fp64, int device) {
 int max_grid_batch(bool fp64, int device, int words) {
   switch (words) {
     case 1:
-      return fp64 ? max_grid_for(batch_kernel<double, 1, false>, device)
-                  : max_grid_for(batch_kernel<float, 1, false>, device);
+      return fp64 ? max_grid_for(batch_kernel<double, 1, false, uint64_t>, device)
+                  : max_grid_for(batch_kernel<float, 1, false, uint64_t>, device);
     case 2:
-      return fp64 ? max_grid_for(batch_kernel<double, 2, false>, device)
-                  : max_grid_for(batch_kernel<float, 2, false>, device);
+      return fp64 ? max_grid_for(batch_kernel<double, 2, false, uint64_t>, device)
+                  : max_grid_for(batch_kernel<float, 2, false, uint64_t>, device);
     case 4:
-      return fp64 ? max_grid_for(batch_kernel<double, 4, false>, device)
-                  : max_grid_for(batch_kernel<float, 4, false>, device);
+      return fp64 ? max_grid_for(batch_kernel<double, 4, false, uint64_t>, device)
+                  : max_grid_for(batch_kernel<float, 4, false, uint64_t>, device);
     default:
       return 0;
   }

@@ -624,6 +624,71 @@ def test_plain_block_and_grid_forms_agree(ctx):
         assert ctx.last_stats()["kernel_kind"] == 1 and ctx.last_stats()["batches"] == len(srcs)
     one = sum(ctx.sources(G, [int(s_)], schedule="plain", delta_fp64=True).copy() for s_ in srcs)
     assert_bc_close(one, ref, True)
+    # the captured launches are replayed for later jobs of the same size: other
+    # sources, another graph, the same graph again
+    g2 = bcgen.rmat(10, 8, seed=7)
+    G2 = ctx.create_graph(g2.row_ptr, g2.col_idx)
+    for gg, GG, seed in ((g, G, 5), (g2, G2, 6), (g, G, 2)):
+        ss = bcgen.sample_sources(gg.n, 40, seed=seed)
+        rr, _ = oracle.bc(gg.n, gg.row_ptr, gg.col_idx, ss)
+        assert_bc_close(ctx.sources(GG, ss, schedule="plain", delta_fp64=True), rr, True)
+    ctx.destroy_graph(G2)
     full, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
     assert_bc_close(ctx.exact(G, schedule="plain", delta_fp64=True), full, True)
     ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("direction", ["pull", "push"])
+def test_32_bit_count_rows_match_64_bit(ctx, direction):
+    """Path counts stored in 32 bits (the default) give the same depths,
+    counts and BC bits as 64-bit storage, pulled or pushed, at every batch
+    width; both match the oracle."""
+    for g in (bcgen.rmat(11, 16, seed=5), bcgen.ba_directed(2500, 8, 9, seed=3), hub_graph()):
+        G = ctx.create_graph(g.row_ptr, g.col_idx)
+        ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+        for kb in (64, 128, 256):
+            for fp64 in (False, True):
+                # one fixed work split, so both runs add in the same order
+                a = ctx.exact(G, batch_k=kb, delta_fp64=fp64, direction=direction,
+                              count_bits=32, schedule="batch_warp").copy()
+                b = ctx.exact(G, batch_k=kb, delta_fp64=fp64, direction=direction,
+                              count_bits=64, schedule="batch_warp").copy()
+                assert_bc_close(a, ref, fp64)
+                assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), (kb, fp64)
+        srcs = [0, 3, g.n - 1]
+        d, sig, _ = ctx.debug_sources(G, srcs, delta_fp64=True, direction=direction)
+        for j, s_ in enumerate(srcs):
+            od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, s_)
+            np.testing.assert_array_equal(d[j], od)
+            np.testing.assert_array_equal(sig[j], osig)
+        ctx.destroy_graph(G)
+
+
+@pytest.mark.parametrize("direction", ["pull", "push"])
+def test_counts_beyond_32_bits_promote_the_job(direction):
+    """A count of 2^32 or more does not fit the 32-bit rows: the job reruns
+    with 64-bit counts (and later jobs on the graph keep them); results and
+    counts stay exact, and 2^64 still overflows as the oracle says."""
+    import paper_1409_7764_gb300 as bc
+    with bc.Context(0) as fresh:
+        g = bcgen.layered_chain(40, 3)  # 3^40 (about 1.2e19) paths: beyond 32 bits, within 64
+        G = fresh.create_graph(g.row_ptr, g.col_idx)
+        ref, ovf = oracle.bc(g.n, g.row_ptr, g.col_idx)
+        assert not ovf.any()
+        assert_bc_close(fresh.exact(G, delta_fp64=True, direction=direction), ref, True)
+        assert_bc_close(fresh.exact(G, delta_fp64=False, direction=direction), ref, False)
+        d, sig, _ = fresh.debug_sources(G, [0, 1], delta_fp64=True, direction=direction)
+        for j, s_ in enumerate([0, 1]):
+            od, osig, _, _ = oracle.single_source(g.n, g.row_ptr, g.col_idx, s_)
+            np.testing.assert_array_equal(d[j], od)
+            np.testing.assert_array_equal(sig[j], osig)
+        assert int(sig[0].max()) > 2 ** 32
+        fresh.destroy_graph(G)
+        bad = bcgen.layered_chain(41, 3)  # 3^41 > 2^64: overflow, flagged like the oracle
+        G = fresh.create_graph(bad.row_ptr, bad.col_idx)
+        with pytest.raises(bc.BCError) as ei:
+            fresh.sources(G, [0, 2], direction=direction)
+        assert ei.value.status == bc.BC_ERR_SIGMA_OVERFLOW
+        _, ovf = oracle.bc(bad.n, bad.row_ptr, bad.col_idx, [0, 2])
+        assert ei.value.stats["overflow_sources"] == int(np.count_nonzero(ovf))
+        fresh.destroy_graph(G)
