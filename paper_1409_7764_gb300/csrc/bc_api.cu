@@ -176,6 +176,7 @@ constexpr bool grabs_fit() {
 static_assert(grabs_fit(), "a fetch larger than the kernels' header rounds hold");
 constexpr int kNumTune = 5;
 constexpr int kTuneRounds = 2; // trial batches per candidate
+constexpr double kTuneMargin = 1.05; // throughput a split must beat the default by
 // Batch widths (mask words) the width trial compares, widest first.
 constexpr int kWidthTrial[3] = {4, 2, 1};
 
@@ -1342,34 +1343,68 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
   j->words = words;
   j->kb = kb;
   // ---- work-split trial ----
+  // Candidates are compared by throughput, not time: the trial batches take
+  // consecutive sources of the grouped order, whose work per batch varies
+  // several-fold (and drops to nothing for sources without out-edges), so
+  // each batch's time is set against the bytes its own counters say it
+  // moved (the design's bytes model, from counter snapshots taken between
+  // the trial batches).
   std::atomic<int> &tuned_slot = j->g->tuned[word_index(words)];
   int cand = fixed >= 0 ? split_cand : std::max(tuned_slot.load(), 0);
   if (kind != WS_QUEUE) cand = 0;
   const int64_t left = (k - b0 + kb - 1) / kb;
   if (!notune && fixed < 0 && tuned_slot.load() < 0 && left >= kNumTune * kTuneRounds + 4) {
+    constexpr int kTrials = kNumTune * kTuneRounds;
+    unsigned long long *d_snap = nullptr;
+    BC_TRY(pool_alloc(ctx, &d_snap, sizeof(unsigned long long) * CNT_N * (kTrials + 1), st));
+    auto snap = [&](int t) {
+      return cudaMemcpyAsync(d_snap + (size_t)t * CNT_N, j->d_cnt,
+                             sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToDevice, st);
+    };
     std::vector<cudaEvent_t> ev;
     std::vector<int> slot_of;
-    std::vector<int64_t> srcs;
-    for (int t = 0; t < kNumTune * kTuneRounds; ++t) {
-      // rounds alternate direction (c0 c1 .. c4 c4 .. c0), so a trend in
-      // batch cost along the source order weighs every candidate alike
+    std::vector<int64_t> ones;
+    bc_status s = BC_OK;
+    if (snap(0) != cudaSuccess) s = BC_ERR_CUDA;
+    for (int t = 0; t < kTrials && s == BC_OK; ++t) {
+      // rounds alternate direction (c0 c1 .. c4 c4 .. c0)
       const int r = t / kNumTune, c = t % kNumTune;
       const int cc = r % 2 == 0 ? c : kNumTune - 1 - c;
-      bc_status s = record(ev);
-      if (s != BC_OK) return s;
-      slot_of.push_back(cc);
-      srcs.push_back(std::min<int64_t>(kb, k - b0));
-      s = launch(kb, words, cc);
-      if (s != BC_OK) return s;
+      s = record(ev);
+      if (s == BC_OK) s = launch(kb, words, cc);
+      if (s == BC_OK && snap(t + 1) != cudaSuccess) s = BC_ERR_CUDA;
+      slot_of.push_back(t); // one slot per trial batch
+      ones.push_back(1);
     }
-    bc_status s = record(ev);
+    if (s == BC_OK) s = record(ev);
+    std::vector<double> ms((size_t)kTrials, 0.0);
+    if (s == BC_OK) s = trial_times(ev, slot_of, ones, ms);
+    std::vector<unsigned long long> h((size_t)CNT_N * (kTrials + 1), 0);
+    if (s == BC_OK &&
+        (cudaMemcpyAsync(h.data(), d_snap, sizeof(unsigned long long) * h.size(),
+                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+      s = BC_ERR_CUDA;
+    cudaFreeAsync(d_snap, st);
     if (s != BC_OK) return s;
-    std::vector<double> per((size_t)kNumTune, 0.0);
-    s = trial_times(ev, slot_of, srcs, per);
-    if (s != BC_OK) return s;
+    const double b = j->opts.delta_fp64 ? 8.0 : 4.0, cb = c32 ? 4.0 : 8.0;
+    std::vector<double> bytes((size_t)kNumTune, 0.0), time((size_t)kNumTune, 0.0);
+    for (int t = 0; t < kTrials; ++t) {
+      auto d = [&](int c) { return (double)(h[(size_t)(t + 1) * CNT_N + c] - h[(size_t)t * CNT_N + c]); };
+      const double moved = 124.0 * d(CNT_ENTRIES) + (4.0 + 8.0 * words) *
+                           (d(CNT_IN_EDGES) + d(CNT_OUT_EDGES)) + (cb + b) * d(CNT_DAG) +
+                           (3.0 * cb + b) * d(CNT_REACHED);
+      const int r = t / kNumTune, c = t % kNumTune;
+      const int cc = r % 2 == 0 ? c : kNumTune - 1 - c;
+      bytes[(size_t)cc] += moved;
+      time[(size_t)cc] += ms[(size_t)t];
+    }
+    // the default split stays unless another is clearly faster: the trial
+    // batches differ in content, so small differences are noise
     int best = 0;
+    auto rate = [&](int c) { return time[(size_t)c] > 0.0 ? bytes[(size_t)c] / time[(size_t)c] : 0.0; };
     for (int c = 1; c < kNumTune; ++c)
-      if (per[(size_t)c] < per[(size_t)best]) best = c;
+      if (rate(c) > rate(best) && rate(c) > kTuneMargin * rate(0)) best = c;
     tuned_slot = best;
     cand = best;
   }

@@ -261,9 +261,57 @@ template <int W> struct GatherUnroll {
 
 // Edges per round of the dependency-coefficient gather: as many as keep 8
 // 8-byte (16 4-byte) values per lane in flight.
+#ifndef BC_NARROW_UNROLL
+#define BC_NARROW_UNROLL 2 // edges in flight of 4-byte gathers, relative to 8-byte ones
+#endif
 template <int W, typename DT> struct CoeffUnroll {
-  static constexpr int value =
-      (BC_GATHER_FORM >= 1 && sizeof(DT) == 4) ? 2 * GatherUnroll<W>::value : GatherUnroll<W>::value;
+  static constexpr int value = (BC_GATHER_FORM >= 1 && sizeof(DT) == 4)
+                                   ? BC_NARROW_UNROLL * GatherUnroll<W>::value
+                                   : GatherUnroll<W>::value;
+};
+
+#ifndef BC_MASK_STAGE
+#define BC_MASK_STAGE 1 // 1: a round's edge masks reach the lanes through shared memory
+#endif
+
+// Per-warp staging of the 32 edge masks of a gather round ([warp][lane][word]):
+// the lane that loaded an edge's mask stores it once, and every lane reads
+// the words of each edge it gathers with one broadcast shared-memory load
+// per 16 bytes instead of two shuffles per 64-bit word.
+__shared__ uint64_t g_mask_stage[kWarpsPerBlock][kWarp][kMaxWords];
+
+template <int W> struct RoundMasks {
+  const uint64_t *stg;
+  __device__ __forceinline__ RoundMasks(const Mask<W> &P, int lane) {
+    uint64_t *row = &g_mask_stage[threadIdx.x >> 5][0][0];
+    stg = row;
+    __syncwarp();
+    if constexpr (W == 1) {
+      row[lane * kMaxWords] = P.w[0];
+    } else {
+#pragma unroll
+      for (int i = 0; i < W; i += 2)
+        *reinterpret_cast<ulonglong2 *>(row + lane * kMaxWords + i) = make_ulonglong2(P.w[i], P.w[i + 1]);
+    }
+    __syncwarp();
+  }
+  // the mask of the edge held by lane src (all zero for src < 0)
+  __device__ __forceinline__ Mask<W> of(int src) const {
+    Mask<W> m;
+    if (src < 0) return Mask<W>::zero();
+    const uint64_t *e = stg + src * kMaxWords;
+    if constexpr (W == 1) {
+      m.w[0] = e[0];
+    } else {
+#pragma unroll
+      for (int i = 0; i < W; i += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(e + i);
+        m.w[i] = t.x;
+        m.w[i + 1] = t.y;
+      }
+    }
+    return m;
+  }
 };
 
 // s += x, with the carry out of the top bit added to c (c counts carries).
@@ -277,7 +325,8 @@ __device__ __forceinline__ void add_count_carry(uint32_t &s, uint32_t x, unsigne
 // Edges per round of the path-count gather: 4-byte counts (the 32-bit
 // storage form) keep twice as many edges in flight in the same registers.
 template <int W, typename CT> struct CountUnroll {
-  static constexpr int value = sizeof(CT) == 4 ? 2 * GatherUnroll<W>::value : GatherUnroll<W>::value;
+  static constexpr int value =
+      sizeof(CT) == 4 ? BC_NARROW_UNROLL * GatherUnroll<W>::value : GatherUnroll<W>::value;
 };
 
 // Path counts over the round's shortest-path edges (lanes whose mask P is not
@@ -293,6 +342,10 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
   constexpr int U = CountUnroll<W, CT>::value;
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, P.any());
+  if (!bal) return;
+#if BC_MASK_STAGE
+  const RoundMasks<W> rm(P, lane);
+#endif
   while (bal) {
     const LanesU<U> q(bal);
     CT x[U][2 * W];
@@ -300,9 +353,16 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
     for (int i = 0; i < U; ++i) {
       const int uu = shfl_or_zero(u, q.l[i]);
       const CT *row = base + (size_t)uu * (kK * W) + lane;
+#if BC_MASK_STAGE
+      const Mask<W> PE = rm.of(q.l[i]);
+#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
+#if BC_MASK_STAGE
+        const uint64_t PP = PE.w[wi];
+#else
         const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
+#endif
         const unsigned lo = (unsigned)PP, hi = (unsigned)(PP >> 32);
         x[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : CT(0);
         x[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : CT(0);
@@ -330,6 +390,10 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
   constexpr int U = CoeffUnroll<W, DT>::value;
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, S.any());
+  if (!bal) return;
+#if BC_MASK_STAGE
+  const RoundMasks<W> rm(S, lane);
+#endif
   while (bal) {
     const LanesU<U> q(bal);
     DT y[U][2 * W];
@@ -337,9 +401,16 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
     for (int i = 0; i < U; ++i) {
       const int xx = shfl_or_zero(x, q.l[i]);
       const DT *row = base + (size_t)xx * (kK * W) + lane;
+#if BC_MASK_STAGE
+      const Mask<W> SE = rm.of(q.l[i]);
+#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
+#if BC_MASK_STAGE
+        const uint64_t SS = SE.w[wi];
+#else
         const uint64_t SS = shfl_or_zero(S.w[wi], q.l[i]);
+#endif
         const unsigned lo = (unsigned)SS, hi = (unsigned)(SS >> 32);
         y[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : DT(0);
         y[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : DT(0);
