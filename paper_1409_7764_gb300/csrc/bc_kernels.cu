@@ -280,14 +280,17 @@ __device__ __forceinline__ void push_counts(const KParams &p, int u, const Mask<
     }
     dag += P.popc(); // per lane; the warp's counters are summed at the flush
     unsigned bal = __ballot_sync(kFull, P.any());
+    if (!bal) continue;
+    const RoundMasks<W> rm(P, lane);
     while (bal) {
       const int src = __ffs(bal) - 1;
       bal &= bal - 1;
       const int xx = __shfl_sync(kFull, x, src);
       CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)xx * (kK * W) + lane;
+      const Mask<W> PE = rm.of(src);
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
-        const uint64_t PP = __shfl_sync(kFull, P.w[wi], src);
+        const uint64_t PP = PE.w[wi];
         if ((unsigned)PP & mybit) push_add(row + 64 * wi, own[2 * wi], wrap);
         if ((unsigned)(PP >> 32) & mybit) push_add(row + 64 * wi + 32, own[2 * wi + 1], wrap);
       }
