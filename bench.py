@@ -517,7 +517,8 @@ def run_ours(args, w, name):
                                             "scanned_out_edges", "dag_pairs", "reached_pairs",
                                             "heavy_chunks", "max_levels", "levels_sum",
                                             "batches", "kernel_kind", "chunk_edges", "grab",
-                                            "batch_sources", "mask_words", "push_levels")},
+                                            "batch_sources", "mask_words", "push_levels",
+                                            "batch_groups")},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -138,6 +138,7 @@ typedef struct {
   int32_t batch_sources;     /* sources per batch in the last launch */
   int32_t mask_words;        /* 64-bit words per source mask in the last launch (1, 2 or 4) */
   int32_t push_levels;       /* forward levels whose path counts were pushed, over all batches */
+  int32_t batch_groups;      /* batches the last launches ran at once (concurrent groups) */
 } bc_stats;
 
 /* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t

@@ -60,7 +60,7 @@ class bc_stats(ctypes.Structure):
                 ("levels_sum", ctypes.c_int32),
                 ("chunk_edges", ctypes.c_int32), ("grab", ctypes.c_int32),
                 ("batch_sources", ctypes.c_int32), ("mask_words", ctypes.c_int32),
-                ("push_levels", ctypes.c_int32)]
+                ("push_levels", ctypes.c_int32), ("batch_groups", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -81,6 +81,8 @@ struct GraphRec {
   std::atomic<int> tuned[3] = {-1, -1, -1};
   // mask words the width trial found fastest per source (0: not tried yet)
   std::atomic<int> tuned_words{0};
+  // concurrent batch groups the groups trial found fastest, per width (0: not tried yet)
+  std::atomic<int> tuned_groups[3] = {0, 0, 0};
   // a batch wider than 64 sources overran its frontier queue or heavy list
   // (sized for 64 distinct depths per vertex): later jobs use 64 sources
   std::atomic<bool> narrow{false};
@@ -243,7 +245,7 @@ WsNeed ws_need(const GraphDev &g, int kind, int kb, int words, int slots = 1) {
   WsNeed nd;
   nd.kind = kind;
   nd.words = kind == WS_QUEUE ? words : 1;
-  nd.slots = kind == WS_PLAIN ? slots : 1;
+  nd.slots = slots;
   nd.n = g.n;
   // a vertex is queued at most once per distinct depth among the batch's
   // sources; wider batches are sized for 64 depths (overruns are detected)
@@ -486,6 +488,10 @@ struct JobRec {
   int words = 1;             // mask words of the last launch
   int cand = 0;              // tuning candidate of the last launch
   int ws_slots = 0;          // one-block plain form: streams (entries of h_slots)
+  int groups = 1;            // concurrent batch groups the job's workspace holds
+  int groups_used = 1;       // concurrent batch groups of the job's last batches
+  Work *h_works = nullptr;   // grouped batches: pinned staging of the groups' workspaces
+  int works_n = 0;           // entries of h_works
   size_t footprint = 0;
   bc_status status = BC_PENDING;
   bc_stats stats{};
@@ -1071,12 +1077,44 @@ int plain_slots(const GraphDev &g, int64_t k) {
   return (int)std::min<int64_t>(kPlainStreams, k);
 }
 
+// Concurrent batch groups of a batched job (MultiParams): the job's batches
+// after its trials run G at a time, each group on 1/G of the SMs.  G is
+// tried per graph and width (kGroupTrial); BC_GROUPS fixes it for
+// experiments.  A job's workspace holds one copy per group it may use.
+constexpr int kGroupTrial[3] = {1, 2, 4};
+constexpr int kNumGroupTrial = 3;
+int forced_groups() {
+  if (const char *env = std::getenv("BC_GROUPS")) return std::max(1, std::min(std::atoi(env), 8));
+  return 0;
+}
+int batch_groups(const GraphRec &gr, int words, int64_t k, int kb) {
+  int want = forced_groups();
+  if (!want) {
+    const int t = gr.tuned_groups[word_index(words)].load();
+    want = t > 0 ? t : kGroupTrial[kNumGroupTrial - 1];
+  }
+  // at least two batches per group
+  while (want > 1 && k < (int64_t)2 * want * kb) want /= 2;
+  return want;
+}
+
+// Bytes a stretch of batches moved by this design's model, from the job
+// counters before (c0) and after (c1) it.
+double moved_bytes(const unsigned long long *c0, const unsigned long long *c1, int words, bool fp64,
+                   bool c32) {
+  auto d = [&](int c) { return (double)(c1[c] - c0[c]); };
+  const double b = fp64 ? 8.0 : 4.0, cb = c32 ? 4.0 : 8.0;
+  return 124.0 * d(CNT_ENTRIES) + (4.0 + 8.0 * words) * (d(CNT_IN_EDGES) + d(CNT_OUT_EDGES)) +
+         (cb + b) * d(CNT_DAG) + (3.0 * cb + b) * d(CNT_REACHED);
+}
+
 size_t job_footprint(const GraphRec &gr, int sched, const bc_opts &o, int64_t k) {
   const GraphDev &g = gr.dev;
   WsRec r;
   const int kind = sched == BC_SCHED_PLAIN ? WS_PLAIN : WS_QUEUE;
   const BatchShape bs = batch_shape(o, kind, k, gr.narrow, false);
-  WsNeed nd = ws_need(g, kind, bs.kb, bs.words, plain_slots(g, k));
+  WsNeed nd = ws_need(g, kind, bs.kb, bs.words,
+                      kind == WS_PLAIN ? plain_slots(g, k) : batch_groups(gr, bs.words, k, bs.kb));
   r.kind = nd.kind;
   r.words = nd.words;
   r.slots = nd.slots;
@@ -1097,6 +1135,8 @@ void job_free_buffers(bc_ctx *ctx, JobRec *j) {
   if (j->d_cnt) cudaFreeAsync(j->d_cnt, j->st);
   if (j->h_slots) pin_put(ctx, j->h_slots, sizeof(KParams) * (size_t)std::max(j->ws_slots, 1));
   j->h_slots = nullptr;
+  if (j->h_works) pin_put(ctx, j->h_works, sizeof(Work) * (size_t)std::max(j->works_n, 1));
+  j->h_works = nullptr;
   j->d_src = nullptr;
   j->d_bc = nullptr;
   j->d_ovf = nullptr;
@@ -1267,8 +1307,9 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
       r.words = words;
       ws_layout(r, static_cast<char *>(ws->mem));
       p.w = r.w;
-      BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->bytes - ctl_bytes,
-                             st));
+      // trials run in the first copy only (the others stay clean)
+      BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0,
+                             ws->slot_bytes - ctl_bytes, st));
       cur_words = words;
     }
     p.g.nchunks = j->g->nch_variant[kTuneCandidates[cand].variant];
@@ -1387,16 +1428,12 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
       s = BC_ERR_CUDA;
     cudaFreeAsync(d_snap, st);
     if (s != BC_OK) return s;
-    const double b = j->opts.delta_fp64 ? 8.0 : 4.0, cb = c32 ? 4.0 : 8.0;
     std::vector<double> bytes((size_t)kNumTune, 0.0), time((size_t)kNumTune, 0.0);
     for (int t = 0; t < kTrials; ++t) {
-      auto d = [&](int c) { return (double)(h[(size_t)(t + 1) * CNT_N + c] - h[(size_t)t * CNT_N + c]); };
-      const double moved = 124.0 * d(CNT_ENTRIES) + (4.0 + 8.0 * words) *
-                           (d(CNT_IN_EDGES) + d(CNT_OUT_EDGES)) + (cb + b) * d(CNT_DAG) +
-                           (3.0 * cb + b) * d(CNT_REACHED);
       const int r = t / kNumTune, c = t % kNumTune;
       const int cc = r % 2 == 0 ? c : kNumTune - 1 - c;
-      bytes[(size_t)cc] += moved;
+      bytes[(size_t)cc] += moved_bytes(h.data() + (size_t)t * CNT_N, h.data() + (size_t)(t + 1) * CNT_N,
+                                       words, j->opts.delta_fp64 != 0, c32);
       time[(size_t)cc] += ms[(size_t)t];
     }
     // the default split stays unless another is clearly faster: the trial
@@ -1408,13 +1445,110 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
     tuned_slot = best;
     cand = best;
   }
-  // ---- the rest of the job ----
-  while (b0 < k) {
-    const bc_status s = launch(kb, words, cand);
+  // ---- concurrent batch groups ----
+  // Sources [b0, end) in groups of G concurrent batches (G = 1: one launch
+  // per batch).  G > 1 runs one launch, group g on its own slot workspace
+  // and BC partial vector, the partials added to the job's BC in group order.
+  const bool groups_ok = kind == WS_QUEUE && !dbg && cur_words == ws->words && words == ws->words;
+  auto run_range = [&](int G, int64_t end) -> bc_status {
+    const int gsize = G > 1 ? ctx->grid_batch[word_index(words)][fp64] / G : 0;
+    if (G <= 1 || gsize < 1 || !groups_ok || G > ws->slots) {
+      if (b0 < end) j->groups_used = 1;
+      while (b0 < end) {
+        const bc_status s = launch(kb, words, cand);
+        if (s != BC_OK) return s;
+      }
+      return BC_OK;
+    }
+    if (!j->h_works) {
+      BC_TRY(pin_get(ctx, &j->h_works, sizeof(Work) * (size_t)ws->slots));
+      j->works_n = ws->slots;
+      for (int i = 0; i < ws->slots; ++i) j->h_works[i] = slot_work(*ws, i);
+      // room for `slots` entries where the one-block plain form keeps its parameters
+      BC_TRY(cudaMemcpyAsync(ws->slot_params, j->h_works, sizeof(Work) * (size_t)ws->slots,
+                             cudaMemcpyHostToDevice, st));
+    }
+    BC_TRY(cudaMemsetAsync(ws->parts, 0, sizeof(double) * (size_t)n * (size_t)G, st));
+    MultiParams mp;
+    mp.base = p;
+    mp.base.g.nchunks = j->g->nch_variant[kTuneCandidates[cand].variant];
+    mp.base.grab = kTuneCandidates[cand].grab;
+    mp.base.src = j->d_src;
+    mp.base.dbg_d = nullptr;
+    mp.works = reinterpret_cast<const Work *>(ws->slot_params);
+    mp.parts = ws->parts;
+    mp.groups = G;
+    mp.gsize = gsize;
+    mp.kb = kb;
+    mp.k = end;
+    mp.first = b0;
+    BC_TRY(launch_multi(mp, fp64, words, c32, st));
+    j->groups_used = G;
+    BC_TRY(launch_sum_parts(ws->parts, G, n, j->d_bc, st, true));
+    BC_TRY(launch_gather_err(ws->w.ctl, ws->slot_bytes, G, st));
+    j->batches += (end - b0 + kb - 1) / kb;
+    j->launches += 3;
+    j->cand = cand;
+    b0 = end;
+    return BC_OK;
+  };
+  const int forced = forced_groups();
+  std::atomic<int> &tuned_g = j->g->tuned_groups[word_index(words)];
+  int G = forced ? forced : std::max(1, tuned_g.load());
+  // the groups trial: 2G batches with each G of kGroupTrial, compared by
+  // throughput like the split trial; the fastest is kept per graph and
+  // width (one group unless another is more than kTuneMargin faster)
+  int64_t need = 0;
+  for (int g : kGroupTrial) need += 2 * (int64_t)g * kb;
+  if (!notune && !forced && tuned_g.load() < 1 && groups_ok &&
+      ws->slots >= kGroupTrial[kNumGroupTrial - 1] && k - b0 >= need) {
+    unsigned long long *d_snap = nullptr;
+    BC_TRY(pool_alloc(ctx, &d_snap, sizeof(unsigned long long) * CNT_N * (kNumGroupTrial + 1), st));
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> slot_of;
+    std::vector<int64_t> ones;
+    bc_status s = BC_OK;
+    for (int t = 0; t <= kNumGroupTrial && s == BC_OK; ++t) {
+      if (cudaMemcpyAsync(d_snap + (size_t)t * CNT_N, j->d_cnt, sizeof(unsigned long long) * CNT_N,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        s = BC_ERR_CUDA;
+      if (s == BC_OK) s = record(ev);
+      if (s == BC_OK && t < kNumGroupTrial) {
+        slot_of.push_back(t);
+        ones.push_back(1);
+        s = run_range(kGroupTrial[t], std::min<int64_t>(k, b0 + 2 * (int64_t)kGroupTrial[t] * kb));
+      }
+    }
+    std::vector<double> ms((size_t)kNumGroupTrial, 0.0);
+    if (s == BC_OK) s = trial_times(ev, slot_of, ones, ms);
+    std::vector<unsigned long long> h((size_t)CNT_N * (kNumGroupTrial + 1), 0);
+    if (s == BC_OK &&
+        (cudaMemcpyAsync(h.data(), d_snap, sizeof(unsigned long long) * h.size(),
+                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+      s = BC_ERR_CUDA;
+    cudaFreeAsync(d_snap, st);
+    if (s != BC_OK) return s;
+    std::vector<double> rate((size_t)kNumGroupTrial, 0.0);
+    for (int t = 0; t < kNumGroupTrial; ++t)
+      rate[(size_t)t] = ms[(size_t)t] > 0.0 ? moved_bytes(h.data() + (size_t)t * CNT_N,
+                                                         h.data() + (size_t)(t + 1) * CNT_N,
+                                                         words, j->opts.delta_fp64 != 0, c32) /
+                                                  ms[(size_t)t]
+                                            : 0.0;
+    int best = 0;
+    for (int t = 1; t < kNumGroupTrial; ++t)
+      if (rate[(size_t)t] > rate[(size_t)best] && rate[(size_t)t] > kTuneMargin * rate[0]) best = t;
+    G = kGroupTrial[best];
+    tuned_g = G;
+  }
+  {
+    const bc_status s = run_range(G, k);
     if (s != BC_OK) return s;
   }
   if (cur_words != ws->words) // back to the workspace's own layout, clean
-    BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->bytes - ctl_bytes, st));
+    BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->slot_bytes - ctl_bytes,
+                           st));
   return BC_OK;
 }
 
@@ -1444,8 +1578,9 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   j->kb = kb;
   j->words = words;
 
-  bc_status s =
-      ws_acquire(ctx, ws_need(g, kind, kb, words, batch ? 1 : plain_slots(g, k)), st, j->ws);
+  j->groups = batch && !dbg ? batch_groups(*j->g, words, k, kb) : 1;
+  bc_status s = ws_acquire(ctx, ws_need(g, kind, kb, words, batch ? j->groups : plain_slots(g, k)),
+                           st, j->ws);
   if (s != BC_OK) return s;
   BC_TRY(pin_get(ctx, &j->h_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1)));
   BC_TRY(pin_get(ctx, &j->h_cnt, sizeof(unsigned long long) * (CNT_N + 1)));
@@ -1586,6 +1721,7 @@ bc_status job_finish(bc_ctx *ctx, JobRec *j) {
   s.mask_words = j->words;
   s.grab = kTuneCandidates[j->cand].grab;
   s.push_levels = (int32_t)j->h_cnt[CNT_PUSH];
+  s.batch_groups = j->groups_used;
   int32_t novf = 0;
   j->ovf_sources.clear();
   for (int64_t i = 0; i < j->k; ++i)

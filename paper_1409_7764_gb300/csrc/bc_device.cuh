@@ -39,15 +39,17 @@ __device__ __forceinline__ int read_err(const Ctl *ctl) {
 // finished level can still be in flight, so the copy is that level's final
 // end, and unlike the live tail (which the next level's enqueues advance) it
 // reads the same in every CTA.  Returns false when the job is in an error
-// state.
-__device__ bool grid_sync(Ctl *ctl, long long timeout_ns, int64_t *snap_dst = nullptr) {
+// state.  `count` CTAs take part (0: the whole grid; a group of CTAs that
+// shares a control block otherwise).
+__device__ bool grid_sync(Ctl *ctl, long long timeout_ns, int64_t *snap_dst = nullptr,
+                          unsigned count = 0) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned *genp = &ctl->bar_gen;
     const unsigned gen = *genp;
     __threadfence();
     const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == (count ? count : gridDim.x) - 1) {
       if (snap_dst) *snap_dst = (int64_t)atomicAdd(&ctl->tail, 0ull);
       ctl->bar_count = 0;
       __threadfence();

@@ -177,16 +177,33 @@ struct ManyParams {
   int32_t kb = kK;                // sources per batch when max_words == 1
 };
 
+// Parameters of a launch that runs a job's batches in concurrent groups of
+// thread blocks: group g (blocks g*gsize .. g*gsize+gsize-1) takes batches
+// g, g+groups, ... of the job's sources from `first` on, with workspace
+// works[g] and BC partial vector parts[g][n].
+struct MultiParams {
+  KParams base;                 // src = the job's source list; bc unused
+  const Work *works = nullptr;  // [groups]
+  double *parts = nullptr;      // [groups][n]
+  int32_t groups = 1;
+  int32_t gsize = 1;
+  int32_t kb = kK;              // sources per batch
+  int64_t k = 0;                // sources of the job
+  int64_t first = 0;            // first source of the grouped range
+};
+
 // Host launchers (bc_kernels.cu).  Return a cudaError_t.
 cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st);
 int max_grid_many(bool fp64, int device);
 cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1,
                          bool counts32 = false);
+cudaError_t launch_multi(const MultiParams &mp, bool fp64, int words, bool counts32,
+                         cudaStream_t st);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain_block(const KParams *slots, int slot, int64_t b, bool fp64,
                                cudaStream_t st);
 cudaError_t launch_sum_parts(const double *parts, int nparts, int64_t n, double *out,
-                             cudaStream_t st);
+                             cudaStream_t st, bool add_to_out = false);
 cudaError_t launch_gather_err(Ctl *first, size_t stride_bytes, int count, cudaStream_t st);
 cudaError_t launch_scale(const double *in, double *out, int64_t n, double factor, cudaStream_t st);
 cudaError_t launch_estimate(const double *sum, const double *sumsq, int64_t n, int64_t k,

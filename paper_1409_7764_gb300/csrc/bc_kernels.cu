@@ -596,6 +596,20 @@ struct GridScope {
   }
 };
 
+// ... or a group of the grid's thread blocks that runs its own batches
+// (several batches at once on disjoint sets of SMs; the group's barrier
+// counts its blocks on its own workspace's control block) ...
+struct GroupScope {
+  static constexpr bool kGrid = true;
+  int g, gsize;
+  __device__ __forceinline__ int rank() const { return (int)blockIdx.x - g * gsize; }
+  __device__ __forceinline__ int size() const { return gsize; }
+  __device__ __forceinline__ bool sync(Ctl *ctl, long long timeout_ns,
+                                       int64_t *snap = nullptr) const {
+    return grid_sync(ctl, timeout_ns, snap, (unsigned)gsize);
+  }
+};
+
 // ... or one thread block that owns the whole batch (CTA barriers; used for
 // many small graphs in one launch).  The snapshot of the queue tail is taken
 // by thread 0 between two barriers, as the grid barrier's last arriver does.
@@ -899,12 +913,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           } else {
             const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
             for (int64_t cc = c0; cc < c0 + nch; ++cc) {
+              uint64_t ow[W];
+#pragma unroll
+              for (int wi = 0; wi < W; ++wi) ow[wi] = ldcg(p.w.partial_ovf + (size_t)cc * W + wi);
 #pragma unroll
               for (int i = 0; i < 2 * W; ++i) {
                 bool o = false;
                 sat_add(t[i], ldcg(pp + (size_t)cc * kRow + 32 * i + lane), o);
-                const uint64_t ow = ldcg(p.w.partial_ovf + (size_t)cc * W + (i >> 1));
-                if (o || ((ow >> ((i & 1) * 32 + lane)) & 1ull)) q |= 1u << i;
+                if (o || ((ow[i >> 1] >> ((i & 1) * 32 + lane)) & 1ull)) q |= 1u << i;
               }
             }
           }
@@ -1108,6 +1124,47 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) batch_kernel(const KP
   batch_body<DT, W, SQ, CT>(p, GridScope(), s_stage[threadIdx.x >> 5], cnt, dag);
   __syncwarp();
   flush_counters(p.job_cnt, to_counters(cnt, dag, lane), lane);
+}
+
+// A job's batches in concurrent groups (MultiParams): fewer SMs per batch
+// make each step's work per warp larger against the fixed costs of a step
+// (the barrier and the last items' tail), which dominate the small steps of
+// small graphs and of deep, narrow traversals.  Every group adds its batches
+// in order into its own BC partial vector; the host sums the vectors in
+// group order, so results repeat bit for bit.
+template <typename DT, int W, bool SQ, typename CT>
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) multi_batch_kernel(const MultiParams mp) {
+  __shared__ int s_stage[kWarpsPerBlock][kStage];
+  __shared__ WarpCounters s_cnt[kWarpsPerBlock];
+  __shared__ KParams sp;
+  const int lane = threadIdx.x & 31;
+  WarpCounters &cnt = s_cnt[threadIdx.x >> 5];
+  zero_counters(cnt, lane);
+  unsigned long long dag = 0;
+  const GroupScope sc{(int)blockIdx.x / mp.gsize, mp.gsize};
+  const int64_t nbatch = (mp.k - mp.first + mp.kb - 1) / mp.kb;
+  if (threadIdx.x == 0) {
+    sp = mp.base;
+    sp.w = mp.works[sc.g];
+    sp.bc = mp.parts + (size_t)sc.g * (size_t)mp.base.g.n;
+    sp.trace = nullptr;
+    sp.skip_block = -1;
+  }
+  for (int64_t b = sc.g; b < nbatch; b += mp.groups) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int64_t s0 = mp.first + b * mp.kb;
+      sp.src = mp.base.src + s0;
+      sp.k = (int32_t)(mp.k - s0 < mp.kb ? mp.k - s0 : mp.kb);
+      sp.src_base = s0;
+    }
+    __syncthreads();
+    batch_body<DT, W, SQ, CT>(sp, sc, s_stage[threadIdx.x >> 5], cnt, dag);
+    // the next batch's set-up must not meet this one's final clean-up
+    if (!sc.sync(sp.w.ctl, sp.timeout_ns)) break;
+  }
+  __syncwarp();
+  flush_counters(mp.base.job_cnt, to_counters(cnt, dag, lane), lane);
 }
 
 // Clears what a batch stopped in its forward sweep may leave behind in a
@@ -1521,12 +1578,12 @@ __global__ void __launch_bounds__(kBlock) plain_block_kernel(const KParams *__re
   plain_body<DT>(sp, CtaScope());
 }
 
-// out[v] = sum over parts of parts[part][v], parts in order (deterministic).
+// out[v] (+)= sum over parts of parts[part][v], parts in order (deterministic).
 __global__ void sum_parts_kernel(const double *__restrict__ parts, int nparts, int64_t n,
-                                 double *__restrict__ out) {
+                                 double *__restrict__ out, bool add) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    double t = 0.0;
+    double t = add ? out[v] : 0.0;
     for (int i = 0; i < nparts; ++i) t += parts[(size_t)i * n + v];
     out[v] = t;
   }
@@ -1669,12 +1726,42 @@ cudaError_t launch_plain_block(const KParams *slots, int slot, int64_t b, bool f
 }
 
 cudaError_t launch_sum_parts(const double *parts, int nparts, int64_t n, double *out,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool add_to_out) {
   if (n <= 0) return cudaSuccess;
   int grid = (int)((n + 255) / 256);
   if (grid > 4096) grid = 4096;
-  sum_parts_kernel<<<grid, 256, 0, st>>>(parts, nparts, n, out);
+  sum_parts_kernel<<<grid, 256, 0, st>>>(parts, nparts, n, out, add_to_out);
   return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t coop_launch_multi(K kernel, const MultiParams &mp, cudaStream_t st) {
+  void *args[] = {const_cast<MultiParams *>(&mp)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kernel),
+                                     dim3(mp.groups * mp.gsize), dim3(kBlock), args, 0, st);
+}
+
+template <typename CT>
+cudaError_t launch_multi_ct(const MultiParams &mp, bool fp64, int words, cudaStream_t st) {
+  switch (words) {
+    case 1:
+      return fp64 ? coop_launch_multi(multi_batch_kernel<double, 1, false, CT>, mp, st)
+                  : coop_launch_multi(multi_batch_kernel<float, 1, false, CT>, mp, st);
+    case 2:
+      return fp64 ? coop_launch_multi(multi_batch_kernel<double, 2, false, CT>, mp, st)
+                  : coop_launch_multi(multi_batch_kernel<float, 2, false, CT>, mp, st);
+    case 4:
+      return fp64 ? coop_launch_multi(multi_batch_kernel<double, 4, false, CT>, mp, st)
+                  : coop_launch_multi(multi_batch_kernel<float, 4, false, CT>, mp, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_multi(const MultiParams &mp, bool fp64, int words, bool counts32,
+                         cudaStream_t st) {
+  return counts32 ? launch_multi_ct<uint32_t>(mp, fp64, words, st)
+                  : launch_multi_ct<uint64_t>(mp, fp64, words, st);
 }
 
 cudaError_t launch_gather_err(Ctl *first, size_t stride_bytes, int count, cudaStream_t st) {

@@ -572,6 +572,9 @@ def test_every_schedule_and_width(ctx, schedule):
     widths = (0,) if schedule == "plain" else (0, 64, 128, 256)
     for kb in widths:
         for fp64 in (False, True):
+            # the graph's first jobs at a width run the tuner's trials
+            for _ in range(3):
+                ctx.exact(G, schedule=schedule, batch_k=kb, delta_fp64=fp64)
             a = ctx.exact(G, schedule=schedule, batch_k=kb, delta_fp64=fp64).copy()
             assert_bc_close(a, ref, fp64)
             b = ctx.exact(G, schedule=schedule, batch_k=kb, delta_fp64=fp64).copy()
@@ -584,22 +587,24 @@ def test_every_schedule_and_width(ctx, schedule):
 
 
 def test_tuner_picks_width_and_split_per_graph():
-    """The first job with enough sources runs the width trial (256, 128 and 64
-    sources per batch, twice each) and the work-split trial at the chosen
-    width on its own batches; the result still matches the oracle, later
-    jobs keep the choice, and they repeat bit for bit."""
+    """The first jobs with enough sources run the width trial (256, 128 and 64
+    sources per batch, twice each), the work-split trial and the concurrent
+    groups trial on their own batches; every result matches the oracle, later
+    jobs keep the choices, and they repeat bit for bit."""
     import paper_1409_7764_gb300 as bc
     g = bcgen.rmat(13, 16, seed=11)  # exact BC: 8192 sources, automatic width 256
     ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
     with bc.Context(0) as fresh:
         G = fresh.create_graph(g.row_ptr, g.col_idx)
-        first = fresh.exact(G).copy()
-        assert_bc_close(first, ref, False)
+        for _ in range(3):
+            assert_bc_close(fresh.exact(G).copy(), ref, False)
         st1 = fresh.last_stats()
         assert st1["batch_sources"] in (64, 128, 256)
+        assert st1["batch_groups"] in (1, 2, 4)
         later = [fresh.exact(G).copy() for _ in range(2)]
         st2 = fresh.last_stats()
-        assert st2["batch_sources"] == st1["batch_sources"]
+        for key in ("batch_sources", "batch_groups", "chunk_edges", "grab"):
+            assert st2[key] == st1[key], key
         assert (st2["chunk_edges"], st2["grab"]) in ((256, 2), (128, 2), (512, 2), (256, 1), (0, 2))
         for x in later:
             assert_bc_close(x, ref, False)
@@ -691,4 +696,32 @@ def test_counts_beyond_32_bits_promote_the_job(direction):
         assert ei.value.status == bc.BC_ERR_SIGMA_OVERFLOW
         _, ovf = oracle.bc(bad.n, bad.row_ptr, bad.col_idx, [0, 2])
         assert ei.value.stats["overflow_sources"] == int(np.count_nonzero(ovf))
+        fresh.destroy_graph(G)
+
+
+@pytest.mark.parametrize("groups", [2, 4])
+def test_concurrent_batch_groups(groups, monkeypatch):
+    """A job's batches after its trials running several at a time, each group
+    of thread blocks on its own workspace and BC partial vector: exact and
+    sampled BC against the oracle, both precisions, both count widths, and a
+    repeated job gives the same bits."""
+    import paper_1409_7764_gb300 as bc
+    monkeypatch.setenv("BC_GROUPS", str(groups))
+    g = bcgen.rmat(12, 16, seed=4)
+    srcs = bcgen.sample_sources(g.n, 1500, seed=8)
+    ref_all, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    ref_s, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    with bc.Context(0) as fresh:
+        G = fresh.create_graph(g.row_ptr, g.col_idx)
+        for _ in range(2):  # the width and split trials
+            fresh.exact(G)
+        for fp64 in (False, True):
+            for bits in (0, 64):
+                a = fresh.exact(G, delta_fp64=fp64, count_bits=bits).copy()
+                assert_bc_close(a, ref_all, fp64)
+                assert fresh.last_stats()["batch_groups"] == groups
+                b = fresh.exact(G, delta_fp64=fp64, count_bits=bits).copy()
+                assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+                assert_bc_close(fresh.sources(G, srcs, delta_fp64=fp64, count_bits=bits,
+                                              batch_k=64), ref_s, fp64)
         fresh.destroy_graph(G)
