@@ -1171,6 +1171,18 @@ int cand_of_split(int variant) {
   return 0;
 }
 
+// BC_SPLIT fixes the tuning candidate (an index into kTuneCandidates) of
+// every batched job and skips the split trial, for experiments and for
+// profiling a tuned configuration under a profiler, whose launch overheads
+// would skew the timed trials (-1: not set).
+int forced_split() {
+  if (const char *env = std::getenv("BC_SPLIT")) {
+    const int c = std::atoi(env);
+    if (c >= 0 && c < kNumTune) return c;
+  }
+  return -1;
+}
+
 // Times the batches launched between consecutive events of `ev` (all of them
 // enqueued already) and returns, per slot of `slot_of`, the summed time per
 // source; the events are destroyed.
@@ -1391,10 +1403,14 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
   // moved (the design's bytes model, from counter snapshots taken between
   // the trial batches).
   std::atomic<int> &tuned_slot = j->g->tuned[word_index(words)];
-  int cand = fixed >= 0 ? split_cand : std::max(tuned_slot.load(), 0);
+  const int forced_cand = forced_split();
+  int cand = fixed >= 0 ? split_cand
+             : forced_cand >= 0 ? forced_cand
+                                : std::max(tuned_slot.load(), 0);
   if (kind != WS_QUEUE) cand = 0;
   const int64_t left = (k - b0 + kb - 1) / kb;
-  if (!notune && fixed < 0 && tuned_slot.load() < 0 && left >= kNumTune * kTuneRounds + 4) {
+  if (!notune && fixed < 0 && forced_cand < 0 && tuned_slot.load() < 0 &&
+      left >= kNumTune * kTuneRounds + 4) {
     constexpr int kTrials = kNumTune * kTuneRounds;
     unsigned long long *d_snap = nullptr;
     BC_TRY(pool_alloc(ctx, &d_snap, sizeof(unsigned long long) * CNT_N * (kTrials + 1), st));
