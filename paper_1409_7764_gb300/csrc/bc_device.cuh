@@ -338,9 +338,12 @@ template <int W, typename CT> struct CountUnroll {
 // count reached 2^64).  Otherwise cbits only counts carries out of the
 // count's width: the caller then takes the exact form (64-bit counts, rare:
 // counts near 2^64) or promotes the job to 64-bit counts (32-bit storage).
+// `unit` (uniform): every predecessor's count is 1 (level 1 of a simple
+// graph), so each set bit adds 1 and no row is loaded.
 template <int W, bool kExact = true, typename CT = uint64_t>
 __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mask<W> &P,
-                                                int lane, CT (&s)[2 * W], unsigned &cbits) {
+                                                int lane, CT (&s)[2 * W], unsigned &cbits,
+                                                bool unit = false) {
   constexpr int U = CountUnroll<W, CT>::value;
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, P.any());
@@ -366,8 +369,8 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
         const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
 #endif
         const unsigned lo = (unsigned)PP, hi = (unsigned)(PP >> 32);
-        x[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : CT(0);
-        x[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : CT(0);
+        x[i][2 * wi] = (lo & mybit) ? (unit ? CT(1) : ldcg(row + 64 * wi)) : CT(0);
+        x[i][2 * wi + 1] = (hi & mybit) ? (unit ? CT(1) : ldcg(row + 64 * wi + 32)) : CT(0);
       }
     }
 #pragma unroll

@@ -201,11 +201,13 @@ __device__ __forceinline__ void stage_new(const KParams &p, const LevelView &lv,
 }
 
 // Path-count pull of an entry (mask F) over its in-edges [ib, ib + din)
-// from the level l-1 masks Pm, in edge order.
+// from the level l-1 masks Pm, in edge order (`unit`: level l-1's counts
+// are all 1, see gather_counts_w).
 template <int W, bool kExact, typename CT>
 __device__ __forceinline__ void pull_counts(const KParams &p, const Mask<W> &F, int ib, int din,
                                             const uint64_t *Pm, int lane, CT (&s)[2 * W],
-                                            unsigned &cbits, unsigned long long &dag) {
+                                            unsigned &cbits, unsigned long long &dag,
+                                            bool unit) {
   for (int r = 0; r < din; r += kWarp) {
     const int t = r + lane;
     int u = 0;
@@ -216,7 +218,7 @@ __device__ __forceinline__ void pull_counts(const KParams &p, const Mask<W> &F, 
     }
     dag += P.popc(); // per lane; the warp's counters are summed at the flush
     gather_counts_w<W, kExact, CT>(reinterpret_cast<const CT *>(p.w.sigma), u, P, lane, s,
-                                   cbits);
+                                   cbits, unit);
   }
 }
 
@@ -225,12 +227,12 @@ __device__ __forceinline__ void pull_counts(const KParams &p, const Mask<W> &F, 
 template <int W>
 __device__ __forceinline__ void exact_counts(const KParams &p, const Mask<W> &F, int ib, int din,
                                           const uint64_t *Pm, int lane, uint64_t (&s)[2 * W],
-                                          unsigned &cbits) {
+                                          unsigned &cbits, bool unit) {
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) s[i] = 0;
   cbits = 0;
   unsigned long long dag = 0; // counted by the fast pull already
-  pull_counts<W, true, uint64_t>(p, F, ib, din, Pm, lane, s, cbits, dag);
+  pull_counts<W, true, uint64_t>(p, F, ib, din, Pm, lane, s, cbits, dag, unit);
 }
 
 // Pushed path counts (the other direction of the forward step at level l):
@@ -317,10 +319,10 @@ template <int W, typename CT>
 __device__ __forceinline__ void settle_carries(const KParams &p, const Mask<W> &F, int ib,
                                                int din, const uint64_t *Pm, int lane,
                                                CT (&s)[2 * W], unsigned &cbits,
-                                               unsigned carries) {
+                                               unsigned carries, bool unit) {
   if (!__any_sync(kFull, carries != 0)) return;
   if constexpr (sizeof(CT) == 4) set_err(p.w.ctl, KERR_WIDE);
-  else exact_counts<W>(p, F, ib, din, Pm, lane, s, cbits);
+  else exact_counts<W>(p, F, ib, din, Pm, lane, s, cbits, unit);
 }
 
 template <int W, typename CT>
@@ -328,7 +330,8 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
                                          int ib, int ie, int ob, int oe,
                                          const uint64_t *A, const uint64_t *Pm, uint64_t *Bn,
                                          int *stage, int &nst, int lane, CT (&s)[2 * W],
-                                         unsigned &cbits, unsigned long long &dag) {
+                                         unsigned &cbits, unsigned long long &dag,
+                                         bool unit = false) {
   const int din = ie > ib ? ie - ib : 0, dout = oe > ob ? oe - ob : 0;
   const int claim_to = lv.lvl + 2;
   constexpr bool kFast = BC_GATHER_FORM >= 1 || sizeof(CT) == 4;
@@ -337,8 +340,8 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
     // wide masks: the pull and the push run as two loops, so the registers
     // of the path-count gathers and of the discovery masks are not live
     // together
-    pull_counts<W, !kFast, CT>(p, F, ib, din, Pm, lane, s, kFast ? carries : cbits, dag);
-    if (kFast) settle_carries<W, CT>(p, F, ib, din, Pm, lane, s, cbits, carries);
+    pull_counts<W, !kFast, CT>(p, F, ib, din, Pm, lane, s, kFast ? carries : cbits, dag, unit);
+    if (kFast) settle_carries<W, CT>(p, F, ib, din, Pm, lane, s, cbits, carries, unit);
     for (int r = 0; r < dout; r += kWarp) {
       const int t = r + lane;
       int x = 0;
@@ -380,10 +383,10 @@ __device__ __forceinline__ void fwd_scan(const KParams &p, const LevelView &lv, 
       Mask<1> PM;
       PM.w[0] = P;
       gather_counts_w<1, !kFast, CT>(reinterpret_cast<const CT *>(p.w.sigma), u, PM, lane, s,
-                                     kFast ? carries : cbits);
+                                     kFast ? carries : cbits, unit);
       stage_new(p, lv, nb != 0 && old == 0, x, stage, nst, lane);
     }
-    if (kFast) settle_carries<1, CT>(p, F, ib, din, Pm, lane, s, cbits, carries);
+    if (kFast) settle_carries<1, CT>(p, F, ib, din, Pm, lane, s, cbits, carries, unit);
   }
 }
 
@@ -681,8 +684,15 @@ __device__ __forceinline__ Counters to_counters(const WarpCounters &w, unsigned 
   return c;
 }
 
-// Sets the path counts of a level-0 entry (every source bit of it is the
-// vertex itself: one path) in the lane's slots.
+// First forward level whose path counts may be pushed (levels 0 and 1 have
+// counts of 1 and need no count step).
+#ifndef BC_FIRST_PUSH_LEVEL
+#define BC_FIRST_PUSH_LEVEL 2
+#endif
+constexpr int kFirstPushLevel = BC_FIRST_PUSH_LEVEL;
+
+// Sets the path counts of a level-0 or level-1 entry (one path per source
+// bit) in the lane's slots.
 template <int W, typename T> __device__ __forceinline__ void unit_counts(T (&s)[2 * W]) {
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i) s[i] = 1;
@@ -776,8 +786,14 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
     lv.hoff_next = lv.hoff + lv.nheavy;
     // direction of this level's path-count step, the same in every block:
     // the degree sums of levels l-1 and l are complete since the last barrier
+    // Levels 0 and 1 need no path-count step: in a simple graph a source
+    // has one shortest path to itself and one (its edge) to each vertex at
+    // depth 1, so their counts are 1 for every source bit.  Level 2 pulls
+    // from those counts of 1: its gathers add 1 per set bit and load no row.
+    const bool unit_level = l <= 1;
+    const bool unit_pull = l == 2;
     bool push = false;
-    if (p.push_ratio != 0 && l >= 1)
+    if (p.push_ratio != 0 && l >= kFirstPushLevel)
       push = p.push_ratio < 0 ||
              (unsigned long long)p.push_ratio * ldcg(p.w.lsum + 2 * (l - 1) + 1) <
                  ldcg(p.w.lsum + 2 * l);
@@ -860,15 +876,21 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         const int64_t c = item - hc.first;
         const int is = __ldg(p.g.in_ptr + w), ie = __ldg(p.g.in_ptr + w + 1);
         const int rs = __ldg(p.g.row_ptr + w), re = __ldg(p.g.row_ptr + w + 1);
-        if (push) {
+        if (push || unit_level) {
           // discovery only, over this chunk's share of the out-edges; the
-          // first chunk records the entry
+          // first chunk records the entry (and, at levels 0 and 1, its
+          // counts of 1)
           const int od = re - rs;
           const int a = (int)(c * od / nch), b = (int)((c + 1) * od / nch);
           CT s[2 * W] = {};
           unsigned cb = 0;
           fwd_scan<W, CT>(p, lv, F, 0, 0, rs + a, rs + b, A, Pm, Bn, stage, nst, lane, s, cb,
                           dag);
+          if (unit_level && c == 0) {
+            unit_counts<W, CT>(s);
+            batch_store_sigma_w<W, CT>(p, w, F, s, 0u, lane);
+            if (l == 1 && lane == 0) dag += F.popc(); // one DAG edge per source bit
+          }
           if (lane == 0) {
             cnt.out_e += (uint64_t)(b - a);
             cnt.heavy++;
@@ -887,8 +909,8 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         const int ib = is + (a < indeg ? a : indeg), ie2 = is + (b < indeg ? b : indeg);
         const int obg = rs + (a > indeg ? a - indeg : 0);
         const int oen = rs + (b > indeg ? b - indeg : 0);
-        fwd_scan<W, CT>(p, lv, F, l > 0 ? ib : 0, l > 0 ? ie2 : 0, obg, oen, A, Pm, Bn, stage,
-                        nst, lane, s, cb, dag);
+        fwd_scan<W, CT>(p, lv, F, ib, ie2, obg, oen, A, Pm, Bn, stage, nst, lane, s, cb, dag,
+                        unit_pull);
         if (lane == 0) {
           cnt.in_e += (uint64_t)((b < indeg ? b : indeg) - (a < indeg ? a : indeg));
           cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
@@ -908,9 +930,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           const int64_t c0 = hc.first;
           uint64_t t[2 * W] = {};
           unsigned q = 0;
-          if (l == 0) {
-            unit_counts<W, uint64_t>(t);
-          } else {
+          {
             const uint64_t *pp = reinterpret_cast<const uint64_t *>(p.w.partial);
             for (int64_t cc = c0; cc < c0 + nch; ++cc) {
               uint64_t ow[W];
@@ -953,10 +973,13 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           const int w = (int)hd.field(FF::kId, i);
           CT s[2 * W] = {};
           unsigned cb = 0;
-          const bool pull = l > 0 && !push;
+          const bool pull = !unit_level && !push;
           fwd_scan<W, CT>(p, lv, F, pull ? is : 0, pull ? ie : 0, rs, re, A, Pm, Bn, stage, nst,
-                          lane, s, cb, dag);
-          if (l == 0) unit_counts<W, CT>(s);
+                          lane, s, cb, dag, unit_pull);
+          if (unit_level) {
+            unit_counts<W, CT>(s);
+            if (l == 1 && lane == 0) dag += F.popc(); // one DAG edge per source bit
+          }
           if (!push) batch_store_sigma_w<W, CT>(p, w, F, s, cb, lane);
           if (lane == 0) {
             store_mask<W>(p.w.qm, e0 + i, F);
@@ -1021,7 +1044,10 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
       const int64_t zlo = ldcg(p.w.qoff + l + 2), zhi = ldcg(p.w.qoff + l + 3);
       for (int64_t i = zlo + gtid; i < zhi; i += nthr) zero_mask<W>(Z, ldcg(p.w.qv + i));
     }
-    const bool deepest = (l == L - 1);
+    // the deepest level has no successors; at level 0 every source bit is
+    // the vertex itself, whose own dependency no BC term uses (only debug
+    // exports report it)
+    const bool gather = l < L - 1 && (l > 0 || p.dbg_d != nullptr);
     unsigned long long *ctr = &ctl->work[step & 3];
     const int64_t total = bl.nhc + (bl.hi - bl.lo);
     trace_step(p, step, -1 - l, total, bl.nhc, gtid);
@@ -1045,9 +1071,9 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         const int od = re - rs;
         const int a = (int)(c * od / nch), b = (int)((c + 1) * od / nch);
         DT acc[2 * W] = {};
-        if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs + a, rs + b, Dn, lane, acc);
+        if (gather) batch_pull_delta_w<W, DT>(p, F, rs + a, rs + b, Dn, lane, acc);
         if (lane == 0) {
-          cnt.out_e += (uint64_t)(deepest ? 0 : b - a);
+          cnt.out_e += (uint64_t)(gather ? b - a : 0);
           cnt.heavy++;
         }
         DT *part = reinterpret_cast<DT *>(p.w.partial) + (size_t)item * kRow;
@@ -1080,15 +1106,15 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           if constexpr (W <= BC_OWN_EARLY_MAX_W) {
             // own counts loaded ahead of the successor scan (overlapping it)
             const EntryOwn<W, CT> own(p, v, F, lane);
-            if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
+            if (gather) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
             batch_finish<DT, W, SQ, CT>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           } else {
             // widest masks: loaded after it, which keeps 4W registers free
-            if (!deepest) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
+            if (gather) batch_pull_delta_w<W, DT>(p, F, rs, re, Dn, lane, acc);
             const EntryOwn<W, CT> own(p, v, F, lane);
             batch_finish<DT, W, SQ, CT>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
           }
-          if (!deepest && lane == 0) cnt.out_e += (uint64_t)(re - rs);
+          if (gather && lane == 0) cnt.out_e += (uint64_t)(re - rs);
         }
       }
       base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
