@@ -146,7 +146,7 @@ DESIGN_MODEL_TEXT = {2: "124E + (4+8W)(I+O) + (8+b)D + (16+b)R, W = mask_words",
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ["bc_kernels.cu", "bc_device.cuh", "bc_internal.cuh"]:
+    for f in ["bc_kernels.cu", "bc_narrow.cu", "bc_batch.cuh", "bc_device.cuh", "bc_internal.cuh"]:
         with open(os.path.join(ROOT, "paper_1409_7764_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

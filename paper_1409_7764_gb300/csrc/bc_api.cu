@@ -459,6 +459,10 @@ struct JobRec {
   bool all_sources = false;
   bc_opts opts{};
   int64_t k = 0;            // number of sources
+  // sources the batched kernels traverse: in grouped order the sources
+  // without out-edges come last, and their traversal (the source alone)
+  // adds nothing to any BC value, so they are not launched
+  int64_t k_traverse = 0;
   int64_t n = 0;            // vertices of the graph (result length)
   // run state
   int slot = -1;
@@ -1558,9 +1562,42 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
     G = kGroupTrial[best];
     tuned_g = G;
   }
+  // Full batches up to the sources without out-edges (the tuning trials
+  // above may have taken some of those already; the rest are not launched),
+  // then the last, partly filled batch: with at most half its sources it
+  // runs with fewer mask words in the same layout (bc_narrow.cu).
+  const int64_t kt = std::max(b0, j->k_traverse);
+  const int64_t full_end = b0 + (kt - b0) / kb * kb;
   {
-    const bc_status s = run_range(G, k);
+    const bc_status s = run_range(G, kind == WS_QUEUE && !dbg ? full_end : kt);
     if (s != BC_OK) return s;
+  }
+  if (b0 < kt) {
+    const int64_t rem = kt - b0;
+    int nw = words;
+    while (nw > 1 && rem <= (int64_t)kK * (nw / 2)) nw /= 2;
+    if (nw < words && cur_words == words && !j->acc_sum && kind == WS_QUEUE && !dbg) {
+      p.g.nchunks = j->g->nch_variant[kTuneCandidates[cand].variant];
+      p.grab = kTuneCandidates[cand].grab;
+      p.src = j->d_src + b0;
+      p.k = (int32_t)rem;
+      p.src_base = b0;
+      p.trace = (j->d_trace && bi == j->trace_batch) ? j->d_trace : nullptr;
+      p.trace_cap = p.trace ? trace_cap : 0;
+      const int grid = pick_grid(ctx, g, kind, fp64, words);
+      if (grid <= 0) return BC_ERR_CUDA;
+      BC_TRY(launch_batch_narrow(p, fp64, grid, st, nw, words, c32));
+      b0 = kt;
+      ++bi;
+      ++j->batches;
+      ++j->launches;
+      j->cand = cand;
+    } else {
+      while (b0 < kt) {
+        const bc_status s = launch(kb, words, cand);
+        if (s != BC_OK) return s;
+      }
+    }
   }
   if (cur_words != ws->words) // back to the workspace's own layout, clean
     BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->slot_bytes - ctl_bytes,
@@ -1634,6 +1671,15 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
         std::sort(keys.begin(), keys.end());
         for (int64_t i = 0; i < k; ++i) j->h_src[i] = (int32_t)(uint32_t)keys[(size_t)i].lo;
       }
+    }
+  }
+  j->k_traverse = k;
+  if (grouped && !j->acc_sum) {
+    const std::vector<int32_t> &rp = j->g->row_ptr;
+    while (j->k_traverse > 0) {
+      const int32_t v = j->h_src[j->k_traverse - 1];
+      if (rp[(size_t)v + 1] != rp[(size_t)v]) break;
+      --j->k_traverse;
     }
   }
   BC_TRY(pool_alloc(ctx, &j->d_src, sizeof(int32_t) * (size_t)std::max<int64_t>(k, 1), st));

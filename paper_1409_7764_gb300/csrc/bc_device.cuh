@@ -215,11 +215,13 @@ template <int W> struct Mask {
   }
 };
 
-// Mask of vertex v from an array of W-word masks, through L2 (16-byte loads
-// for W >= 2).
-template <int W> __device__ __forceinline__ Mask<W> load_mask(const uint64_t *base, int64_t v) {
+// Mask of vertex v from an array of S-word masks (its first W words), through
+// L2 (16-byte loads for W >= 2).  S > W: a batch of fewer sources run in a
+// workspace laid out for wider ones (the unused words stay zero).
+template <int W, int S = W>
+__device__ __forceinline__ Mask<W> load_mask(const uint64_t *base, int64_t v) {
   Mask<W> m;
-  const uint64_t *q = base + (size_t)v * W;
+  const uint64_t *q = base + (size_t)v * S;
   if constexpr (W == 1) {
     m.w[0] = ldcg(q);
   } else {
@@ -233,15 +235,15 @@ template <int W> __device__ __forceinline__ Mask<W> load_mask(const uint64_t *ba
   return m;
 }
 
-template <int W> __device__ __forceinline__ void store_mask(uint64_t *base, int64_t v,
-                                                            const Mask<W> &m) {
-  uint64_t *q = base + (size_t)v * W;
+template <int W, int S = W>
+__device__ __forceinline__ void store_mask(uint64_t *base, int64_t v, const Mask<W> &m) {
+  uint64_t *q = base + (size_t)v * S;
 #pragma unroll
   for (int i = 0; i < W; ++i) q[i] = m.w[i];
 }
 
-template <int W> __device__ __forceinline__ void zero_mask(uint64_t *base, int64_t v) {
-  store_mask<W>(base, v, Mask<W>::zero());
+template <int W, int S = W> __device__ __forceinline__ void zero_mask(uint64_t *base, int64_t v) {
+  store_mask<W, S>(base, v, Mask<W>::zero());
 }
 
 template <int W> __device__ __forceinline__ Mask<W> shfl_mask(const Mask<W> &m, int src) {
@@ -340,7 +342,7 @@ template <int W, typename CT> struct CountUnroll {
 // counts near 2^64) or promotes the job to 64-bit counts (32-bit storage).
 // `unit` (uniform): every predecessor's count is 1 (level 1 of a simple
 // graph), so each set bit adds 1 and no row is loaded.
-template <int W, bool kExact = true, typename CT = uint64_t>
+template <int W, bool kExact = true, typename CT = uint64_t, int S = W>
 __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mask<W> &P,
                                                 int lane, CT (&s)[2 * W], unsigned &cbits,
                                                 bool unit = false) {
@@ -357,7 +359,7 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const int uu = shfl_or_zero(u, q.l[i]);
-      const CT *row = base + (size_t)uu * (kK * W) + lane;
+      const CT *row = base + (size_t)uu * (kK * S) + lane;
 #if BC_MASK_STAGE
       const Mask<W> PE = rm.of(q.l[i]);
 #endif
@@ -389,7 +391,7 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
 
 // Dependency coefficients over the round's successor edges, added in edge
 // order (a missing edge adds +0, which changes no sum of non-negative terms).
-template <int W, typename DT>
+template <int W, typename DT, int LS = W>
 __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mask<W> &S,
                                                 int lane, DT (&a)[2 * W]) {
   constexpr int U = CoeffUnroll<W, DT>::value;
@@ -405,7 +407,7 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const int xx = shfl_or_zero(x, q.l[i]);
-      const DT *row = base + (size_t)xx * (kK * W) + lane;
+      const DT *row = base + (size_t)xx * (kK * LS) + lane;
 #if BC_MASK_STAGE
       const Mask<W> SE = rm.of(q.l[i]);
 #endif
@@ -431,7 +433,7 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
 // Dependency pull over out-edges [eb, ee) of an entry with mask F from the
 // level l+1 masks Dn: lane j sums c[x][32*i + j] over successors x whose
 // level-(l+1) mask has source 32*i + j, in edge order.
-template <int W, typename DT>
+template <int W, typename DT, int LS = W>
 __device__ __forceinline__ void batch_pull_delta_w(const KParams &p, const Mask<W> &F, int eb,
                                                    int ee, const uint64_t *Dn, int lane,
                                                    DT (&a)[2 * W]) {
@@ -442,20 +444,20 @@ __device__ __forceinline__ void batch_pull_delta_w(const KParams &p, const Mask<
     Mask<W> S = Mask<W>::zero();
     if (e < ee) {
       x = __ldg(p.g.col_idx + e);
-      S = load_mask<W>(Dn, x) & F;
+      S = load_mask<W, LS>(Dn, x) & F;
     }
-    gather_coeffs_w<W, DT>(cdep, x, S, lane, a);
+    gather_coeffs_w<W, DT, LS>(cdep, x, S, lane, a);
   }
 }
 
 // Writes the path counts of entry w (mask F; counts saturated where the carry
 // bit is set) and records the overflowing sources in the control block.
 // Counts are stored as CT (32-bit counts are below 2^32 here).
-template <int W, typename CT, typename AT>
+template <int W, typename CT, typename AT, int S = W>
 __device__ __forceinline__ void batch_store_sigma_w(const KParams &p, int w, const Mask<W> &F,
                                                     const AT (&s)[2 * W], unsigned cbits,
                                                     int lane) {
-  CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)w * (kK * W);
+  CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)w * (kK * S);
 #pragma unroll
   for (int i = 0; i < 2 * W; ++i)
     if (F.has(i, lane)) row[32 * i + lane] = ((cbits >> i) & 1u) ? CT(~0ull) : CT(s[i]);

@@ -199,6 +199,10 @@ cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st,
                          bool counts32 = false);
 cudaError_t launch_multi(const MultiParams &mp, bool fp64, int words, bool counts32,
                          cudaStream_t st);
+// A batch of `words` mask words in a workspace laid out for layout_words >
+// words (bc_narrow.cu); plain BC only (no squared terms).
+cudaError_t launch_batch_narrow(const KParams &p, bool fp64, int grid, cudaStream_t st,
+                                int words, int layout_words, bool counts32);
 cudaError_t launch_plain(const KParams &p, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain_block(const KParams *slots, int slot, int64_t b, bool fp64,
                                cudaStream_t st);

@@ -725,3 +725,32 @@ def test_concurrent_batch_groups(groups, monkeypatch):
                 assert_bc_close(fresh.sources(G, srcs, delta_fp64=fp64, count_bits=bits,
                                               batch_k=64), ref_s, fp64)
         fresh.destroy_graph(G)
+
+
+@pytest.mark.parametrize("kb,active", [(256, 306), (256, 356), (128, 168), (256, 456)])
+def test_last_batch_narrow_and_sources_without_out_edges(ctx, kb, active):
+    """Sources without out-edges are ordered last and not launched (their
+    traversal is the source alone and adds nothing); the last batch of the
+    others, when at most half full, runs with fewer mask words in the wide
+    batches' layout (64 of 256, 128 of 256, 64 of 128).  BC against the
+    oracle in both precisions and count widths, the same bits on a repeat,
+    and a list of such sources alone gives zeros without a launch."""
+    g = bcgen.rmat(12, 16, seed=6)
+    outdeg = np.diff(g.row_ptr)
+    act = np.flatnonzero(outdeg > 0).astype(np.int32)
+    sinks = np.flatnonzero(outdeg == 0).astype(np.int32)
+    rs = np.random.default_rng(active)
+    srcs = np.concatenate([rs.choice(act, active, replace=False), sinks[:30]]).astype(np.int32)
+    rs.shuffle(srcs)
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    G = ctx.create_graph(g.row_ptr, g.col_idx)
+    for fp64 in (False, True):
+        for bits in (0, 64):
+            a = ctx.sources(G, srcs, delta_fp64=fp64, batch_k=kb, count_bits=bits).copy()
+            assert_bc_close(a, ref, fp64)
+            assert ctx.last_stats()["batches"] == -(-active // kb)
+            b = ctx.sources(G, srcs, delta_fp64=fp64, batch_k=kb, count_bits=bits).copy()
+            assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    none = ctx.sources(G, np.tile(sinks[:40], 8), batch_k=kb)
+    assert not none.any() and ctx.last_stats()["batches"] == 0
+    ctx.destroy_graph(G)
