@@ -671,7 +671,7 @@ bc_status prep_host(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, i
     const int64_t ch = kChunkCandidates[c];
     for (int32_t v = 0; v < n; ++v) {
       const int64_t cost = (int64_t)(rp[(size_t)v + 1] - rp[v]) + (h.ip[(size_t)v + 1] - h.ip[v]);
-      if (cost > ch) {
+      if (cost > heavy_threshold(ch)) {
         const int32_t k = (int32_t)((cost + ch - 1) / ch);
         h.nc[(size_t)c * n + v] = k;
         h.heavy_v[c]++;

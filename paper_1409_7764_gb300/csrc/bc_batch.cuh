@@ -918,6 +918,17 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           cnt.out_e += (uint64_t)((b > indeg ? b - indeg : 0) - (a > indeg ? a - indeg : 0));
           cnt.heavy++;
         }
+        if (nch == 1) {
+          // an entry listed with the heavy ones for its size but not split
+          // (so it starts early in the step): it stores its counts itself
+          batch_store_sigma_w<W, CT, CT, S>(p, w, F, s, cb, lane);
+          if (lane == 0) {
+            store_mask<W, S>(p.w.qm, e, F);
+            cnt.entries++;
+            cnt.reached += F.popc();
+          }
+          continue;
+        }
         uint64_t *part = reinterpret_cast<uint64_t *>(p.w.partial) + (size_t)item * kRow;
 #pragma unroll
         for (int i = 0; i < 2 * W; ++i) part[32 * i + lane] = s[i];
@@ -1077,6 +1088,11 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         if (lane == 0) {
           cnt.out_e += (uint64_t)(gather ? b - a : 0);
           cnt.heavy++;
+        }
+        if (nch == 1) { // not split: the entry closes itself
+          const EntryOwn<W, CT, S> own(p, v, F, lane);
+          batch_finish<DT, W, SQ, CT, S>(p, l, v, F, acc, own.sg, own.bcv, Wn, lane);
+          continue;
         }
         DT *part = reinterpret_cast<DT *>(p.w.partial) + (size_t)item * kRow;
 #pragma unroll

@@ -146,7 +146,7 @@ __global__ void graph_keys_kernel(const int32_t *__restrict__ row_ptr,
       for (int c = 0; c < kChunkVariants; ++c) {
         const int64_t ch = kSizes[c];
         int32_t nc = 0;
-        if (cost > ch) {
+        if (cost > heavy_threshold(ch)) {
           nc = (int32_t)((cost + ch - 1) / ch);
           atomicAdd(totals + 2 * c, 1ull);
           atomicAdd(totals + 2 * c + 1, (unsigned long long)nc);
