@@ -318,6 +318,62 @@ template <int W> struct RoundMasks {
   }
 };
 
+#ifndef BC_ROUND_LIST
+#define BC_ROUND_LIST 1 // 1: a round's edges with sources reach the lanes as a packed list
+#endif
+
+// Per-warp list of a gather round's edges that carry sources (non-empty
+// mask), packed in lane order: the lane holding such an edge writes its
+// vertex and mask at its rank among them, and every lane then reads entry i
+// with broadcast shared-memory loads: no search of the ballot for the i-th
+// edge's lane and no shuffle of its vertex.  Entries from cnt on read as
+// vertex 0 with an empty mask (they gather nothing).
+__shared__ int32_t g_vert_stage[kWarpsPerBlock][kWarp];
+
+template <int W> struct RoundList {
+  const uint64_t *stg;
+  const int32_t *vst;
+  int cnt;
+  __device__ __forceinline__ RoundList(const Mask<W> &P, int v, unsigned bal, int lane) {
+    uint64_t *row = &g_mask_stage[threadIdx.x >> 5][0][0];
+    int32_t *vr = g_vert_stage[threadIdx.x >> 5];
+    stg = row;
+    vst = vr;
+    cnt = __popc(bal);
+    __syncwarp();
+    if ((bal >> lane) & 1u) {
+      const int pos = __popc(bal & lanemask_lt());
+      vr[pos] = v;
+      if constexpr (W == 1) {
+        row[pos * kMaxWords] = P.w[0];
+      } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2)
+          *reinterpret_cast<ulonglong2 *>(row + pos * kMaxWords + i) =
+              make_ulonglong2(P.w[i], P.w[i + 1]);
+      }
+    }
+    __syncwarp();
+  }
+  __device__ __forceinline__ int vert(int i) const { return i < cnt ? vst[i] : 0; }
+  __device__ __forceinline__ Mask<W> mask(int i) const {
+    Mask<W> m;
+    if (i >= cnt) return Mask<W>::zero();
+    const uint64_t *e = stg + i * kMaxWords;
+    if constexpr (W == 1) {
+      m.w[0] = e[0];
+    } else {
+#pragma unroll
+      for (int j = 0; j < W; j += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(e + j);
+        m.w[j] = t.x;
+        m.w[j + 1] = t.y;
+      }
+    }
+    return m;
+  }
+};
+
 // s += x, with the carry out of the top bit added to c (c counts carries).
 __device__ __forceinline__ void add_count_carry(uint64_t &s, uint64_t x, unsigned &c) {
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(s), "+r"(c) : "l"(x));
@@ -350,6 +406,15 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, P.any());
   if (!bal) return;
+#if BC_ROUND_LIST
+  const RoundList<W> rl(P, u, bal, lane);
+  for (int i0 = 0; i0 < rl.cnt; i0 += U) {
+    CT x[U][2 * W];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const CT *row = base + (size_t)rl.vert(i0 + i) * (kK * S) + lane;
+      const Mask<W> PE = rl.mask(i0 + i);
+#else
 #if BC_MASK_STAGE
   const RoundMasks<W> rm(P, lane);
 #endif
@@ -363,9 +428,10 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
 #if BC_MASK_STAGE
       const Mask<W> PE = rm.of(q.l[i]);
 #endif
+#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
-#if BC_MASK_STAGE
+#if BC_MASK_STAGE || BC_ROUND_LIST
         const uint64_t PP = PE.w[wi];
 #else
         const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
@@ -398,6 +464,15 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, S.any());
   if (!bal) return;
+#if BC_ROUND_LIST
+  const RoundList<W> rl(S, x, bal, lane);
+  for (int i0 = 0; i0 < rl.cnt; i0 += U) {
+    DT y[U][2 * W];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const DT *row = base + (size_t)rl.vert(i0 + i) * (kK * LS) + lane;
+      const Mask<W> SE = rl.mask(i0 + i);
+#else
 #if BC_MASK_STAGE
   const RoundMasks<W> rm(S, lane);
 #endif
@@ -411,9 +486,10 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
 #if BC_MASK_STAGE
       const Mask<W> SE = rm.of(q.l[i]);
 #endif
+#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
-#if BC_MASK_STAGE
+#if BC_MASK_STAGE || BC_ROUND_LIST
         const uint64_t SS = SE.w[wi];
 #else
         const uint64_t SS = shfl_or_zero(S.w[wi], q.l[i]);
