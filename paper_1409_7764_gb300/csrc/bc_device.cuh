@@ -268,9 +268,15 @@ template <int W> struct GatherUnroll {
 #ifndef BC_NARROW_UNROLL
 #define BC_NARROW_UNROLL 2 // edges in flight of 4-byte gathers, relative to 8-byte ones
 #endif
+#ifndef BC_NARROW_UNROLL_W4
+#define BC_NARROW_UNROLL_W4 3 // 4-byte gathers of 256-source batches: edges per round
+#endif
+template <int W> struct NarrowUnroll {
+  static constexpr int value = W == 4 ? BC_NARROW_UNROLL_W4 : BC_NARROW_UNROLL * GatherUnroll<W>::value;
+};
 template <int W, typename DT> struct CoeffUnroll {
   static constexpr int value = (BC_GATHER_FORM >= 1 && sizeof(DT) == 4)
-                                   ? BC_NARROW_UNROLL * GatherUnroll<W>::value
+                                   ? NarrowUnroll<W>::value
                                    : GatherUnroll<W>::value;
 };
 
@@ -385,8 +391,7 @@ __device__ __forceinline__ void add_count_carry(uint32_t &s, uint32_t x, unsigne
 // Edges per round of the path-count gather: 4-byte counts (the 32-bit
 // storage form) keep twice as many edges in flight in the same registers.
 template <int W, typename CT> struct CountUnroll {
-  static constexpr int value =
-      sizeof(CT) == 4 ? BC_NARROW_UNROLL * GatherUnroll<W>::value : GatherUnroll<W>::value;
+  static constexpr int value = sizeof(CT) == 4 ? NarrowUnroll<W>::value : GatherUnroll<W>::value;
 };
 
 // Path counts over the round's shortest-path edges (lanes whose mask P is not
