@@ -284,20 +284,10 @@ __device__ __forceinline__ void push_counts(const KParams &p, int u, const Mask<
     dag += P.popc(); // per lane; the warp's counters are summed at the flush
     unsigned bal = __ballot_sync(kFull, P.any());
     if (!bal) continue;
-#if BC_ROUND_LIST
     const RoundList<W> rl(P, x, bal, lane);
     for (int i = 0; i < rl.cnt; ++i) {
       CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)rl.vert(i) * (kK * S) + lane;
       const Mask<W> PE = rl.mask(i);
-#else
-    const RoundMasks<W> rm(P, lane);
-    while (bal) {
-      const int src = __ffs(bal) - 1;
-      bal &= bal - 1;
-      const int xx = __shfl_sync(kFull, x, src);
-      CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)xx * (kK * S) + lane;
-      const Mask<W> PE = rm.of(src);
-#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
         const uint64_t PP = PE.w[wi];

@@ -122,9 +122,6 @@ __device__ __forceinline__ long long phase_clock() {
 }
 
 
-template <typename T> __device__ __forceinline__ T shfl_or_zero(T v, int src) {
-  return src >= 0 ? __shfl_sync(kFull, v, src) : T(0);
-}
 
 // Optional per-step trace (block 0, thread 0): globaltimer at the start of
 // the step, the step's level (negative = backward), items and heavy chunks.
@@ -154,18 +151,6 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 #ifndef BC_GATHER_UNROLL
 #define BC_GATHER_UNROLL 4 // DAG edges gathered per round (lanes-per-source form)
 #endif
-
-// Up to U set lanes of a ballot, in lane order; missing ones are -1.
-template <int U> struct LanesU {
-  int l[U];
-  __device__ __forceinline__ explicit LanesU(unsigned &bal) {
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-      l[i] = bal ? __ffs(bal) - 1 : -1;
-      bal &= bal - 1;
-    }
-  }
-};
 
 // ---------------------------------------------------------------------------
 // Source masks of W 64-bit words (64*W sources per batch).  Lane j owns the
@@ -246,12 +231,6 @@ template <int W, int S = W> __device__ __forceinline__ void zero_mask(uint64_t *
   store_mask<W, S>(base, v, Mask<W>::zero());
 }
 
-template <int W> __device__ __forceinline__ Mask<W> shfl_mask(const Mask<W> &m, int src) {
-  Mask<W> r;
-#pragma unroll
-  for (int i = 0; i < W; ++i) r.w[i] = shfl_or_zero(m.w[i], src);
-  return r;
-}
 
 // Edges whose predecessor rows a warp gathers per round: 8 row loads per
 // lane in flight whatever the mask width.
@@ -280,53 +259,9 @@ template <int W, typename DT> struct CoeffUnroll {
                                    : GatherUnroll<W>::value;
 };
 
-#ifndef BC_MASK_STAGE
-#define BC_MASK_STAGE 1 // 1: a round's edge masks reach the lanes through shared memory
-#endif
-
-// Per-warp staging of the 32 edge masks of a gather round ([warp][lane][word]):
-// the lane that loaded an edge's mask stores it once, and every lane reads
-// the words of each edge it gathers with one broadcast shared-memory load
-// per 16 bytes instead of two shuffles per 64-bit word.
+// Per-warp staging of a gather round's edge masks ([warp][entry][word], see
+// RoundList).
 __shared__ uint64_t g_mask_stage[kWarpsPerBlock][kWarp][kMaxWords];
-
-template <int W> struct RoundMasks {
-  const uint64_t *stg;
-  __device__ __forceinline__ RoundMasks(const Mask<W> &P, int lane) {
-    uint64_t *row = &g_mask_stage[threadIdx.x >> 5][0][0];
-    stg = row;
-    __syncwarp();
-    if constexpr (W == 1) {
-      row[lane * kMaxWords] = P.w[0];
-    } else {
-#pragma unroll
-      for (int i = 0; i < W; i += 2)
-        *reinterpret_cast<ulonglong2 *>(row + lane * kMaxWords + i) = make_ulonglong2(P.w[i], P.w[i + 1]);
-    }
-    __syncwarp();
-  }
-  // the mask of the edge held by lane src (all zero for src < 0)
-  __device__ __forceinline__ Mask<W> of(int src) const {
-    Mask<W> m;
-    if (src < 0) return Mask<W>::zero();
-    const uint64_t *e = stg + src * kMaxWords;
-    if constexpr (W == 1) {
-      m.w[0] = e[0];
-    } else {
-#pragma unroll
-      for (int i = 0; i < W; i += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(e + i);
-        m.w[i] = t.x;
-        m.w[i + 1] = t.y;
-      }
-    }
-    return m;
-  }
-};
-
-#ifndef BC_ROUND_LIST
-#define BC_ROUND_LIST 1 // 1: a round's edges with sources reach the lanes as a packed list
-#endif
 
 // Per-warp list of a gather round's edges that carry sources (non-empty
 // mask), packed in lane order: the lane holding such an edge writes its
@@ -411,7 +346,6 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, P.any());
   if (!bal) return;
-#if BC_ROUND_LIST
   const RoundList<W> rl(P, u, bal, lane);
   for (int i0 = 0; i0 < rl.cnt; i0 += U) {
     CT x[U][2 * W];
@@ -419,28 +353,9 @@ __device__ __forceinline__ void gather_counts_w(const CT *base, int u, const Mas
     for (int i = 0; i < U; ++i) {
       const CT *row = base + (size_t)rl.vert(i0 + i) * (kK * S) + lane;
       const Mask<W> PE = rl.mask(i0 + i);
-#else
-#if BC_MASK_STAGE
-  const RoundMasks<W> rm(P, lane);
-#endif
-  while (bal) {
-    const LanesU<U> q(bal);
-    CT x[U][2 * W];
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-      const int uu = shfl_or_zero(u, q.l[i]);
-      const CT *row = base + (size_t)uu * (kK * S) + lane;
-#if BC_MASK_STAGE
-      const Mask<W> PE = rm.of(q.l[i]);
-#endif
-#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
-#if BC_MASK_STAGE || BC_ROUND_LIST
         const uint64_t PP = PE.w[wi];
-#else
-        const uint64_t PP = shfl_or_zero(P.w[wi], q.l[i]);
-#endif
         const unsigned lo = (unsigned)PP, hi = (unsigned)(PP >> 32);
         x[i][2 * wi] = (lo & mybit) ? (unit ? CT(1) : ldcg(row + 64 * wi)) : CT(0);
         x[i][2 * wi + 1] = (hi & mybit) ? (unit ? CT(1) : ldcg(row + 64 * wi + 32)) : CT(0);
@@ -469,7 +384,6 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
   const unsigned mybit = 1u << lane;
   unsigned bal = __ballot_sync(kFull, S.any());
   if (!bal) return;
-#if BC_ROUND_LIST
   const RoundList<W> rl(S, x, bal, lane);
   for (int i0 = 0; i0 < rl.cnt; i0 += U) {
     DT y[U][2 * W];
@@ -477,28 +391,9 @@ __device__ __forceinline__ void gather_coeffs_w(const DT *base, int x, const Mas
     for (int i = 0; i < U; ++i) {
       const DT *row = base + (size_t)rl.vert(i0 + i) * (kK * LS) + lane;
       const Mask<W> SE = rl.mask(i0 + i);
-#else
-#if BC_MASK_STAGE
-  const RoundMasks<W> rm(S, lane);
-#endif
-  while (bal) {
-    const LanesU<U> q(bal);
-    DT y[U][2 * W];
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-      const int xx = shfl_or_zero(x, q.l[i]);
-      const DT *row = base + (size_t)xx * (kK * LS) + lane;
-#if BC_MASK_STAGE
-      const Mask<W> SE = rm.of(q.l[i]);
-#endif
-#endif
 #pragma unroll
       for (int wi = 0; wi < W; ++wi) {
-#if BC_MASK_STAGE || BC_ROUND_LIST
         const uint64_t SS = SE.w[wi];
-#else
-        const uint64_t SS = shfl_or_zero(S.w[wi], q.l[i]);
-#endif
         const unsigned lo = (unsigned)SS, hi = (unsigned)(SS >> 32);
         y[i][2 * wi] = (lo & mybit) ? ldcg(row + 64 * wi) : DT(0);
         y[i][2 * wi + 1] = (hi & mybit) ? ldcg(row + 64 * wi + 32) : DT(0);
