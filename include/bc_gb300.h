@@ -120,7 +120,9 @@ typedef struct {
   int64_t n;                 /* vertices */
   int64_t m;                 /* canonical edges */
   int64_t sources;           /* sources processed */
-  int64_t batches;           /* kernel passes (one per batch, or per source for PLAIN) */
+  int64_t batches;           /* kernel passes (one per batch, or per source for PLAIN); batched
+                                calls in the library's source order do not launch sources
+                                without out-edges (their traversal adds nothing to BC) */
   int64_t kernel_launches;   /* kernels launched by the call */
   int32_t max_levels;        /* deepest BFS level count over all sources */
   int32_t overflow_sources;  /* sources whose path count reached 2^64 */
@@ -135,8 +137,9 @@ typedef struct {
   int32_t levels_sum;        /* BFS level counts summed over all batches */
   int32_t chunk_edges;       /* edges per chunk of a high-degree vertex in the last launch */
   int32_t grab;              /* work items a warp fetched at a time in the last launch */
-  int32_t batch_sources;     /* sources per batch in the last launch */
-  int32_t mask_words;        /* 64-bit words per source mask in the last launch (1, 2 or 4) */
+  int32_t batch_sources;     /* sources per batch of the call's full batches (a last batch of at
+                                most half as many runs with fewer mask words) */
+  int32_t mask_words;        /* 64-bit words per source mask of those batches (1, 2 or 4) */
   int32_t push_levels;       /* forward levels whose path counts were pushed, over all batches */
   int32_t batch_groups;      /* batches the last launches ran at once (concurrent groups) */
 } bc_stats;
