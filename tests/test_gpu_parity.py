@@ -754,3 +754,33 @@ def test_last_batch_narrow_and_sources_without_out_edges(ctx, kb, active):
     none = ctx.sources(G, np.tile(sinks[:40], 8), batch_k=kb)
     assert not none.any() and ctx.last_stats()["batches"] == 0
     ctx.destroy_graph(G)
+
+
+def test_512_edge_split_with_unsplit_long_entries(monkeypatch):
+    """With 512-edge chunks, entries of 257..512 in+out edges run as single
+    unsplit items started with the hubs' chunks (and larger hubs as chunks):
+    BC against the oracle in both precisions and count widths, exact and
+    sampled, pulled and pushed, and a repeated job gives the same bits."""
+    import paper_1409_7764_gb300 as bc
+    monkeypatch.setenv("BC_SPLIT", "2")  # the 512-edge candidate of the tuner
+    g = bcgen.rmat(12, 16, seed=3)  # 66 vertices with 257..512 edges, 13 above
+    deg = np.diff(g.row_ptr) + np.bincount(g.col_idx, minlength=g.n)
+    assert ((deg > 256) & (deg <= 512)).sum() > 10 and (deg > 512).sum() > 5
+    ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+    srcs = bcgen.sample_sources(g.n, 700, seed=5)
+    sref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs)
+    with bc.Context(0) as fresh:
+        G = fresh.create_graph(g.row_ptr, g.col_idx)
+        for fp64 in (False, True):
+            for bits in (0, 64):
+                for direction in ("pull", "push"):
+                    a = fresh.exact(G, delta_fp64=fp64, count_bits=bits, direction=direction,
+                                    batch_k=256).copy()
+                    assert fresh.last_stats()["chunk_edges"] == 512
+                    assert_bc_close(a, ref, fp64)
+                    b = fresh.exact(G, delta_fp64=fp64, count_bits=bits, direction=direction,
+                                    batch_k=256).copy()
+                    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+                    assert_bc_close(fresh.sources(G, srcs, delta_fp64=fp64, count_bits=bits,
+                                                  direction=direction, batch_k=128), sref, fp64)
+        fresh.destroy_graph(G)
