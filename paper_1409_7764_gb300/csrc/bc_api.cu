@@ -98,7 +98,44 @@ struct GraphRec {
   std::vector<int32_t> order;
   int32_t *d_order = nullptr;
   std::mutex order_mu;
+  uint64_t fingerprint = 0; // of the CSR as given (0: tuning not remembered, see TuneMemo)
 };
+
+// Tuning results of a graph, remembered by its context beyond the graph's
+// destruction and keyed by a fingerprint of the CSR as given (n, m and evenly
+// spaced samples of the offsets and column ids): a graph created again (a
+// service reloading it, or a benchmark's fresh copies) starts with the width,
+// split and group choices and the fallbacks (64-source batches, pulled
+// counts, 64-bit counts) that its earlier copies found, instead of running
+// the timed trials again.  Every choice computes the same BC, so a different
+// graph with the same fingerprint only inherits launch choices.  Kept for
+// graphs of kTuneMemoMinEdges edges or more, where the trials cost the most.
+struct TuneMemo {
+  int tuned[3];
+  int tuned_words;
+  int tuned_groups[3];
+  bool narrow, no_push, wide_counts;
+};
+constexpr int64_t kTuneMemoMinEdges = 1 << 20;
+constexpr size_t kTuneMemoMax = 4096; // entries (the memo is cleared when full)
+
+uint64_t memo_mix(uint64_t h, uint64_t v) {
+  // splitmix64 finaliser over the running hash and the next value
+  uint64_t z = h ^ (v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2));
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+uint64_t graph_fingerprint(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t m) {
+  constexpr int kSamples = 512;
+  uint64_t h = memo_mix(memo_mix(0x6a09e667f3bcc908ull, (uint64_t)n), (uint64_t)m);
+  for (int i = 0; i <= kSamples; ++i) {
+    h = memo_mix(h, (uint64_t)(uint32_t)row_ptr[(int64_t)n * i / kSamples]);
+    if (m > 0 && i < kSamples) h = memo_mix(h, (uint64_t)(uint32_t)col_idx[m * i / kSamples]);
+  }
+  return h ? h : 1;
+}
 
 // Batch composition order of the vertices as sources.  A batch advances
 // the union of its sources' frontiers, so its cost grows with the (vertex,
@@ -370,6 +407,9 @@ struct bc_ctx {
   std::mutex pin_mu;
   std::multimap<size_t, void *> pin_free;
   size_t pin_free_bytes = 0;
+
+  std::mutex memo_mu;
+  std::unordered_map<uint64_t, TuneMemo> tune_memo; // by graph fingerprint
 
   std::mutex mu;
   std::unordered_map<int64_t, std::unique_ptr<GraphRec>> graphs;
@@ -1300,6 +1340,41 @@ bc_status run_plain_blocks(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *db
 //   - then, unless the schedule fixes it, the work-split trial at the chosen
 //     width: kTuneRounds batches per candidate, fastest kept per graph and
 //     width.
+// Records graph g's current tuning results in its context's memo.
+void remember_tuning(bc_ctx *ctx, const GraphRec &g) {
+  if (!g.fingerprint) return;
+  TuneMemo t;
+  for (int i = 0; i < 3; ++i) {
+    t.tuned[i] = g.tuned[i].load();
+    t.tuned_groups[i] = g.tuned_groups[i].load();
+  }
+  t.tuned_words = g.tuned_words.load();
+  t.narrow = g.narrow.load();
+  t.no_push = g.no_push.load();
+  t.wide_counts = g.wide_counts.load();
+  std::lock_guard<std::mutex> lk(ctx->memo_mu);
+  if (ctx->tune_memo.size() >= kTuneMemoMax && !ctx->tune_memo.count(g.fingerprint))
+    ctx->tune_memo.clear();
+  ctx->tune_memo[g.fingerprint] = t;
+}
+
+// Gives a new graph the tuning results remembered for its fingerprint, if any.
+void recall_tuning(bc_ctx *ctx, GraphRec &g) {
+  if (!g.fingerprint) return;
+  std::lock_guard<std::mutex> lk(ctx->memo_mu);
+  auto it = ctx->tune_memo.find(g.fingerprint);
+  if (it == ctx->tune_memo.end()) return;
+  const TuneMemo &t = it->second;
+  for (int i = 0; i < 3; ++i) {
+    g.tuned[i] = t.tuned[i];
+    g.tuned_groups[i] = t.tuned_groups[i];
+  }
+  g.tuned_words = t.tuned_words;
+  g.narrow = t.narrow;
+  g.no_push = t.no_push;
+  g.wide_counts = t.wide_counts;
+}
+
 bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bool wtrial,
                       int trace_cap) {
   const GraphDev &g = j->g->dev;
@@ -1602,6 +1677,7 @@ bc_status run_batches(bc_ctx *ctx, JobRec *j, KParams p, const DebugOut *dbg, bo
   if (cur_words != ws->words) // back to the workspace's own layout, clean
     BC_TRY(cudaMemsetAsync(static_cast<char *>(ws->mem) + ctl_bytes, 0, ws->slot_bytes - ctl_bytes,
                            st));
+  if (!notune) remember_tuning(ctx, *j->g);
   return BC_OK;
 }
 
@@ -2084,6 +2160,10 @@ bc_status bc_create_graph(bc_ctx *ctx, const int32_t *row_ptr, const int32_t *co
   std::unique_ptr<GraphRec> g;
   bc_status s = build_graph(ctx, row_ptr, col_idx, n, m, g, m_effective);
   if (s != BC_OK) return s;
+  if (m >= kTuneMemoMinEdges) {
+    g->fingerprint = graph_fingerprint(row_ptr, col_idx, n, m);
+    recall_tuning(ctx, *g);
+  }
   std::lock_guard<std::mutex> lk(ctx->mu);
   g->handle = ctx->next_graph++;
   *out = g->handle;
