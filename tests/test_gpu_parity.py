@@ -784,3 +784,30 @@ def test_512_edge_split_with_unsplit_long_entries(monkeypatch):
                     assert_bc_close(fresh.sources(G, srcs, delta_fp64=fp64, count_bits=bits,
                                                   direction=direction, batch_k=128), sref, fp64)
         fresh.destroy_graph(G)
+
+
+def test_tuning_remembered_when_a_graph_is_created_again():
+    """A large graph destroyed and created again in the same context starts
+    with the tuning its first copy found: its first job runs no trials (the
+    same batches as the tuned copy's jobs) and gives the tuned copy's bits."""
+    import paper_1409_7764_gb300 as bc
+    g = bcgen.rmat(17, 16, seed=2)
+    assert g.m >= 1 << 20
+    srcs = bcgen.sample_sources(g.n, 4096, seed=3)
+    keys = ("batch_sources", "mask_words", "chunk_edges", "grab", "batch_groups", "batches")
+    with bc.Context(0) as fresh:
+        G = fresh.create_graph(g.row_ptr, g.col_idx)
+        for _ in range(3):  # the width, split and groups trials
+            fresh.sources(G, srcs)
+        tuned = fresh.sources(G, srcs).copy()
+        st = fresh.last_stats()
+        fresh.destroy_graph(G)
+        G2 = fresh.create_graph(g.row_ptr, g.col_idx)
+        again = fresh.sources(G2, srcs).copy()
+        st2 = fresh.last_stats()
+        for key in keys:
+            assert st2[key] == st[key], key
+        assert np.array_equal(again.view(np.uint64), tuned.view(np.uint64))
+        ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx, srcs[:64])
+        assert_bc_close(fresh.sources(G2, srcs[:64]), ref, False)
+        fresh.destroy_graph(G2)
