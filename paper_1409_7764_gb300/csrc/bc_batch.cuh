@@ -444,8 +444,8 @@ template <typename DT, int W> struct EntrySum {
 // The dependency coefficient's division.  FP64: IEEE division.  FP32: the
 // fast reciprocal-based division (__fdividef, within 2 ulp for these
 // operands: path counts below 2^64 are far from the range where it returns
-// 0), about a fifth of the IEEE sequence's instructions; the FP32 path's
-// bound against the FP64 oracle (1e-4 relative) is unaffected.
+// 0), about a fifth of the IEEE sequence's instructions; well inside the FP32
+// path's error bound (1e-4 relative to exact FP64 dependencies).
 __device__ __forceinline__ double coeff_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float coeff_div(float a, float b) {
   return BC_FAST_FP32_DIV ? __fdividef(a, b) : a / b;

@@ -434,15 +434,23 @@ __device__ __forceinline__ void batch_store_sigma_w(const KParams &p, int w, con
                                                     const AT (&s)[2 * W], unsigned cbits,
                                                     int lane) {
   CT *row = reinterpret_cast<CT *>(p.w.sigma) + (size_t)w * (kK * S);
+  if constexpr (sizeof(CT) == 4) {
+    // 32-bit counts never saturate (a count of 2^32 or more promotes the
+    // job to 64-bit counts before it is stored): no carry bits to record
 #pragma unroll
-  for (int i = 0; i < 2 * W; ++i)
-    if (F.has(i, lane)) row[32 * i + lane] = ((cbits >> i) & 1u) ? CT(~0ull) : CT(s[i]);
+    for (int i = 0; i < 2 * W; ++i)
+      if (F.has(i, lane)) row[32 * i + lane] = CT(s[i]);
+  } else {
 #pragma unroll
-  for (int wi = 0; wi < W; ++wi) {
-    const uint64_t ob = ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi)) & 1u) |
-                         ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi + 1)) & 1u) << 32)) &
-                        F.w[wi];
-    if (ob && lane == 0) atomicOr(&p.w.ctl->ovf[wi], (unsigned long long)ob);
+    for (int i = 0; i < 2 * W; ++i)
+      if (F.has(i, lane)) row[32 * i + lane] = ((cbits >> i) & 1u) ? CT(~0ull) : CT(s[i]);
+#pragma unroll
+    for (int wi = 0; wi < W; ++wi) {
+      const uint64_t ob = ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi)) & 1u) |
+                           ((uint64_t)__ballot_sync(kFull, (cbits >> (2 * wi + 1)) & 1u) << 32)) &
+                          F.w[wi];
+      if (ob && lane == 0) atomicOr(&p.w.ctl->ovf[wi], (unsigned long long)ob);
+    }
   }
 }
 
