@@ -116,7 +116,7 @@ struct TuneMemo {
   int tuned_groups[3];
   bool narrow, no_push, wide_counts;
 };
-constexpr int64_t kTuneMemoMinEdges = 1 << 20;
+constexpr int64_t kTuneMemoMinEdges = 1 << 18;
 constexpr size_t kTuneMemoMax = 4096; // entries (the memo is cleared when full)
 
 uint64_t memo_mix(uint64_t h, uint64_t v) {
