@@ -185,7 +185,11 @@ bc_status bc_destroy_graph(bc_ctx *ctx, bc_graph g);
 
 /* Exact BC over all n sources (paper, Section I).  bc_out: float64[n].
  * opts may be NULL (FP32 dependencies, automatic schedule, raw output to
- * host memory).  Blocks until the result is written. */
+ * host memory).  Blocks until the result is written.  Errors (this and the
+ * other BC calls): BC_ERR_ARG also when a batched schedule meets a graph
+ * whose 2n + 2 x (heavy-vertex chunks) reaches 2^31 (the kernels index a
+ * level step's work items in 32 bits; such a graph's workspace would not
+ * fit one GPU anyway). */
 bc_status bc_exact(bc_ctx *ctx, bc_graph g, const bc_opts *opts, double *bc_out);
 
 /* BC summed over the k given sources (host int32[k], each in [0, n);

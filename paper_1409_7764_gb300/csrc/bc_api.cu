@@ -1693,6 +1693,9 @@ bc_status job_launch(bc_ctx *ctx, JobRec *j, double *out, const DebugOut *dbg) {
   cudaStream_t st = j->st;
   const int kind = batch ? WS_QUEUE : WS_PLAIN;
   j->kind = kind;
+  // the batched kernels index a step's work items (two levels' entries and
+  // heavy chunks) in 32 bits
+  if (batch && 2 * n + 2 * g.heavy_chunks >= (int64_t)INT32_MAX) return BC_ERR_ARG;
   BatchShape bs = batch_shape(j->opts, kind, k, j->g->narrow, dbg != nullptr);
   // wider than one mask word: the queue kernel only
   if (bs.words > 1 && kind != WS_QUEUE) return BC_ERR_ARG;

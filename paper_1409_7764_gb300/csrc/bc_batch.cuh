@@ -106,7 +106,8 @@ __device__ __forceinline__ int64_t next_items(unsigned long long *ctr, int64_t t
 
 // Tracks the heavy entry of consecutive chunk items within one warp.
 struct HeavyCursor {
-  int64_t h = -1, first = 0, end = 0;
+  int64_t h = -1;
+  int first = 0, end = 0;
   __device__ __forceinline__ void seek(const KParams &p, const LevelView &lv, int64_t item,
                                        int lane) {
     if (h >= 0 && item >= first && item < end) return;
@@ -115,8 +116,8 @@ struct HeavyCursor {
     } else {
       h = warp_find_heavy(p.w.hq_c, lv.hoff, lv.nheavy, item, lane);
     }
-    first = ldcg(p.w.hq_c + h);
-    end = (h + 1 < lv.hoff + lv.nheavy) ? ldcg(p.w.hq_c + h + 1) : lv.nhc;
+    first = (int)ldcg(p.w.hq_c + h);
+    end = (int)((h + 1 < lv.hoff + lv.nheavy) ? ldcg(p.w.hq_c + h + 1) : lv.nhc);
   }
 };
 
@@ -726,8 +727,8 @@ template <typename DT, int W, bool SQ, typename CT, typename Scope, int S = W>
 __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int *stage,
                                            WarpCounters &cnt, unsigned long long &dag) {
   const int lane = threadIdx.x & 31;
-  const int64_t gwarp = (int64_t)sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)sc.size() * kWarpsPerBlock;
+  const int gwarp = sc.rank() * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int nwarps = sc.size() * kWarpsPerBlock;
   const int64_t gtid = (int64_t)sc.rank() * kBlock + threadIdx.x;
   const int64_t nthr = (int64_t)sc.size() * kBlock;
   Ctl *ctl = p.w.ctl;
@@ -848,21 +849,24 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
       pv.nheavy = (int64_t)(hpp >> 32);
       pv.nhc = (int64_t)(hpp & 0xffffffffull);
     }
-    const int64_t poff = push ? pv.nhc + (pv.hi - pv.lo) : 0;
+    const int poff = push ? (int)(pv.nhc + (pv.hi - pv.lo)) : 0;
 
     unsigned long long *ctr = &ctl->work[step & 3];
-    const int64_t total = poff + lv.nhc + (lv.hi - lv.lo);
+    // a step's work items (and the warps' indices into them) are 32-bit:
+    // fewer than 2n + 2 x (heavy chunks) < 2^31, which the host checks for
+    // every graph a batched job runs on; 64-bit counters here spilled
+    const int total = poff + (int)(lv.nhc + (lv.hi - lv.lo));
     trace_step(p, step, l, total, lv.nhc, gtid);
     HeavyCursor hc, hcp;
     int nst = 0; // staged new vertices of this warp
     const int grab = p.grab;
-    const int64_t stat = nwarps * grab;
-    int64_t base = gwarp * grab;
+    const int stat = nwarps * grab;
+    int base = gwarp * grab;
     const long long t_step = phase_clock();
     while (base < total) {
-      const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
-      const int64_t end = base + grab < total ? base + grab : total;
-      for (int64_t item = base; item < end && item < poff; ++item) {
+      const int next = BC_PREFETCH_GROUPS ? (int)next_items(ctr, total, stat, grab, lane) : 0;
+      const int end = base + grab < total ? base + grab : total;
+      for (int item = base; item < end && item < poff; ++item) {
         // push form: one entry (or one chunk of a heavy entry) of level l-1
         int u, ob, oe;
         if (item < pv.nhc) {
@@ -883,9 +887,9 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
         if (lane == 0) cnt.out_e += (uint64_t)(oe - ob);
       }
       // level l's own items, numbered from 0
-      const int64_t lbase = base > poff ? base - poff : 0;
-      const int64_t lend = end > poff ? end - poff : 0;
-      for (int64_t item = lbase; item < lend && item < lv.nhc; ++item) {
+      const int lbase = base > poff ? base - poff : 0;
+      const int lend = end > poff ? end - poff : 0;
+      for (int item = lbase; item < lend && item < (int)lv.nhc; ++item) {
         // one chunk of a heavy entry
         hc.seek(p, lv, item, lane);
         const int64_t h = hc.h;
@@ -1021,7 +1025,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           }
         }
       }
-      base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
+      base = BC_PREFETCH_GROUPS ? next : (int)next_items(ctr, total, stat, grab, lane);
     }
     __syncwarp();
     stage_flush(p, lv, stage, nst, lane);
@@ -1080,17 +1084,17 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
     // exports report it)
     const bool gather = l < L - 1 && (l > 0 || p.dbg_d != nullptr);
     unsigned long long *ctr = &ctl->work[step & 3];
-    const int64_t total = bl.nhc + (bl.hi - bl.lo);
+    const int total = (int)(bl.nhc + (bl.hi - bl.lo));
     trace_step(p, step, -1 - l, total, bl.nhc, gtid);
     HeavyCursor hc;
     const int grab = p.grab;
-    const int64_t stat = nwarps * grab;
-    int64_t base = gwarp * grab;
+    const int stat = nwarps * grab;
+    int base = gwarp * grab;
     const long long t_step = phase_clock();
     while (base < total) {
-      const int64_t next = BC_PREFETCH_GROUPS ? next_items(ctr, total, stat, grab, lane) : 0;
-      const int64_t end = base + grab < total ? base + grab : total;
-      for (int64_t item = base; item < end && item < bl.nhc; ++item) {
+      const int next = BC_PREFETCH_GROUPS ? (int)next_items(ctr, total, stat, grab, lane) : 0;
+      const int end = base + grab < total ? base + grab : total;
+      for (int item = base; item < end && item < (int)bl.nhc; ++item) {
         hc.seek(p, bl, item, lane);
         const int64_t h = hc.h;
         const int64_t e = ldcg(p.w.hq_e + h);
@@ -1153,7 +1157,7 @@ __device__ __forceinline__ void batch_body(const KParams &p, const Scope sc, int
           if (gather && lane == 0) cnt.out_e += (uint64_t)(re - rs);
         }
       }
-      base = BC_PREFETCH_GROUPS ? next : next_items(ctr, total, stat, grab, lane);
+      base = BC_PREFETCH_GROUPS ? next : (int)next_items(ctr, total, stat, grab, lane);
     }
     const long long t_done = phase_clock();
     if (!sc.sync(ctl, p.timeout_ns)) return;
