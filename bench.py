@@ -100,8 +100,8 @@ def bytes_model(stats, delta_bytes):
            4 + 8W B per scanned edge (the neighbour id and its W-word mask),
            (8 + b) B per (source, DAG edge) (predecessor path count,
            successor coefficient), (16 + b) B per (source, reached vertex)
-           (path count write and read, coefficient write; counts need no
-           reset, since a count is only read where its batch wrote it).
+           (path count write and read, coefficient write; the reset of each
+           count after its backward step is not counted).
     plain kernel (1): (84 + b) B per entry, 8 B per scanned edge (column +
            int32 depth), (8 + b) B per DAG edge.
     """

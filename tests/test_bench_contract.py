@@ -27,3 +27,20 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_bytes_models_follow_their_stated_formulas():
+    """The two bytes models of the roofline, on made-up counters, equal the
+    formulas the benchmark line states (so a reader can redo them by hand)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    E, I, O, D, R = 10, 100, 200, 1000, 50
+    st = dict(frontier_entries=E, scanned_in_edges=I, scanned_out_edges=O, dag_pairs=D,
+              reached_pairs=R, kernel_kind=2, mask_words=4)
+    for b in (4, 8):
+        assert bench.method_bytes_model(st, b) == 8 * E + 4 * (I + O) + 32 * (I + O) + \
+            (16 + b) * D + (16 + b) * R
+        assert bench.bytes_model(st, b) == 124 * E + 36 * (I + O) + (8 + b) * D + (16 + b) * R
+    plain = dict(st, kernel_kind=1)
+    assert bench.method_bytes_model(plain, 8) == 8 * (I + O) + 32 * D + 88 * E
+    assert bench.bytes_model(plain, 8) == 92 * E + 8 * (I + O) + 16 * D
