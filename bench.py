@@ -565,7 +565,7 @@ def run_many(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order,
-                       batch_k=max(args.batch_k, 0))
+                       batch_k=max(args.batch_k, 0), count_bits=args.count_bits)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -576,7 +576,7 @@ def run_many(args):
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
         ctx.exact_many(hs, delta_fp64=fp64, keep_source_order=args.keep_source_order,
-                       batch_k=max(args.batch_k, 0))
+                       batch_k=max(args.batch_k, 0), count_bits=args.count_bits)
         e.record(stream)
         torch.cuda.synchronize()
         ms.append(s.elapsed_time(e))
@@ -592,7 +592,8 @@ def run_many(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = ctx.create_graphs([(g.row_ptr, g.col_idx) for g in graphs])
-        ctx.exact_many(h2, delta_fp64=fp64, batch_k=max(args.batch_k, 0))
+        ctx.exact_many(h2, delta_fp64=fp64, batch_k=max(args.batch_k, 0),
+                       count_bits=args.count_bits)
         for h in h2:
             ctx.destroy_graph(h)
         e2e.append(time.perf_counter() - t0)
@@ -623,7 +624,8 @@ def run_many(args):
         "metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
-        "dtype": "u64+f64" if fp64 else "u64+f32", "data": "synthetic",
+        "dtype": ("u64" if args.count_bits == 64 else "u32") + ("+f64" if fp64 else "+f32"),
+        "data": "synthetic",
         "config": {"workload": "rmat-many10k", "graphs": len(graphs),
                    "scales": "6..12 uniform", "edge_factors": "4..16 uniform",
                    "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs)),

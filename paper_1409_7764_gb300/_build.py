@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbc_gb300.so")
-SOURCES = ["bc_kernels.cu", "bc_narrow.cu", "bc_graph.cu", "bc_api.cu", "bc_noalloc.cu"]
+SOURCES = ["bc_kernels.cu", "bc_narrow.cu", "bc_many.cu", "bc_graph.cu", "bc_api.cu",
+           "bc_noalloc.cu"]
 HEADERS = ["bc_internal.cuh", "bc_device.cuh", "bc_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

@@ -2686,8 +2686,22 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
   void *ws_mem = nullptr;
   Work *d_works = nullptr;
   GraphDev *d_graphs = nullptr;
-  int32_t *d_order = nullptr, *d_iota = nullptr;
+  int32_t *d_order = nullptr, *d_iota = nullptr, *d_trav = nullptr;
   int64_t *d_off = nullptr;
+  // sources each small graph runs: with grouped batches, its vertices with
+  // out-edges (first in its batch order; a source without out-edges reaches
+  // nothing and adds nothing to BC)
+  const bool grouped = o.source_order == 0;
+  std::vector<int32_t> trav((size_t)count, 0);
+  for (int32_t i : small) {
+    const GraphRec &gr = *gs[(size_t)i];
+    int32_t t = gr.dev.n;
+    if (grouped && gr.dev.order && !gr.order.empty()) {
+      t = 0;
+      for (int32_t v = 0; v < gr.dev.n; ++v) t += gr.row_ptr[(size_t)v + 1] != gr.row_ptr[(size_t)v];
+    }
+    trav[(size_t)i] = t;
+  }
   unsigned *d_next = nullptr;
   if (!small.empty()) {
     // one workspace per thread block, sized for the largest small graph
@@ -2729,6 +2743,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     alloc(reinterpret_cast<void **>(&d_order), sizeof(int32_t) * small.size());
     alloc(reinterpret_cast<void **>(&d_iota), sizeof(int32_t) * iota.size());
     alloc(reinterpret_cast<void **>(&d_off), sizeof(int64_t) * off.size());
+    alloc(reinterpret_cast<void **>(&d_trav), sizeof(int32_t) * trav.size());
     alloc(reinterpret_cast<void **>(&d_next), sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemsetAsync(ws_mem, 0, stride * (size_t)grid, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_works, works.data(), sizeof(Work) * works.size(), cudaMemcpyHostToDevice, st);
@@ -2736,6 +2751,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, small.data(), sizeof(int32_t) * small.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_iota, iota.data(), sizeof(int32_t) * iota.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && count) e = cudaMemcpyAsync(d_trav, trav.data(), sizeof(int32_t) * trav.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(unsigned), st);
     ManyParams mp;
     mp.base.ovf_flags = d_ovf;
@@ -2751,7 +2767,9 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     mp.kb = kb;
     mp.max_words = ws_words;
     total.mask_words = std::max(total.mask_words, ws_words);
-    mp.grouped = o.source_order == 0 ? 1 : 0;
+    mp.grouped = grouped ? 1 : 0;
+    mp.traverse = d_trav;
+    mp.counts64 = o.count_bits == 64 ? 1 : 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -2773,7 +2791,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     for (int32_t i : small) {
       const int64_t gn = gs[(size_t)i]->dev.n;
       const int64_t gkb = ws_words > 1 ? kK * auto_words(gn, ws_words) : kb;
-      total.batches += (gn + gkb - 1) / gkb;
+      total.batches += (trav[(size_t)i] + gkb - 1) / gkb;
     }
     total.kernel_launches += 1;
   }
@@ -2832,6 +2850,7 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
   if (d_order) cudaFreeAsync(d_order, st);
   if (d_iota) cudaFreeAsync(d_iota, st);
   if (d_off) cudaFreeAsync(d_off, st);
+  if (d_trav) cudaFreeAsync(d_trav, st);
   if (d_next) cudaFreeAsync(d_next, st);
   cudaStreamSynchronize(st);
   if (ws_mem) cudaFree(ws_mem);

@@ -1249,14 +1249,27 @@ __device__ void block_reset_workspace(const Work &w, int n) {
   __syncthreads();
 }
 
+// One batch of the many-graph launch with `words` mask words and path-count
+// rows of CT.
+template <typename DT, typename CT>
+__device__ __forceinline__ void many_batch(const KParams &p, int words, int *stage,
+                                           WarpCounters &cnt, unsigned long long &dag) {
+  if (words == 4) batch_body<DT, 4, false, CT>(p, CtaScope(), stage, cnt, dag);
+  else if (words == 2) batch_body<DT, 2, false, CT>(p, CtaScope(), stage, cnt, dag);
+  else batch_body<DT, 1, false, CT>(p, CtaScope(), stage, cnt, dag);
+}
+
 // Exact BC of many small graphs in one launch: each thread block takes the
 // next graph from a shared counter (largest work first) and runs all of that
 // graph's source batches itself, with CTA barriers between levels, so every
 // graph's BC is written by one block without atomics.  Each graph gets its
-// own batch width (auto_words of its vertex count, up to mp.max_words); a
-// wide batch that overruns its queue (sized for 64 depths per vertex) is
-// stopped in its forward sweep, before any BC is written, and the graph's
-// remaining sources continue 64 per batch.
+// own batch width (auto_words of its vertex count, up to mp.max_words) and
+// starts with 32-bit path-count rows unless mp.counts64.  A batch that
+// cannot finish in its configuration stops in its forward sweep, before any
+// BC is written, and is run again: after a queue overrun of a wide batch
+// the graph's remaining sources continue 64 per batch, after a count of
+// 2^32 or more with 64-bit rows.  Sources without out-edges, last in the
+// grouped order, are not run (their dependencies are all zero).
 template <typename DT>
 __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const ManyParams mp) {
   __shared__ int s_stage[kWarpsPerBlock][kStage];
@@ -1277,24 +1290,27 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks) many_kernel(const Man
     const int gi = __ldg(mp.order + it);
     p.g = mp.graphs[gi];
     const int64_t off = __ldg(mp.out_off + gi);
+    const int nt = __ldg(mp.traverse + gi);
     p.bc = mp.out + off;
     int words = mp.max_words > 1 ? auto_words(p.g.n, mp.max_words) : 1;
-    for (int b0 = 0; b0 < p.g.n;) {
+    bool wide = mp.counts64 != 0;
+    for (int b0 = 0; b0 < nt;) {
       const int kb = words > 1 ? kK * words : mp.kb;
       p.src = (mp.grouped && p.g.order ? p.g.order : mp.iota) + b0;
-      p.k = p.g.n - b0 < kb ? p.g.n - b0 : kb;
+      p.k = nt - b0 < kb ? nt - b0 : kb;
       p.src_base = off + b0;
-      if (words == 4)
-        batch_body<DT, 4, false, uint64_t>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
-      else if (words == 2)
-        batch_body<DT, 2, false, uint64_t>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
-      else
-        batch_body<DT, 1, false, uint64_t>(p, CtaScope(), s_stage[threadIdx.x >> 5], cnt, dag);
+      if (wide) many_batch<DT, uint64_t>(p, words, s_stage[threadIdx.x >> 5], cnt, dag);
+      else many_batch<DT, uint32_t>(p, words, s_stage[threadIdx.x >> 5], cnt, dag);
       __syncthreads();
       const int e = read_err(p.w.ctl);
       if ((e == KERR_QUEUE || e == KERR_HEAVY) && words > 1) {
         block_reset_workspace(p.w, p.g.n);
         words = 1; // redo these sources 64 per batch
+        continue;
+      }
+      if (e == KERR_WIDE && !wide) {
+        block_reset_workspace(p.w, p.g.n);
+        wide = true; // redo these sources with 64-bit counts
         continue;
       }
       if (e) break;

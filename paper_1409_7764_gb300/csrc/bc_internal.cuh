@@ -185,7 +185,13 @@ struct ManyParams {
   const Work *works = nullptr;    // [grid] one workspace per thread block
   const int32_t *iota = nullptr;  // [max n] 0, 1, 2, ...: the sources of exact BC in given order
   int32_t grouped = 1;            // 1: batches take the sources in GraphDev::order
+  const int32_t *traverse = nullptr; // [count] sources each graph runs: with grouped
+                                  // batches its vertices with out-edges (first in
+                                  // GraphDev::order; the others add nothing), else n
   int32_t max_words = 1;          // widest source masks a graph may use (auto_words)
+  int32_t counts64 = 0;           // 1: 64-bit path-count rows throughout; 0: 32-bit rows,
+                                  // and a graph with a count of 2^32 or more continues
+                                  // (from the batch that found it) with 64-bit rows
   double *out = nullptr;          // [sum of n]
   unsigned *next = nullptr;       // graph counter
   int32_t kb = kK;                // sources per batch when max_words == 1
@@ -206,7 +212,8 @@ struct MultiParams {
   int64_t first = 0;            // first source of the grouped range
 };
 
-// Host launchers (bc_kernels.cu).  Return a cudaError_t.
+// Host launchers (bc_kernels.cu; the many-graph launch in bc_many.cu).
+// Return a cudaError_t.
 cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st);
 int max_grid_many(bool fp64, int device);
 cudaError_t launch_batch(const KParams &p, bool fp64, int grid, cudaStream_t st, int words = 1,

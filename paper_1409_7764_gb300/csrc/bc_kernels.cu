@@ -1,7 +1,7 @@
 // Kernel translation unit of the GB300 betweenness-centrality library: the
 // batched kernels in their standard instantiations (one workspace layout per
-// mask width), the many-graph kernel, the one-source plain kernels and the
-// small helper kernels, with their host launchers.  The batched sweeps
+// mask width), the one-source plain kernels and the small helper kernels,
+// with their host launchers.  The batched sweeps
 // themselves are in bc_batch.cuh.
 #include "bc_batch.cuh"
 
@@ -575,17 +575,6 @@ cudaError_t launch_max_rel_err(const double *est, const double *err, int64_t n, 
   if (grid > 1024) grid = 1024;
   max_rel_err_kernel<<<grid, 256, 0, st>>>(est, err, n, min_est, out);
   return cudaGetLastError();
-}
-
-cudaError_t launch_many(const ManyParams &mp, bool fp64, int grid, cudaStream_t st) {
-  if (fp64) many_kernel<double><<<grid, kBlock, 0, st>>>(mp);
-  else many_kernel<float><<<grid, kBlock, 0, st>>>(mp);
-  return cudaGetLastError();
-}
-
-int max_grid_many(bool fp64, int device) {
-  return fp64 ? max_grid_for(many_kernel<double>, device)
-              : max_grid_for(many_kernel<float>, device);
 }
 
 int max_grid_batch(bool fp64, int device, int words) {

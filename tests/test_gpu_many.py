@@ -82,6 +82,31 @@ def test_many_graphs_per_graph_width_and_overrun(ctx):
         ctx.destroy_graph(h)
 
 
+def test_many_graphs_count_rows_and_sources_without_out_edges(ctx):
+    """Path counts start in 32-bit rows: a graph whose counts reach 2^32
+    (layered chains of 32 and 40 stages: 2^32 and 2^40 paths to the last
+    sink) continues with 64-bit rows from the batch that found it, and every
+    result equals the run with 64-bit rows throughout bit for bit and the
+    oracle.  Sources without out-edges are not run: an out-star runs its
+    centre alone."""
+    gs = [bcgen.layered_chain(40, 2), bcgen.layered_chain(32, 2), bcgen.layered_chain(31, 2),
+          bcgen.star(3000, "out"), bcgen.rmat(12, 4, seed=9), bcgen.rmat(11, 16, seed=4),
+          bcgen.rmat(8, 4, seed=2)]
+    handles = [ctx.create_graph(g.row_ptr, g.col_idx) for g in gs]
+    for fp64, tol in ((True, 1e-12), (False, 1e-4)):
+        a = [x.copy() for x in ctx.exact_many(handles, delta_fp64=fp64)]
+        b = ctx.exact_many(handles, delta_fp64=fp64, count_bits=64)
+        for g, x, y in zip(gs, a, b):
+            np.testing.assert_array_equal(x, y)
+            ref, _ = oracle.bc(g.n, g.row_ptr, g.col_idx)
+            close(x, ref, tol)
+    out = ctx.exact_many([handles[3]], delta_fp64=True)[0]
+    assert ctx.last_stats()["batches"] == 1
+    assert not out.any()
+    for h in handles:
+        ctx.destroy_graph(h)
+
+
 def test_create_graphs_in_one_call(ctx):
     """bc_create_graphs: small graphs prepared on host threads, a large one on
     the device, a non-canonical one canonicalised; each resident graph equals
