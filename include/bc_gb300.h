@@ -112,7 +112,9 @@ typedef struct {
                             bits, and a job in which a count reaches 2^32 reruns with 64 bits
                             (so do later jobs on that graph); 64 = always 64 bits.  Sums and
                             results are the same; 32-bit rows halve the bytes each
-                            shortest-path edge moves.  Estimator calls use 64 bits */
+                            shortest-path edge moves.  bc_exact_many follows it per graph:
+                            a graph whose count reaches 2^32 continues with 64 bits from
+                            that batch.  Estimator calls use 64 bits */
 } bc_opts;
 
 /* Per-call statistics.  Counters feed the bytes model of the roofline. */
@@ -291,8 +293,10 @@ bc_status bc_debug_graph(bc_ctx *ctx, bc_graph g, int32_t *row_ptr, int32_t *col
  * with batch_k = 0 each graph gets 64, 128 or 256 by the automatic rule on
  * its vertex count, and a wide batch that overruns its frontier queue
  * continues 64 per batch) with block-level barriers between BFS levels and
- * writes that graph's BC itself; larger graphs run one after another through the
- * grid-wide batched kernel.  bc_out receives the vectors back to back (graph
+ * writes that graph's BC itself (path counts in 32-bit rows unless
+ * opts.count_bits = 64; with batches composed by the library, source_order = 0,
+ * a graph's sources without out-edges, whose terms are all zero, are not run);
+ * larger graphs run one after another through the grid-wide batched kernel.  bc_out receives the vectors back to back (graph
  * i at offset sum_{j<i} n_j), host or device memory per opts.out_device;
  * normalize applies per graph, scale_sampled has no effect (all sources).
  * BC_ERR_ADMISSION when the per-block workspaces do not fit the budget. */

@@ -234,17 +234,23 @@ class Context:
         res = (est[:g.n], err[:g.n], int(used.value))
         return self._finish(rc, res, "bc_sources_adaptive")
 
-    def exact_many(self, graphs, **opts):
+    def exact_many(self, graphs, out=None, **opts):
+        """BC of the graphs in one vector of sum(n) doubles, graph i at offset
+        sum_{j<i} n_j.  With `out` a torch CUDA float64 tensor of that length
+        the vector is written there on the device and `out` is returned;
+        otherwise a list of per-graph host arrays (views of one vector)."""
         hs = np.array([g.handle for g in graphs], dtype=np.int64)
         total = sum(g.n for g in graphs)
-        out = np.empty(max(total, 1), dtype=np.float64)
-        o = make_opts(**opts)
+        ptr, dev, holder = _out_buffer(out, total)
+        o = make_opts(out_device=dev, **opts)
         rc = self._lib.bc_exact_many(self._h, hs.ctypes.data if hs.size else None, len(graphs),
-                                     ctypes.byref(o), out.ctypes.data)
+                                     ctypes.byref(o), ptr)
         _check(rc, "bc_exact_many")
+        if dev:
+            return holder
         res, off = [], 0
         for g in graphs:
-            res.append(out[off:off + g.n])
+            res.append(holder[off:off + g.n])
             off += g.n
         return res
 

@@ -2722,8 +2722,21 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     const size_t ws_budget = (ctx->budget > ctx->used ? ctx->budget - ctx->used : 0) / 2;
     grid = (int)std::min<int64_t>(grid, std::max<int64_t>(1, (int64_t)(ws_budget / stride)));
     grid = (int)std::min<int64_t>(grid, (int64_t)small.size());
-    if (grid < 1 || stride * (size_t)grid > ws_budget) return BC_ERR_ADMISSION;
-    BC_TRY(cudaMalloc(&ws_mem, stride * (size_t)grid));
+    auto release = [&] {
+      cudaFreeAsync(d_out, st);
+      cudaFreeAsync(d_ovf, st);
+      cudaFreeAsync(d_cnt, st);
+    };
+    if (grid < 1 || stride * (size_t)grid > ws_budget) {
+      release();
+      return BC_ERR_ADMISSION;
+    }
+    const cudaError_t ea = cudaMalloc(&ws_mem, stride * (size_t)grid);
+    if (ea != cudaSuccess) {
+      ws_mem = nullptr;
+      release();
+      return cuda_status(ea);
+    }
     std::vector<Work> works((size_t)grid);
     for (int c = 0; c < grid; ++c) {
       WsRec r = proto;
@@ -2776,24 +2789,24 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     if (e == cudaSuccess) e = launch_many(mp, fp64, grid, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-    // the block workspaces' control words carry any device error
-    std::vector<int> errs((size_t)grid, 0);
-    for (int c = 0; c < grid && e == cudaSuccess; ++c)
-      e = cudaMemcpyAsync(&errs[(size_t)c], &works[(size_t)c].ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    // the block workspaces' control words carry any device error: the first
+    // one found is gathered into block 0's and read back once
+    int err0 = 0;
+    if (e == cudaSuccess) e = launch_gather_err(works[0].ctl, stride, grid, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&err0, &works[0].ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) cudaEventElapsedTime(&many_ms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) status = cuda_status(e);
-    for (int c = 0; c < grid && status == BC_OK; ++c)
-      if (errs[(size_t)c]) status = BC_ERR_INTERNAL;
-    total.batches += 0;
+    if (status == BC_OK && err0) status = BC_ERR_INTERNAL;
     for (int32_t i : small) {
       const int64_t gn = gs[(size_t)i]->dev.n;
       const int64_t gkb = ws_words > 1 ? kK * auto_words(gn, ws_words) : kb;
       total.batches += (trav[(size_t)i] + gkb - 1) / gkb;
     }
-    total.kernel_launches += 1;
+    total.kernel_launches += 2;
   }
   // larger graphs, one grid-wide job each, straight into the device result
   for (int32_t i : big) {

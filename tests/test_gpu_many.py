@@ -103,6 +103,12 @@ def test_many_graphs_count_rows_and_sources_without_out_edges(ctx):
     out = ctx.exact_many([handles[3]], delta_fp64=True)[0]
     assert ctx.last_stats()["batches"] == 1
     assert not out.any()
+    # the same vectors written into a device tensor
+    import torch
+    host = ctx.exact_many(handles, delta_fp64=True)
+    dev = torch.full((sum(g.n for g in gs),), -1.0, dtype=torch.float64, device="cuda")
+    assert ctx.exact_many(handles, out=dev, delta_fp64=True) is dev
+    np.testing.assert_array_equal(dev.cpu().numpy(), np.concatenate(host))
     for h in handles:
         ctx.destroy_graph(h)
 
