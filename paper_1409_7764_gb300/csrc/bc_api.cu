@@ -99,6 +99,7 @@ struct GraphRec {
   int32_t *d_order = nullptr;
   std::mutex order_mu;
   uint64_t fingerprint = 0; // of the CSR as given (0: tuning not remembered, see TuneMemo)
+  std::atomic<int32_t> with_out{-1}; // vertices with out-edges (-1: not counted yet)
 };
 
 // Tuning results of a graph, remembered by its context beyond the graph's
@@ -2694,11 +2695,15 @@ bc_status bc_exact_many(bc_ctx *ctx, const bc_graph *graphs, int32_t count, cons
   const bool grouped = o.source_order == 0;
   std::vector<int32_t> trav((size_t)count, 0);
   for (int32_t i : small) {
-    const GraphRec &gr = *gs[(size_t)i];
+    GraphRec &gr = *gs[(size_t)i];
     int32_t t = gr.dev.n;
     if (grouped && gr.dev.order && !gr.order.empty()) {
-      t = 0;
-      for (int32_t v = 0; v < gr.dev.n; ++v) t += gr.row_ptr[(size_t)v + 1] != gr.row_ptr[(size_t)v];
+      t = gr.with_out.load();
+      if (t < 0) { // counted once per graph (concurrent callers store the same count)
+        t = 0;
+        for (int32_t v = 0; v < gr.dev.n; ++v) t += gr.row_ptr[(size_t)v + 1] != gr.row_ptr[(size_t)v];
+        gr.with_out = t;
+      }
     }
     trav[(size_t)i] = t;
   }
