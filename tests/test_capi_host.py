@@ -86,3 +86,12 @@ def test_options_struct_matches_header(tmp_path):
         want.append(ctypes.sizeof(cls))
         want += [getattr(cls, fname).offset for fname, _ in cls._fields_]
     assert got == want
+
+
+def test_build_compiles_every_source_and_tracks_every_header():
+    """Every translation unit under csrc/ is compiled into the library, and
+    every header it includes makes the library stale when it changes."""
+    from paper_1409_7764_gb300 import _build
+    files = os.listdir(_build.CSRC)
+    assert sorted(f for f in files if f.endswith(".cu")) == sorted(_build.SOURCES)
+    assert sorted(f for f in files if f.endswith(".cuh")) == sorted(_build.HEADERS)
