@@ -44,3 +44,19 @@ def test_bytes_models_follow_their_stated_formulas():
     plain = dict(st, kernel_kind=1)
     assert bench.method_bytes_model(plain, 8) == 8 * (I + O) + 32 * D + 88 * E
     assert bench.bytes_model(plain, 8) == 92 * E + 8 * (I + O) + 16 * D
+
+
+def test_traffic_reported_only_for_the_kernel_it_was_measured_on(monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while its
+    kernel hash matches the current kernel sources."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+        rec = json.load(fh)
+    entry = rec["rmat20-sampled4096"]
+    assert len(bench.kernel_source_sha()) == 16
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: entry["kernel_sha"])
+    assert bench.ncu_traffic("rmat20-sampled4096") == entry["dram_bytes_per_launch"]
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
+    assert bench.ncu_traffic("rmat20-sampled4096") is None
+    assert bench.ncu_traffic("no-such-workload") is None
